@@ -1,0 +1,190 @@
+/*
+ * rlqr.h -- C ABI of the B300 dual-regularized LQR solver.
+ *
+ * The library solves the first-order optimality system of a dual-regularized
+ * LQR problem (Section "Dual-Regularized LQR", eq. min-max-with-ys), i.e. the
+ * linear system of eq. primal-dual-linear-system specialised as in eq.
+ * optimal-control-specialization:
+ *
+ *     [ P  C^T ] [x]     [s]        x = (x_0, u_0, x_1, u_1, ..., x_N)
+ *     [ C  -D  ] [y] = - [c]        y = (y_0, ..., y_N)
+ *
+ * with P = blkdiag([Q_i M_i; M_i^T R_i], Q_N), C the bidiagonal dynamics
+ * matrix (-I on the diagonal, [A_i B_i] below it), D = blkdiag(Delta_i) with
+ * Delta_i = delta * I for i = 0..N, s = (q_0, r_0, ..., q_N), c = (c_0..c_N).
+ *
+ * It returns x, u, the costates y and a per-stage pivot-PD certificate
+ * (Section "Inertia Certification", Theorem
+ * riccati-inertia-certification-theorem): for delta > 0 the KKT matrix has
+ * inertia (N(n+m)+n, (N+1)n, 0) iff every flag byte equals 3.
+ *
+ * Conventions shared by every entry point
+ *   - All problem arrays are DEVICE pointers to FP64 values, row-major
+ *     matrices, stage-major and contiguous:
+ *       Q (N+1)*nx*nx   M N*nx*nu   R N*nu*nu   q (N+1)*nx   r N*nu
+ *       A N*nx*nx       B N*nx*nu   c (N+1)*nx
+ *     Q_i and R_i are read as (X + X^T)/2.  c_0 is the initial-state term,
+ *     c_{i+1} the offset of the dynamics x_{i+1} = A_i x_i + B_i u_i + c_{i+1}.
+ *   - Outputs x (N+1)*nx, u N*nu, y (N+1)*nx (FP64) and pivot_pd (N+1 bytes)
+ *     are DEVICE pointers.  pivot_pd[i] bit0 = (I + delta P_i) is PD,
+ *     bit1 = G_i is PD (set for i = N, which has no control pivot).
+ *   - The caller owns every buffer.  The library never allocates device
+ *     memory: scratch lives in a caller-provided workspace whose size the
+ *     *_workspace_bytes functions return.
+ *   - Every call is asynchronous on the given stream (a cudaStream_t; NULL =
+ *     the legacy default stream) and issues no host synchronisation.  The
+ *     host return value covers argument validation and launch errors only;
+ *     per-instance outcomes (status, relative residual, refinement
+ *     iterations) are written to device arrays.
+ *   - A zero or non-finite pivot makes the recursion undefined: that
+ *     instance's status becomes RLQR_ERR_SINGULAR and its outputs are
+ *     unspecified.  A pivot that is merely not PD gives RLQR_NOT_PD, which is
+ *     informational: by Theorem riccati-rational-identity-theorem the result
+ *     is still the unique KKT solution.
+ */
+#ifndef RLQR_H_
+#define RLQR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t, declared here so that this header does not
+ * need the CUDA headers. */
+typedef struct CUstream_st *rlqr_stream_t;
+
+typedef enum {
+  RLQR_OK = 0,
+  RLQR_NOT_PD = 1,             /* solved; at least one pivot is not PD (informational) */
+  RLQR_ERR_ARG = 2,            /* invalid argument (dimensions, null pointer, option) */
+  RLQR_ERR_SINGULAR = 3,       /* zero or non-finite pivot: recursion undefined */
+  RLQR_ERR_NOT_CONVERGED = 4,  /* refinement stopped above the residual tolerance */
+  RLQR_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+  RLQR_ERR_WORKSPACE = 6,      /* workspace too small or misaligned */
+  RLQR_ERR_CUDA = 7            /* a CUDA launch or runtime call failed */
+} rlqr_status;
+
+typedef enum {
+  RLQR_ALGO_AUTO = 0, /* SEQ unless the horizon is long and there are few instances */
+  RLQR_ALGO_SEQ = 1,  /* sequential Riccati recursion, O(N) depth (Section "Sequential Algorithm") */
+  RLQR_ALGO_SCAN = 2  /* associative-scan recursion, O(log N) depth (Section "Parallel Algorithm") */
+} rlqr_algo;
+
+typedef enum {
+  RLQR_FP64 = 0, /* every step in FP64 */
+  RLQR_MIXED = 1 /* FP32 recursion; FP64 pivot certificate, FP64 residual, FP64 correction */
+} rlqr_prec;
+
+/* One dual-regularized LQR instance (all pointers device, see above). */
+typedef struct {
+  int32_t N;  /* number of stages, >= 1 */
+  int32_t nx; /* state dimension n, >= 1 */
+  int32_t nu; /* control dimension m, >= 1 */
+  const double *Q, *M, *R, *q, *r, *A, *B, *c;
+  double delta; /* Delta_i = delta * I, delta >= 0 (0 = standard LQR, SEQ only) */
+} rlqr_problem;
+
+typedef struct {
+  int32_t max_refine; /* iterative-refinement passes after the first solve (MIXED); >= 0 */
+  double tol;         /* target normwise backward error ||Kz+b|| / (||K|| ||z|| + ||b||) */
+  rlqr_algo algo;
+  rlqr_prec prec;
+} rlqr_opts;
+
+/* Default options: SEQ-or-SCAN automatic, FP64, tol 1e-9, max_refine 3. */
+rlqr_opts rlqr_default_opts(void);
+
+/* Version string of the library build. */
+const char *rlqr_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char *rlqr_status_string(rlqr_status s);
+
+/* ------------------------------------------------------------------ *
+ * Single instance: factor / solve / residual, the split of the factor, *
+ * solve and residual callbacks (Section "Software"), with factor reuse  *
+ * across right-hand sides by Corollary p-recurrence.                    *
+ * ------------------------------------------------------------------ */
+
+/* Bytes of workspace rlqr_factor needs for these dimensions and options.
+ * Returns 0 for invalid dimensions. */
+size_t rlqr_workspace_bytes(int32_t N, int32_t nx, int32_t nu, const rlqr_opts *opts);
+
+/* Backward Riccati sweep (Theorem main-seq-theorem, eq. value-fn-formulas;
+ * or the associative-scan form of Section "Parallel Algorithm") for the
+ * matrices of `prob`: writes into `ws` the per-stage factors (W_i = P_i
+ * (I + delta P_i)^{-1}, K_i, G_i^{-1}) and writes the certificate to
+ * pivot_pd (device, N+1 bytes).  `ws` (device, >= rlqr_workspace_bytes,
+ * 256-byte aligned) stays valid for rlqr_solve until the next rlqr_factor on
+ * it.  The right-hand side (q, r, c) of `prob` is not read.  status (device
+ * int32[1], may be NULL) receives the instance status. */
+rlqr_status rlqr_factor(const rlqr_problem *prob, const rlqr_opts *opts, void *ws,
+                        size_t ws_bytes, uint8_t *pivot_pd, int32_t *status,
+                        rlqr_stream_t stream);
+
+/* Solve with the factor in `ws` for the right-hand side (q, r, c) of `prob`
+ * (the matrices of `prob` must be those given to rlqr_factor): the
+ * p-recurrence of Corollary p-recurrence backward, then the forward rollout
+ * of eq. recover-x0 / control-law / recover-x with y_k = P_k x_k + p_k.
+ * Writes x, u, y (device).  In RLQR_MIXED mode it then refines against the
+ * FP64 residual up to opts->max_refine times (Section "Residual
+ * Computation").  rel_resid (device double[1], may be NULL in FP64 mode)
+ * receives the final normwise backward error; iters (device int32[1], may be
+ * NULL) the refinement passes taken.  `ws` is also used as solve scratch. */
+rlqr_status rlqr_solve(const rlqr_problem *prob, const rlqr_opts *opts, void *ws,
+                       size_t ws_bytes, double *x, double *u, double *y, double *rel_resid,
+                       int32_t *iters, int32_t *status, rlqr_stream_t stream);
+
+/* FP64 KKT residual of Section "Residual Computation":
+ *   res_q[i] = Q_i x_i + M_i u_i + A_i^T y_{i+1} + q_i - y_i   (i < N)
+ *   res_r[i] = M_i^T x_i + R_i u_i + B_i^T y_{i+1} + r_i       (i < N)
+ *   res_q[N] = Q_N x_N + q_N - y_N
+ *   res_c[0] = c_0 - delta y_0 - x_0
+ *   res_c[i+1] = A_i x_i + B_i u_i + c_{i+1} - delta y_{i+1} - x_{i+1}
+ * res (device, (N+1)*nx + N*nu + (N+1)*nx doubles, laid out res_q | res_r |
+ * res_c) may be NULL.  norms (device double[5]) receives
+ * [||Kz+b||_inf, ||K||_inf, ||z||_inf, ||b||_inf, rel] with
+ * rel = ||Kz+b|| / (||K|| ||z|| + ||b||). */
+rlqr_status rlqr_residual(const rlqr_problem *prob, const double *x, const double *u,
+                          const double *y, double *res, double *norms, rlqr_stream_t stream);
+
+/* ------------------------------------------------------------------ *
+ * Batches of independent instances, possibly of different N, nx, nu.  *
+ * ------------------------------------------------------------------ */
+
+/* Instance b's arrays start at the given element offsets into the pooled
+ * buffers.  All arrays below are DEVICE arrays of length `count`; h_N, h_nx,
+ * h_nu are HOST copies of N, nx, nu used for validation, workspace sizing
+ * and scheduling. */
+typedef struct {
+  int32_t count;
+  const int32_t *h_N, *h_nx, *h_nu;             /* host [count] */
+  const int32_t *N, *nx, *nu;                   /* device [count] */
+  const int64_t *off_Q, *off_M, *off_R, *off_q, *off_r, *off_A, *off_B, *off_c; /* device */
+  const int64_t *off_x, *off_u, *off_y, *off_flag;                               /* device */
+  const double *delta;                                                            /* device */
+  const double *Q, *M, *R, *q, *r, *A, *B, *c; /* pooled device inputs */
+  double *x, *u, *y;                           /* pooled device outputs */
+  uint8_t *pivot_pd;                           /* pooled device certificate */
+} rlqr_batch;
+
+/* Workspace bytes for rlqr_solve_batched (reads only the host dims). */
+size_t rlqr_batched_workspace_bytes(const rlqr_batch *batch, const rlqr_opts *opts);
+
+/* Factor + solve (+ refinement in RLQR_MIXED mode) for every instance of the
+ * batch, stream-ordered, no host synchronisation.  Per instance (device
+ * arrays [count], each may be NULL): status, rel_resid (final normwise
+ * backward error; computed when non-NULL or in MIXED mode), iters
+ * (refinement passes). */
+rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, void *ws,
+                               size_t ws_bytes, int32_t *status, double *rel_resid,
+                               int32_t *iters, rlqr_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RLQR_H_ */
