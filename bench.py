@@ -1,0 +1,331 @@
+"""Benchmark: LQR stage-solves/s at KKT rel-resid <= 1e-9 on B300.
+
+Workload (the configuration the metric is quoted on): a batch of 1024
+dual-regularized LQR instances, n_x = 12, n_u = 4, N = 256, delta log-uniform
+in [1e-8, 1e-2]; 30% with a non-convex Q (two negative eigenvalues, pivots PD),
+5% pivot-indefinite on purpose; synthetic, seeded (paper_2509_16370_b300.inputs).
+
+One step = one rlqr_solve_batched call over the whole batch: FP32 Riccati
+sweep with the FP64 pivot certificate, FP64 KKT residual, FP32 corrections with
+FP64 accumulation until every instance reaches rel-resid <= 1e-9 (device-side
+early exit), i.e. every row of the hot path.  Inputs (0.9 GB) exceed L2, so no
+flush is needed between steps.  The plain FP64 GPU recursion on the same batch
+is timed beside it, and the FP64 CPU oracle is the CPU baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank solves its own copy of the batch (weak
+scaling, no data-path collective); value = all ranks' stage-solves / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="batch of 1024 dual-regularized LQRs, n_x=12, n_u=4, N=256, "
+                         "delta log-uniform [1e-8,1e-2], 30% non-convex Q, 5% pivot-indefinite",
+                instances=1024, N=256, n_x=12, n_u=4, l2="inputs 0.9 GB > L2 (no flush needed)")
+METRIC = "LQR stage-solves/s at KKT rel-resid <=1e-9 (mixed+batched; plain FP64 beside)"
+TOL = 1e-9
+FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12  # 2 DFMA/clk/SM (measured rate), max SM clock
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    dist.init_process_group("nccl")
+    return rank, ws, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu, self.rows, self.proc = gpu, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def kernel_models(n, m, stages):
+    """Algorithmic work per launch of each kernel for the roofline.
+
+    Bytes: the FP64 problem data every pass must read (Q, M, R, q, r, A, B, c:
+    8 (2n^2 + 2nm + m^2 + 2n + m) B per stage) plus the FP64 solution it must
+    write (x, u, y: 8 (2n + m) B) and one flag byte; 3649 B per stage at
+    n = 12, m = 4.  FLOPs of the FP64 residual: 2 (3n^2 + 4nm + m^2) per stage
+    (the products of Section "Residual Computation")."""
+    data = 8 * (2 * n * n + 2 * n * m + m * m + 2 * n + m)
+    out = 8 * (2 * n + m) + 1
+    return {
+        "k_seq_fp32_solve": ("hbm", (data + out) * stages, "GB/s"),
+        "k_seq_fp64_solve": ("hbm", (data + out) * stages, "GB/s"),
+        "k_solve_refine": ("hbm", (data + 2 * out) * stages, "GB/s"),
+        "k_residual_fp64": ("alu", 2.0 * (3 * n * n + 4 * n * m + m * m) * stages, "TFLOP/s"),
+    }
+
+
+def roofline(report, steps, n, m, stages, peaks):
+    k = [(ms, name, cnt) for name, (cnt, ms) in report.items() if name != "k_plan"]
+    if not k:
+        return None
+    ms, name, cnt = max(k)
+    bound, work, unit = kernel_models(n, m, stages).get(name, ("hbm", 0.0, "GB/s"))
+    per_launch_s = ms / cnt / 1e3
+    if bound == "hbm":
+        achieved = work / per_launch_s / 1e9
+        peak = float(peaks.get("hbm_gbs", 6400.0))
+        peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    else:
+        achieved = work / per_launch_s / 1e12
+        peak = FP64_PEAK_TFLOPS
+        peak_src = "derived (148 SM x 2 FP64 FMA/clk x 2032 MHz)"
+    total = sum(v[1] for v in report.values())
+    return {"kernel": name, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
+            "peak_source": peak_src, "unit": unit, "frac": round(achieved / peak, 4),
+            "traffic": None, "launch_ms": round(ms / cnt, 4), "share": round(ms / total, 3)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(bh, min_seconds=10.0):
+    """The FP64 oracle's sequential recursion (OpenMP over instances) on the
+    same batch, repeated until ~min_seconds of CPU work."""
+    import oracle
+    oracle.riccati_batch(bh)  # warm (builds the oracle if needed)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.riccati_batch(bh)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= min_seconds or reps >= 200:
+            break
+    stages = bh.count * bh.N * reps
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": stages / dt, "unit": "stage-solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} x full batch ({bh.count} instances x N={bh.N}), {dt:.1f} s"}
+
+
+def run_reference(args):
+    # The oracle is a host program: under torchrun only rank 0 runs it.
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    from paper_2509_16370_b300 import inputs
+    import oracle
+    bh = inputs.workload2()
+    for _ in range(args.warmup):
+        oracle.riccati_batch(bh)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.riccati_batch(bh)
+    dt = time.perf_counter() - t0
+    value = bh.count * bh.N * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"metric": METRIC, "value": value, "unit": "stage-solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": WORKLOAD, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "stage-solves/s", "cores": cores,
+                             "kind": "oracle", "sample": f"full batch per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": "stage-solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    from paper_2509_16370_b300 import inputs, rlqr
+
+    bh = inputs.workload2()
+    db = rlqr.DeviceBatch.from_uniform(bh)
+    B, N, n, m = bh.count, bh.N, bh.n, bh.m
+    stages = B * N
+    stream = torch.cuda.current_stream()
+
+    def setup(prec):
+        opts = rlqr.make_opts(prec, tol=TOL, max_refine=3)
+        ws = rlqr.alloc_workspace(rlqr.rlqr_batched_workspace_bytes(db, opts))
+        st = torch.zeros(B, dtype=torch.int32, device="cuda")
+        rel = torch.zeros(B, dtype=torch.float64, device="cuda")
+        it = torch.zeros(B, dtype=torch.int32, device="cuda")
+        return opts, ws, st, rel, it
+
+    def timed(prec, steps, warmup, instrument=False):
+        opts, ws, st, rel, it = setup(prec)
+        for _ in range(warmup):
+            rlqr.rlqr_solve_batched(db, opts, ws, st, rel, it)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if instrument:
+            rlqr.rlqr_instrument(True)
+        e0.record(stream)
+        for _ in range(steps):
+            rlqr.rlqr_solve_batched(db, opts, ws, st, rel, it)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        report = rlqr.rlqr_instrument_report() if instrument else {}
+        if instrument:
+            rlqr.rlqr_instrument(False)
+        if world > 1:
+            torch.distributed.barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        stv = st.cpu().numpy()
+        relv = rel.cpu().numpy()
+        ok = bool(np.all(relv <= TOL) and np.all((stv == 0) | (stv == 1)))
+        return ms, report, dict(max_rel=float(relv.max()), ok=ok, iters=int(it.max().item()),
+                                not_pd=int((stv == 1).sum()))
+
+    with ClockSampler(local) as clk:
+        ms_mixed, report, chk_mixed = timed(rlqr.RLQR_MIXED, args.steps, args.warmup, True)
+    ms_fp64, _, chk_fp64 = timed(rlqr.RLQR_FP64, max(3, args.steps // 4), args.warmup)
+
+    # end to end through the C ABI from pinned host buffers
+    opts, ws, st, rel, it = setup(rlqr.RLQR_MIXED)
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(bh, k)).reshape(-1)).pin_memory()
+            for k in ("Q", "M", "R", "q", "r", "A", "B", "c")}
+    hx = torch.empty(db.x.numel(), dtype=torch.float64).pin_memory()
+    hu = torch.empty(db.u.numel(), dtype=torch.float64).pin_memory()
+    hy = torch.empty(db.y.numel(), dtype=torch.float64).pin_memory()
+    hf = torch.empty(db.pivot_pd.numel(), dtype=torch.uint8).pin_memory()
+    hrel = torch.empty(B, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = sum(t.numel() * t.element_size() for t in (hx, hu, hy, hf, hrel))
+
+    def e2e_step():
+        for k, t in host.items():
+            db.bufs[k].copy_(t, non_blocking=True)
+        rlqr.rlqr_solve_batched(db, opts, ws, st, rel, it)
+        hx.copy_(db.x, non_blocking=True)
+        hu.copy_(db.u, non_blocking=True)
+        hy.copy_(db.y, non_blocking=True)
+        hf.copy_(db.pivot_pd, non_blocking=True)
+        hrel.copy_(rel, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([ms_e2e], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+
+    if rank != 0:
+        return
+    value = world * stages / (ms_mixed / 1e3)
+    fp64_value = world * stages / (ms_fp64 / 1e3)
+    launches = sum(c for c, _ in report.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": "stage-solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64 (FP32 sweep; FP64 certificate, residual, correction)",
+        "data": "synthetic", "config": dict(WORKLOAD, parallelism=f"replicas x{world}",
+                                              precision="mixed", max_refine=3, tol=TOL),
+        "roofline": roofline(report, args.steps, n, m, stages, load_peaks()),
+        "kernels": {k: {"launches": c, "ms_total": round(t, 4)} for k, (c, t) in report.items()},
+        "gpu_launches": launches,
+        "accuracy": {"max_rel_resid": chk_mixed["max_rel"], "all_le_tol": chk_mixed["ok"],
+                     "max_refine_iters": chk_mixed["iters"], "not_pd_instances": chk_mixed["not_pd"]},
+        "fp64_plain": {"value": fp64_value, "ms_per_step": ms_fp64,
+                       "max_rel_resid": chk_fp64["max_rel"], "all_le_tol": chk_fp64["ok"]},
+        "speedup_vs_fp64_plain": value / fp64_value,
+        "e2e": {"value": world * stages / (ms_e2e / 1e3), "unit": "stage-solves/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(bh, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

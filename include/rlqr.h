@@ -23,7 +23,8 @@
  *     matrices, stage-major and contiguous:
  *       Q (N+1)*nx*nx   M N*nx*nu   R N*nu*nu   q (N+1)*nx   r N*nu
  *       A N*nx*nx       B N*nx*nu   c (N+1)*nx
- *     Q_i and R_i are read as (X + X^T)/2.  c_0 is the initial-state term,
+ *     Q_i and R_i must be symmetric: only their upper triangle (row <= column)
+ *     is read.  c_0 is the initial-state term,
  *     c_{i+1} the offset of the dynamics x_{i+1} = A_i x_i + B_i u_i + c_{i+1}.
  *   - Outputs x (N+1)*nx, u N*nu, y (N+1)*nx (FP64) and pivot_pd (N+1 bytes)
  *     are DEVICE pointers.  pivot_pd[i] bit0 = (I + delta P_i) is PD,
@@ -182,6 +183,23 @@ size_t rlqr_batched_workspace_bytes(const rlqr_batch *batch, const rlqr_opts *op
 rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, void *ws,
                                size_t ws_bytes, int32_t *status, double *rel_resid,
                                int32_t *iters, rlqr_stream_t stream);
+
+/* ------------------------------------------------------------------ *
+ * Instrumentation (no counterpart in the paper): per-kernel timing.    *
+ * ------------------------------------------------------------------ */
+
+/* enable != 0: from now on every kernel the library launches is bracketed by
+ * a pair of CUDA events recorded on the launch stream (at most 8192 launches
+ * are kept; later ones are counted but not timed).  enable == 0 stops it.
+ * Either call discards the launches recorded so far.  Events are created on
+ * first use (no device memory is allocated).  Not thread-safe. */
+rlqr_status rlqr_instrument(int enable);
+
+/* Waits for the recorded events and reports, per kernel name, the number of
+ * launches and their summed device time in milliseconds.  names[i] receives
+ * a pointer to a static string.  Returns the number of distinct kernels
+ * (entries beyond max are dropped), or -1 on a CUDA error. */
+int rlqr_instrument_report(int max, const char **names, int64_t *launches, double *ms);
 
 #ifdef __cplusplus
 }

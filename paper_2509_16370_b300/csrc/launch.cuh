@@ -1,0 +1,65 @@
+// launch.cuh -- kernel selection shared by the translation units of the
+// library (the FP32 and FP64 kernel instantiations compile separately).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace rlqr {
+
+// ---- optional per-kernel timing (rlqr_instrument)
+struct Instr {
+  bool on = false;
+  int n = 0;                     // launches recorded (timed ones: min(n, kMax))
+  static constexpr int kMax = 8192;
+  cudaEvent_t ev[2 * kMax];
+  const char *name[kMax];
+  int created = 0;               // events created so far
+};
+extern Instr g_instr;
+
+struct LaunchScope {             // brackets one kernel launch
+  int slot = -1;
+  cudaStream_t s;
+  LaunchScope(const char *name, cudaStream_t st) : s(st) {
+    if (!g_instr.on) return;
+    int i = g_instr.n++;
+    if (i >= Instr::kMax) return;
+    while (g_instr.created < 2 * (i + 1)) {
+      if (cudaEventCreate(&g_instr.ev[g_instr.created]) != cudaSuccess) return;
+      ++g_instr.created;
+    }
+    g_instr.name[i] = name;
+    slot = i;
+    cudaEventRecord(g_instr.ev[2 * i], s);
+  }
+  ~LaunchScope() {
+    if (slot >= 0) cudaEventRecord(g_instr.ev[2 * slot + 1], s);
+  }
+};
+
+// Dimension buckets: the smallest (NM, MM) >= (n, m) selects the kernel
+// instantiation.  Sizes above the last bucket are rejected.
+constexpr int kMaxN = 48, kMaxM = 16;
+
+inline int bucket_of(int n, int m) {
+  if (n <= 8 && m <= 4) return 0;
+  if (n <= 16 && m <= 8) return 1;
+  if (n <= 32 && m <= 16) return 2;
+  if (n <= 48 && m <= 16) return 3;
+  return -1;
+}
+
+template <typename F>
+inline cudaError_t set_smem(F *kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Defined in launch_fp32.cu / launch_fp64.cu (explicit instantiations).
+template <typename T, bool SOLVE>
+cudaError_t launch_seq(int n, int m, bool uniform, const BatchArgs &a, cudaStream_t s);
+template <typename T, bool FROM_RES>
+cudaError_t launch_solve(int n, int m, bool uniform, const BatchArgs &a, cudaStream_t s);
+
+}  // namespace rlqr

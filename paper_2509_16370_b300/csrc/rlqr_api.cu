@@ -1,0 +1,314 @@
+// rlqr_api.cu -- C ABI of the B300 dual-regularized LQR library (include/rlqr.h).
+//
+// Host side: argument validation, workspace layout, kernel selection by the
+// instance dimensions, and the launch sequences of the factor / solve /
+// residual / batched entry points.  Every step of the solve runs in the
+// kernels of seq.cuh and refine.cuh; nothing here touches problem data.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "launch.cuh"
+#include "residual.cuh"
+
+namespace rlqr {
+
+Instr g_instr;
+
+// One warp per stage; as many warps per CTA (<= 8) as the dense stage blocks
+// of the largest instance fit in shared memory.
+static cudaError_t launch_residual(const BatchArgs &a, int rs_max, int store, double *res_out,
+                                   double *norms_out, int recompute, int standalone,
+                                   cudaStream_t s, int cert_g = 0, int do_residual = 1) {
+  const size_t per_warp = residual_warp_bytes(rs_max);
+  int warps = (int)std::min<size_t>(8, (200u * 1024u) / per_warp);
+  warps = std::max(warps, 1);
+  const size_t bytes = per_warp * warps;
+  cudaError_t e = set_smem(k_residual, bytes);
+  if (e != cudaSuccess) return e;
+  LaunchScope ls(do_residual ? "k_residual_fp64" : "k_cert_fp64", s);
+  k_residual<<<a.count, 32 * warps, bytes, s>>>(a, store, res_out, norms_out, recompute,
+                                               standalone, rs_max, cert_g, do_residual);
+  return cudaGetLastError();
+}
+
+// Per-instance workspace offsets of a batch: exclusive prefix sum of
+// ws_layout(...).total, after the header that holds the offsets themselves.
+__global__ void k_plan(int count, const int32_t *dN, const int32_t *dn, const int32_t *dm,
+                       int tsize, int64_t *ows) {
+  __shared__ int64_t part[1024];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int per = (count + T - 1) / T;
+  const int lo = min(count, t * per), hi = min(count, lo + per);
+  int64_t s = 0;
+  for (int b = lo; b < hi; ++b) s += (int64_t)ws_layout(dN[b], dn[b], dm[b], tsize).total;
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int64_t acc = (int64_t)align_up((size_t)count * sizeof(int64_t));
+    for (int i = 0; i < T; ++i) {
+      int64_t v = part[i];
+      part[i] = acc;
+      acc += v;
+    }
+  }
+  __syncthreads();
+  int64_t acc = part[t];
+  for (int b = lo; b < hi; ++b) {
+    ows[b] = acc;
+    acc += (int64_t)ws_layout(dN[b], dn[b], dm[b], tsize).total;
+  }
+}
+
+static bool valid_opts(const rlqr_opts *o) {
+  if (!o) return false;
+  if (o->prec != RLQR_FP64 && o->prec != RLQR_MIXED) return false;
+  if (o->algo != RLQR_ALGO_AUTO && o->algo != RLQR_ALGO_SEQ) return false;
+  if (o->max_refine < 0 || o->max_refine > 64) return false;
+  if (!(o->tol > 0.0) || !std::isfinite(o->tol)) return false;
+  return true;
+}
+
+static bool valid_dims(int N, int n, int m) {
+  return N >= 1 && n >= 1 && m >= 1 && bucket_of(n, m) >= 0 && N < (1 << 28);
+}
+
+static bool valid_problem(const rlqr_problem *p) {
+  if (!p || !valid_dims(p->N, p->nx, p->nu)) return false;
+  if (!(p->delta >= 0.0) || !std::isfinite(p->delta)) return false;
+  return p->Q && p->M && p->R && p->q && p->r && p->A && p->B && p->c;
+}
+
+static BatchArgs single_args(const rlqr_problem *p, const rlqr_opts *o, void *ws) {
+  BatchArgs a{};
+  a.count = 1;
+  a.single = 1;
+  a.N = p->N;
+  a.n = p->nx;
+  a.m = p->nu;
+  a.delta = p->delta;
+  a.Q = p->Q; a.M = p->M; a.R = p->R; a.q = p->q; a.r = p->r; a.A = p->A; a.B = p->B; a.c = p->c;
+  a.ws = static_cast<char *>(ws);
+  a.tsize = (o && o->prec == RLQR_MIXED) ? 4 : 8;
+  a.tol = o ? o->tol : 1e-9;
+  a.max_refine = o ? o->max_refine : 0;
+  return a;
+}
+
+static rlqr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RLQR_OK : RLQR_ERR_CUDA; }
+
+}  // namespace rlqr
+
+using namespace rlqr;
+
+extern "C" {
+
+rlqr_opts rlqr_default_opts(void) {
+  rlqr_opts o;
+  o.max_refine = 3;
+  o.tol = 1e-9;
+  o.algo = RLQR_ALGO_AUTO;
+  o.prec = RLQR_FP64;
+  return o;
+}
+
+const char *rlqr_version(void) { return "rlqr-b300 0.1 (sm_103a)"; }
+
+const char *rlqr_status_string(rlqr_status s) {
+  switch (s) {
+    case RLQR_OK: return "ok";
+    case RLQR_NOT_PD: return "solved; a pivot is not positive-definite";
+    case RLQR_ERR_ARG: return "invalid argument";
+    case RLQR_ERR_SINGULAR: return "zero or non-finite pivot";
+    case RLQR_ERR_NOT_CONVERGED: return "refinement did not reach the tolerance";
+    case RLQR_ERR_TIMEOUT: return "device wait timed out";
+    case RLQR_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case RLQR_ERR_CUDA: return "CUDA error";
+  }
+  return "unknown status";
+}
+
+size_t rlqr_workspace_bytes(int32_t N, int32_t nx, int32_t nu, const rlqr_opts *opts) {
+  if (!valid_dims(N, nx, nu) || !valid_opts(opts)) return 0;
+  int tsize = opts->prec == RLQR_MIXED ? 4 : 8;
+  return ws_layout(N, nx, nu, tsize).total;
+}
+
+rlqr_status rlqr_factor(const rlqr_problem *prob, const rlqr_opts *opts, void *ws,
+                        size_t ws_bytes, uint8_t *pivot_pd, int32_t *status,
+                        rlqr_stream_t stream) {
+  if (!valid_problem(prob) || !valid_opts(opts) || !pivot_pd) return RLQR_ERR_ARG;
+  size_t need = rlqr_workspace_bytes(prob->N, prob->nx, prob->nu, opts);
+  if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
+    return RLQR_ERR_WORKSPACE;
+  BatchArgs a = single_args(prob, opts, ws);
+  a.flags = pivot_pd;
+  a.status = status;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int n = prob->nx, m = prob->nu;
+  if (opts->prec == RLQR_MIXED) {
+    cudaError_t e = launch_seq<float, false>(n, m, true, a, s);
+    if (e != cudaSuccess) return RLQR_ERR_CUDA;
+    // FP64 certificate of the control pivots stored by the FP32 sweep
+    return cuda_status(launch_residual(a, 2 * n + m, 0, nullptr, nullptr, 0, 0, s, 1, 0));
+  }
+  return cuda_status(launch_seq<double, false>(n, m, true, a, s));
+}
+
+rlqr_status rlqr_solve(const rlqr_problem *prob, const rlqr_opts *opts, void *ws,
+                       size_t ws_bytes, double *x, double *u, double *y, double *rel_resid,
+                       int32_t *iters, int32_t *status, rlqr_stream_t stream) {
+  if (!valid_problem(prob) || !valid_opts(opts) || !x || !u || !y) return RLQR_ERR_ARG;
+  size_t need = rlqr_workspace_bytes(prob->N, prob->nx, prob->nu, opts);
+  if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
+    return RLQR_ERR_WORKSPACE;
+  BatchArgs a = single_args(prob, opts, ws);
+  a.x = x;
+  a.u = u;
+  a.y = y;
+  a.rel = rel_resid;
+  a.iters = iters;
+  a.status = status;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int n = prob->nx, m = prob->nu;
+  const bool mixed = opts->prec == RLQR_MIXED;
+  cudaError_t e = mixed ? launch_solve<float, false>(n, m, true, a, s)
+                        : launch_solve<double, false>(n, m, true, a, s);
+  if (e != cudaSuccess) return RLQR_ERR_CUDA;
+  if (mixed || rel_resid) {
+    e = launch_residual(a, 2 * prob->nx + prob->nu, mixed ? 1 : 0, nullptr, nullptr, 1, 0, s);
+    if (e != cudaSuccess) return RLQR_ERR_CUDA;
+  }
+  if (mixed)
+    for (int it = 0; it < opts->max_refine; ++it) {
+      e = launch_solve<float, true>(n, m, true, a, s);
+      if (e != cudaSuccess) return RLQR_ERR_CUDA;
+    }
+  return RLQR_OK;
+}
+
+rlqr_status rlqr_residual(const rlqr_problem *prob, const double *x, const double *u,
+                          const double *y, double *res, double *norms, rlqr_stream_t stream) {
+  if (!valid_problem(prob) || !x || !u || !y || !norms) return RLQR_ERR_ARG;
+  BatchArgs a = single_args(prob, nullptr, nullptr);
+  a.x = const_cast<double *>(x);
+  a.u = const_cast<double *>(u);
+  a.y = const_cast<double *>(y);
+  a.tol = 1e-9;
+  return cuda_status(launch_residual(a, 2 * prob->nx + prob->nu, 0, res, norms, 1, 1,
+                                     reinterpret_cast<cudaStream_t>(stream)));
+}
+
+size_t rlqr_batched_workspace_bytes(const rlqr_batch *batch, const rlqr_opts *opts) {
+  if (!batch || batch->count < 1 || !batch->h_N || !batch->h_nx || !batch->h_nu ||
+      !valid_opts(opts))
+    return 0;
+  int tsize = opts->prec == RLQR_MIXED ? 4 : 8;
+  size_t tot = align_up((size_t)batch->count * sizeof(int64_t));
+  for (int b = 0; b < batch->count; ++b) {
+    if (!valid_dims(batch->h_N[b], batch->h_nx[b], batch->h_nu[b])) return 0;
+    tot += ws_layout(batch->h_N[b], batch->h_nx[b], batch->h_nu[b], tsize).total;
+  }
+  return tot;
+}
+
+rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, void *ws,
+                               size_t ws_bytes, int32_t *status, double *rel_resid,
+                               int32_t *iters, rlqr_stream_t stream) {
+  if (!batch || batch->count < 1 || !valid_opts(opts)) return RLQR_ERR_ARG;
+  const rlqr_batch &B = *batch;
+  if (!B.N || !B.nx || !B.nu || !B.delta || !B.off_Q || !B.off_M || !B.off_R || !B.off_q ||
+      !B.off_r || !B.off_A || !B.off_B || !B.off_c || !B.off_x || !B.off_u || !B.off_y ||
+      !B.off_flag || !B.Q || !B.M || !B.R || !B.q || !B.r || !B.A || !B.B || !B.c || !B.x ||
+      !B.u || !B.y || !B.pivot_pd)
+    return RLQR_ERR_ARG;
+  size_t need = rlqr_batched_workspace_bytes(batch, opts);
+  if (need == 0) return RLQR_ERR_ARG;
+  if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
+    return RLQR_ERR_WORKSPACE;
+  // one kernel instantiation covers the whole batch: exact dimensions when
+  // all instances share them, else the bucket of the largest
+  int nmax = 0, mmax = 0, rs_max = 0;
+  bool uniform = true;
+  for (int b = 0; b < B.count; ++b) {
+    nmax = std::max(nmax, B.h_nx[b]);
+    mmax = std::max(mmax, B.h_nu[b]);
+    rs_max = std::max(rs_max, 2 * B.h_nx[b] + B.h_nu[b]);
+    uniform = uniform && B.h_nx[b] == B.h_nx[0] && B.h_nu[b] == B.h_nu[0];
+  }
+  const bool mixed = opts->prec == RLQR_MIXED;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  BatchArgs a{};
+  a.count = B.count;
+  a.single = 0;
+  a.dN = B.N; a.dn = B.nx; a.dm = B.nu; a.ddelta = B.delta;
+  a.oQ = B.off_Q; a.oM = B.off_M; a.oR = B.off_R; a.oq = B.off_q; a.or_ = B.off_r;
+  a.oA = B.off_A; a.oB = B.off_B; a.oc = B.off_c; a.ox = B.off_x; a.ou = B.off_u;
+  a.oy = B.off_y; a.of = B.off_flag;
+  a.Q = B.Q; a.M = B.M; a.R = B.R; a.q = B.q; a.r = B.r; a.A = B.A; a.B = B.B; a.c = B.c;
+  a.x = B.x; a.u = B.u; a.y = B.y; a.flags = B.pivot_pd;
+  a.ws = static_cast<char *>(ws);
+  a.ows = reinterpret_cast<const int64_t *>(ws);
+  a.tsize = mixed ? 4 : 8;
+  a.status = status;
+  a.rel = rel_resid;
+  a.iters = iters;
+  a.tol = opts->tol;
+  a.max_refine = opts->max_refine;
+  a.want_norms = (mixed || rel_resid) ? 1 : 0;
+  cudaError_t e;
+  {
+    LaunchScope ls("k_plan", s);
+    k_plan<<<1, 1024, 0, s>>>(B.count, B.N, B.nx, B.nu, a.tsize,
+                              reinterpret_cast<int64_t *>(ws));
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return RLQR_ERR_CUDA;
+  e = mixed ? launch_seq<float, true>(nmax, mmax, uniform, a, s)
+            : launch_seq<double, true>(nmax, mmax, uniform, a, s);
+  if (e != cudaSuccess) return RLQR_ERR_CUDA;
+  if (mixed || rel_resid) {
+    e = launch_residual(a, rs_max, mixed ? 1 : 0, nullptr, nullptr, 0, 0, s, mixed ? 1 : 0, 1);
+    if (e != cudaSuccess) return RLQR_ERR_CUDA;
+  }
+  if (mixed)
+    for (int it = 0; it < opts->max_refine; ++it) {
+      e = launch_solve<float, true>(nmax, mmax, uniform, a, s);
+      if (e != cudaSuccess) return RLQR_ERR_CUDA;
+    }
+  return RLQR_OK;
+}
+
+rlqr_status rlqr_instrument(int enable) {
+  g_instr.on = enable != 0;
+  g_instr.n = 0;
+  return RLQR_OK;
+}
+
+int rlqr_instrument_report(int max, const char **names, int64_t *launches, double *ms) {
+  const int timed = std::min(g_instr.n, Instr::kMax);
+  int k = 0;
+  for (int i = 0; i < timed; ++i) {
+    if (cudaEventSynchronize(g_instr.ev[2 * i + 1]) != cudaSuccess) return -1;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, g_instr.ev[2 * i], g_instr.ev[2 * i + 1]) != cudaSuccess)
+      return -1;
+    int j = 0;
+    while (j < k && std::strcmp(names[j], g_instr.name[i]) != 0) ++j;
+    if (j == k) {
+      if (k >= max) continue;
+      names[k] = g_instr.name[i];
+      launches[k] = 0;
+      ms[k] = 0.0;
+      ++k;
+    }
+    launches[j] += 1;
+    ms[j] += t;
+  }
+  return k;
+}
+
+}  // extern "C"

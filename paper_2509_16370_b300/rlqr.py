@@ -1,0 +1,307 @@
+"""Thin Python binding of the C ABI in include/rlqr.h (ctypes).
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels of
+librlqr.so.  PyTorch provides device memory and streams.  The functions keep
+the C names (rlqr_factor, rlqr_solve, rlqr_residual, rlqr_solve_batched, ...)
+and take torch tensors where the C ABI takes device pointers.
+
+The library is loaded from paper_2509_16370_b300/_lib/librlqr.so; if it is
+missing this module raises at import time (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "librlqr.so")
+
+RLQR_OK, RLQR_NOT_PD, RLQR_ERR_ARG, RLQR_ERR_SINGULAR = 0, 1, 2, 3
+RLQR_ERR_NOT_CONVERGED, RLQR_ERR_TIMEOUT, RLQR_ERR_WORKSPACE, RLQR_ERR_CUDA = 4, 5, 6, 7
+RLQR_ALGO_AUTO, RLQR_ALGO_SEQ, RLQR_ALGO_SCAN = 0, 1, 2
+RLQR_FP64, RLQR_MIXED = 0, 1
+
+EXPORTED = ("rlqr_default_opts", "rlqr_version", "rlqr_status_string", "rlqr_workspace_bytes",
+            "rlqr_factor", "rlqr_solve", "rlqr_residual", "rlqr_batched_workspace_bytes",
+            "rlqr_solve_batched", "rlqr_instrument", "rlqr_instrument_report")
+
+_dp = ctypes.c_void_p
+
+
+class rlqr_problem(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("nx", ctypes.c_int32), ("nu", ctypes.c_int32),
+                ("Q", _dp), ("M", _dp), ("R", _dp), ("q", _dp), ("r", _dp), ("A", _dp),
+                ("B", _dp), ("c", _dp), ("delta", ctypes.c_double)]
+
+
+class rlqr_opts(ctypes.Structure):
+    _fields_ = [("max_refine", ctypes.c_int32), ("tol", ctypes.c_double), ("algo", ctypes.c_int),
+                ("prec", ctypes.c_int)]
+
+
+class rlqr_batch(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("h_N", _dp), ("h_nx", _dp), ("h_nu", _dp),
+                ("N", _dp), ("nx", _dp), ("nu", _dp)] + [
+        (f"off_{k}", _dp) for k in ("Q", "M", "R", "q", "r", "A", "B", "c", "x", "u", "y",
+                                    "flag")] + [
+        ("delta", _dp)] + [(k, _dp) for k in ("Q", "M", "R", "q", "r", "A", "B", "c", "x", "u",
+                                              "y", "pivot_pd")]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2509_16370_b300.csrc.build` (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    st, sz = ctypes.c_int, ctypes.c_size_t
+    P = ctypes.POINTER
+    lib.rlqr_default_opts.restype = rlqr_opts
+    lib.rlqr_version.restype = ctypes.c_char_p
+    lib.rlqr_status_string.restype = ctypes.c_char_p
+    lib.rlqr_status_string.argtypes = [st]
+    lib.rlqr_workspace_bytes.restype = sz
+    lib.rlqr_workspace_bytes.argtypes = [ctypes.c_int32] * 3 + [P(rlqr_opts)]
+    lib.rlqr_factor.restype = st
+    lib.rlqr_factor.argtypes = [P(rlqr_problem), P(rlqr_opts), _dp, sz, _dp, _dp, _dp]
+    lib.rlqr_solve.restype = st
+    lib.rlqr_solve.argtypes = [P(rlqr_problem), P(rlqr_opts), _dp, sz, _dp, _dp, _dp, _dp, _dp,
+                               _dp, _dp]
+    lib.rlqr_residual.restype = st
+    lib.rlqr_residual.argtypes = [P(rlqr_problem), _dp, _dp, _dp, _dp, _dp, _dp]
+    lib.rlqr_batched_workspace_bytes.restype = sz
+    lib.rlqr_batched_workspace_bytes.argtypes = [P(rlqr_batch), P(rlqr_opts)]
+    lib.rlqr_solve_batched.restype = st
+    lib.rlqr_solve_batched.argtypes = [P(rlqr_batch), P(rlqr_opts), _dp, sz, _dp, _dp, _dp, _dp]
+    lib.rlqr_instrument.restype = st
+    lib.rlqr_instrument.argtypes = [ctypes.c_int]
+    lib.rlqr_instrument_report.restype = ctypes.c_int
+    lib.rlqr_instrument_report.argtypes = [ctypes.c_int, P(ctypes.c_char_p),
+                                           P(ctypes.c_int64), P(ctypes.c_double)]
+    return lib
+
+
+lib = _load()
+
+
+class RlqrError(RuntimeError):
+    pass
+
+
+def _check(code: int, what: str):
+    if code != RLQR_OK:
+        raise RlqrError(f"{what}: {lib.rlqr_status_string(code).decode()} ({code})")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_contiguous(), "tensors passed to librlqr must be contiguous"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def version() -> str:
+    return lib.rlqr_version().decode()
+
+
+def make_opts(prec=RLQR_FP64, algo=RLQR_ALGO_AUTO, tol=1e-9, max_refine=3) -> rlqr_opts:
+    o = lib.rlqr_default_opts()
+    o.prec, o.algo, o.tol, o.max_refine = int(prec), int(algo), float(tol), int(max_refine)
+    return o
+
+
+def rlqr_instrument(enable: bool):
+    _check(lib.rlqr_instrument(1 if enable else 0), "rlqr_instrument")
+
+
+def rlqr_instrument_report(max_kernels: int = 32) -> dict:
+    """{kernel name: (launches, total ms)} of the launches since rlqr_instrument."""
+    names = (ctypes.c_char_p * max_kernels)()
+    launches = (ctypes.c_int64 * max_kernels)()
+    ms = (ctypes.c_double * max_kernels)()
+    k = lib.rlqr_instrument_report(max_kernels, names, launches, ms)
+    if k < 0:
+        raise RlqrError("rlqr_instrument_report: CUDA error")
+    return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(k)}
+
+
+# ------------------------------------------------------------ single instance
+
+@dataclass
+class DeviceProblem:
+    """One instance's FP64 arrays on the device (stage-major, contiguous)."""
+    N: int
+    n: int
+    m: int
+    Q: torch.Tensor
+    M: torch.Tensor
+    R: torch.Tensor
+    q: torch.Tensor
+    r: torch.Tensor
+    A: torch.Tensor
+    B: torch.Tensor
+    c: torch.Tensor
+    delta: float
+
+    @staticmethod
+    def from_host(p, device="cuda") -> "DeviceProblem":
+        t = {k: torch.from_numpy(np.ascontiguousarray(getattr(p, k), dtype=np.float64)).to(device)
+             for k in ("Q", "M", "R", "q", "r", "A", "B", "c")}
+        return DeviceProblem(p.N, p.n, p.m, delta=float(p.delta), **t)
+
+    def c_struct(self) -> rlqr_problem:
+        s = rlqr_problem()
+        s.N, s.nx, s.nu, s.delta = self.N, self.n, self.m, float(self.delta)
+        for k in ("Q", "M", "R", "q", "r", "A", "B", "c"):
+            setattr(s, k, _ptr(getattr(self, k)).value)
+        return s
+
+
+def rlqr_workspace_bytes(N: int, nx: int, nu: int, opts: rlqr_opts) -> int:
+    return int(lib.rlqr_workspace_bytes(N, nx, nu, ctypes.byref(opts)))
+
+
+def alloc_workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    """Caller-owned workspace (torch allocations are 256-byte aligned)."""
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def rlqr_factor(prob: DeviceProblem, opts: rlqr_opts, ws: torch.Tensor, pivot_pd: torch.Tensor,
+                status: torch.Tensor | None = None, stream=None):
+    ps = prob.c_struct()
+    _check(lib.rlqr_factor(ctypes.byref(ps), ctypes.byref(opts), _ptr(ws), ws.numel(),
+                           _ptr(pivot_pd), _ptr(status), _stream(stream)), "rlqr_factor")
+
+
+def rlqr_solve(prob: DeviceProblem, opts: rlqr_opts, ws: torch.Tensor, x, u, y, rel_resid=None,
+               iters=None, status=None, stream=None):
+    ps = prob.c_struct()
+    _check(lib.rlqr_solve(ctypes.byref(ps), ctypes.byref(opts), _ptr(ws), ws.numel(), _ptr(x),
+                          _ptr(u), _ptr(y), _ptr(rel_resid), _ptr(iters), _ptr(status),
+                          _stream(stream)), "rlqr_solve")
+
+
+def rlqr_residual(prob: DeviceProblem, x, u, y, res=None, norms=None, stream=None):
+    ps = prob.c_struct()
+    _check(lib.rlqr_residual(ctypes.byref(ps), _ptr(x), _ptr(u), _ptr(y), _ptr(res), _ptr(norms),
+                             _stream(stream)), "rlqr_residual")
+
+
+# ------------------------------------------------------------------- batches
+
+@dataclass
+class DeviceBatch:
+    """Pooled device buffers of a batch plus the per-instance offset arrays.
+
+    Works for uniform and ragged batches alike.  Instance b's arrays start at
+    element offsets off_*[b] of the pooled buffers."""
+    count: int
+    h_dims: np.ndarray          # (count, 3) int32 host copy of (N, nx, nu)
+    dims: torch.Tensor          # (3, count) int32 device
+    offs: dict                  # name -> int64 device tensor [count]
+    delta: torch.Tensor         # float64 [count]
+    bufs: dict                  # name -> pooled float64 device tensor
+    x: torch.Tensor
+    u: torch.Tensor
+    y: torch.Tensor
+    pivot_pd: torch.Tensor
+    _h_cols: tuple = ()
+    _struct: rlqr_batch | None = None
+
+    @staticmethod
+    def from_problems(probs, device="cuda") -> "DeviceBatch":
+        dims = np.array([[p.N, p.n, p.m] for p in probs], dtype=np.int32)
+        sizes = {
+            "Q": [(p.N + 1) * p.n * p.n for p in probs], "M": [p.N * p.n * p.m for p in probs],
+            "R": [p.N * p.m * p.m for p in probs], "q": [(p.N + 1) * p.n for p in probs],
+            "r": [p.N * p.m for p in probs], "A": [p.N * p.n * p.n for p in probs],
+            "B": [p.N * p.n * p.m for p in probs], "c": [(p.N + 1) * p.n for p in probs],
+            "x": [(p.N + 1) * p.n for p in probs], "u": [p.N * p.m for p in probs],
+            "y": [(p.N + 1) * p.n for p in probs], "flag": [p.N + 1 for p in probs]}
+        offs_h = {k: np.concatenate([[0], np.cumsum(v)[:-1]]).astype(np.int64)
+                  for k, v in sizes.items()}
+        bufs = {}
+        for k in ("Q", "M", "R", "q", "r", "A", "B", "c"):
+            flat = np.concatenate([np.ascontiguousarray(getattr(p, k), np.float64).ravel()
+                                   for p in probs])
+            bufs[k] = torch.from_numpy(flat).to(device)
+        return DeviceBatch._finish(len(probs), dims, offs_h, sizes, bufs,
+                                   np.array([p.delta for p in probs], np.float64), device)
+
+    @staticmethod
+    def from_uniform(batch, device="cuda", pinned_host=None) -> "DeviceBatch":
+        """A uniform host batch (stacked arrays) without per-instance copies."""
+        B, N, n, m = batch.count, batch.N, batch.n, batch.m
+        dims = np.tile(np.array([[N, n, m]], np.int32), (B, 1))
+        per = {"Q": (N + 1) * n * n, "M": N * n * m, "R": N * m * m, "q": (N + 1) * n,
+               "r": N * m, "A": N * n * n, "B": N * n * m, "c": (N + 1) * n, "x": (N + 1) * n,
+               "u": N * m, "y": (N + 1) * n, "flag": N + 1}
+        offs_h = {k: (np.arange(B, dtype=np.int64) * v) for k, v in per.items()}
+        sizes = {k: [v] * B for k, v in per.items()}
+        bufs = {k: torch.from_numpy(np.ascontiguousarray(getattr(batch, k), np.float64).reshape(-1))
+                .to(device) for k in ("Q", "M", "R", "q", "r", "A", "B", "c")}
+        return DeviceBatch._finish(B, dims, offs_h, sizes, bufs,
+                                   np.asarray(batch.delta, np.float64), device)
+
+    @staticmethod
+    def _finish(count, dims, offs_h, sizes, bufs, delta, device):
+        offs = {k: torch.from_numpy(v).to(device) for k, v in offs_h.items()}
+        tot = {k: int(sum(v)) for k, v in sizes.items()}
+        x = torch.zeros(tot["x"], dtype=torch.float64, device=device)
+        u = torch.zeros(tot["u"], dtype=torch.float64, device=device)
+        y = torch.zeros(tot["y"], dtype=torch.float64, device=device)
+        flags = torch.zeros(tot["flag"], dtype=torch.uint8, device=device)
+        hcols = tuple(np.ascontiguousarray(dims[:, i]) for i in range(3))
+        db = DeviceBatch(count, dims, torch.from_numpy(np.ascontiguousarray(dims.T)).to(device),
+                         offs, torch.from_numpy(delta).to(device), bufs, x, u, y, flags, hcols)
+        db._offs_h = offs_h
+        return db
+
+    def c_struct(self) -> rlqr_batch:
+        s = rlqr_batch()
+        s.count = self.count
+        s.h_N, s.h_nx, s.h_nu = (c.ctypes.data for c in self._h_cols)
+        s.N = self.dims[0].data_ptr()
+        s.nx = self.dims[1].data_ptr()
+        s.nu = self.dims[2].data_ptr()
+        for k, t in self.offs.items():
+            setattr(s, f"off_{k}", t.data_ptr())
+        s.delta = self.delta.data_ptr()
+        for k, t in self.bufs.items():
+            setattr(s, k, t.data_ptr())
+        s.x, s.u, s.y, s.pivot_pd = (self.x.data_ptr(), self.u.data_ptr(), self.y.data_ptr(),
+                                     self.pivot_pd.data_ptr())
+        self._struct = s
+        return s
+
+    def instance_view(self, b: int):
+        """(x, u, y, flags) host arrays of instance b (copies back)."""
+        N, n, m = (int(v) for v in self.h_dims[b])
+        o = self._offs_h
+        x = self.x[o["x"][b]:o["x"][b] + (N + 1) * n].view(N + 1, n).cpu().numpy()
+        u = self.u[o["u"][b]:o["u"][b] + N * m].view(N, m).cpu().numpy()
+        y = self.y[o["y"][b]:o["y"][b] + (N + 1) * n].view(N + 1, n).cpu().numpy()
+        f = self.pivot_pd[o["flag"][b]:o["flag"][b] + N + 1].cpu().numpy()
+        return x, u, y, f
+
+
+def rlqr_batched_workspace_bytes(batch: DeviceBatch, opts: rlqr_opts) -> int:
+    s = batch.c_struct()
+    return int(lib.rlqr_batched_workspace_bytes(ctypes.byref(s), ctypes.byref(opts)))
+
+
+def rlqr_solve_batched(batch: DeviceBatch, opts: rlqr_opts, ws: torch.Tensor, status=None,
+                       rel_resid=None, iters=None, stream=None):
+    s = batch.c_struct()
+    _check(lib.rlqr_solve_batched(ctypes.byref(s), ctypes.byref(opts), _ptr(ws), ws.numel(),
+                                  _ptr(status), _ptr(rel_resid), _ptr(iters), _stream(stream)),
+           "rlqr_solve_batched")

@@ -1,0 +1,212 @@
+"""GPU parity of the sequential Riccati path against the FP64 oracle, through
+the C ABI (rlqr_factor / rlqr_solve / rlqr_residual / rlqr_solve_batched)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_16370_b300 import inputs
+from paper_2509_16370_b300 import rlqr
+from tests.gpu_helpers import FWD_TOL, REL_TOL, check_against_oracle, solve_batch, solve_single
+
+pytestmark = pytest.mark.gpu
+PRECS = [rlqr.RLQR_FP64, rlqr.RLQR_MIXED]
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        d = json.load(f)
+    arr = {k: np.array(d[k], dtype=np.float64) for k in ("Q", "M", "R", "q", "r", "A", "B", "c")}
+    return d, inputs.Problem(d["N"], d["n"], d["m"], delta=float(d["delta"]), **arr)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_workload1_single_instance(prec):
+    """n=4, m=2, N=64, delta=1e-6: flags identical, rel-resid <= 1e-9, and the
+    dense Bunch-Kaufman solution of the full KKT system agrees."""
+    p = inputs.workload1()
+    out = solve_single(p, prec)
+    rel, fe, ref = check_against_oracle(p, out, prec)
+    assert out["status"] == rlqr.RLQR_OK and out["status_factor"] == rlqr.RLQR_OK
+    x, u, y, inertia = oracle.dense_solve(p)
+    assert oracle.forward_error((x, u, y), out["x"], out["u"], out["y"]) <= FWD_TOL[prec]
+    nxp, nyd = oracle.kkt_dims(p.N, p.n, p.m)
+    assert inertia == (nxp, nyd, 0) and (out["flags"] == 3).all()
+    # the GPU's own residual agrees with the oracle's
+    assert out["rel"] == pytest.approx(oracle.residual(p, out["x"], out["u"], out["y"]).rel,
+                                       rel=1e-3, abs=1e-15)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_worked_examples(prec):
+    d, p = _golden("worked_example_1.json")
+    out = solve_single(p, prec)
+    z = oracle.join_solution(p, out["x"], out["u"], out["y"])
+    np.testing.assert_allclose(z, d["printed_solution"]["value"], atol=1e-12)
+    d, p = _golden("worked_example_2.json")
+    out = solve_single(p, prec)
+    check_against_oracle(p, out, prec)
+    assert list(out["flags"]) == [3, 3]
+
+
+CASES = [  # (seed, N, n, m, delta, with_M) spanning every kernel bucket and ragged tails
+    (1, 1, 1, 1, 1e-3, True), (2, 2, 3, 1, 0.0, True), (3, 7, 4, 2, 1e-2, True),
+    (4, 33, 8, 4, 1e-6, True), (5, 5, 9, 3, 0.5, True), (6, 17, 12, 4, 1e-8, False),
+    (7, 9, 16, 8, 1e-4, True), (8, 6, 17, 5, 1e-3, True), (9, 4, 32, 16, 1e-2, True),
+    (10, 3, 33, 11, 1e-5, True), (11, 3, 48, 16, 1e-7, True), (12, 40, 6, 2, 2.0, True)]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"N{c[1]}n{c[2]}m{c[3]}" for c in CASES])
+@pytest.mark.parametrize("prec", PRECS)
+def test_random_instances(case, prec):
+    seed, N, n, m, delta, withM = case
+    p = inputs.random_instance(seed, N, n, m, delta, with_M=withM)
+    out = solve_single(p, prec)
+    check_against_oracle(p, out, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_nonconvex_and_indefinite_pivots(prec):
+    """Indefinite stage Hessians with nonsingular KKT: flags report the failing
+    pivots exactly and the solution is still the KKT solution (Theorem
+    riccati-rational-identity-theorem)."""
+    p = inputs.random_instance(77, 12, 3, 2, 0.3, with_M=True)
+    p.Q[4] -= 4.0 * np.eye(3)
+    p.R[7] -= 3.0 * np.eye(2)
+    ref = oracle.riccati(p)
+    assert ref.status == oracle.NOT_PD
+    out = solve_single(p, prec)
+    check_against_oracle(p, out, prec)
+    assert out["status_factor"] == rlqr.RLQR_NOT_PD
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_singular_pivot_reports_status(prec):
+    """I + delta P_1 = 1 + (-1) = 0: the recursion is undefined; the library
+    reports RLQR_ERR_SINGULAR and returns normally."""
+    p = inputs.Problem(1, 1, 1, Q=np.array([[[1.0]], [[-1.0]]]), M=np.zeros((1, 1, 1)),
+                       R=np.array([[[1.0]]]), q=np.ones((2, 1)), r=np.ones((1, 1)),
+                       A=np.ones((1, 1, 1)), B=np.ones((1, 1, 1)), c=np.ones((2, 1)), delta=1.0)
+    out = solve_single(p, prec)
+    assert out["status_factor"] == rlqr.RLQR_ERR_SINGULAR
+    assert out["status"] == rlqr.RLQR_ERR_SINGULAR
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_factor_reuse_for_new_rhs(prec):
+    """Corollary p-recurrence: one factorization serves several right-hand sides."""
+    p = inputs.random_instance(90, 20, 5, 2, 1e-3)
+    out = solve_single(p, prec)
+    check_against_oracle(p, out, prec)
+    rng = np.random.default_rng(3)
+    for _ in range(2):
+        p.q = rng.standard_normal(p.q.shape)
+        p.r = rng.standard_normal(p.r.shape)
+        p.c = rng.standard_normal(p.c.shape)
+        dp = rlqr.DeviceProblem.from_host(p)
+        x = torch.zeros(p.N + 1, p.n, dtype=torch.float64, device="cuda")
+        u = torch.zeros(p.N, p.m, dtype=torch.float64, device="cuda")
+        y = torch.zeros_like(x)
+        rel = torch.zeros(1, dtype=torch.float64, device="cuda")
+        rlqr.rlqr_solve(dp, out["opts"], out["ws"], x, u, y, rel)
+        torch.cuda.synchronize()
+        o2 = dict(x=x.cpu().numpy(), u=u.cpu().numpy(), y=y.cpu().numpy(), flags=out["flags"])
+        check_against_oracle(p, o2, prec)
+
+
+def test_residual_matches_oracle():
+    p = inputs.random_instance(91, 15, 6, 3, 0.2)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((p.N + 1, p.n))
+    u = rng.standard_normal((p.N, p.m))
+    y = rng.standard_normal((p.N + 1, p.n))
+    dp = rlqr.DeviceProblem.from_host(p)
+    tx, tu, ty = (torch.from_numpy(a).cuda() for a in (x, u, y))
+    dim = (p.N + 1) * p.n * 2 + p.N * p.m
+    res = torch.zeros(dim, dtype=torch.float64, device="cuda")
+    norms = torch.zeros(5, dtype=torch.float64, device="cuda")
+    rlqr.rlqr_residual(dp, tx, tu, ty, res, norms)
+    torch.cuda.synchronize()
+    ref = oracle.residual(p, x, u, y)
+    want = np.concatenate([ref.res_q.ravel(), ref.res_r.ravel(), ref.res_c.ravel()])
+    np.testing.assert_allclose(res.cpu().numpy(), want, rtol=1e-13, atol=1e-13)
+    nv = norms.cpu().numpy()
+    np.testing.assert_allclose(nv, [ref.rmax, ref.kmax, ref.zmax, ref.bmax, ref.rel], rtol=1e-12)
+
+
+def test_workspace_errors():
+    p = inputs.random_instance(92, 4, 3, 1, 1e-3)
+    dp = rlqr.DeviceProblem.from_host(p)
+    opts = rlqr.make_opts(rlqr.RLQR_FP64)
+    nb = rlqr.rlqr_workspace_bytes(p.N, p.n, p.m, opts)
+    small = rlqr.alloc_workspace(nb - 8)
+    flags = torch.zeros(p.N + 1, dtype=torch.uint8, device="cuda")
+    with pytest.raises(rlqr.RlqrError, match="workspace"):
+        rlqr.rlqr_factor(dp, opts, small, flags)
+    big = rlqr.alloc_workspace(nb + 512)
+    with pytest.raises(rlqr.RlqrError, match="workspace"):
+        rlqr.rlqr_factor(dp, opts, big[8:], flags)  # misaligned
+
+
+def _batch_parity(batch_host, dbatch, prec, out):
+    st, xo, uo, yo, fo = oracle.riccati_batch(batch_host)
+    rels = []
+    for b in range(batch_host.count):
+        x, u, y, f = dbatch.instance_view(b)
+        np.testing.assert_array_equal(f, fo[b])
+        p = batch_host.instance(b)
+        rel = oracle.residual(p, x, u, y).rel
+        rels.append(rel)
+        want = rlqr.RLQR_NOT_PD if st[b] == oracle.NOT_PD else rlqr.RLQR_OK
+        assert out["status"][b] == want
+    rels = np.array(rels)
+    assert rels.max() <= REL_TOL, f"max oracle rel-resid {rels.max():.3e}"
+    if out["rel"] is not None:
+        # the device's residual bookkeeping agrees with the oracle's
+        assert np.all(out["rel"] <= REL_TOL)
+        # equal up to the rounding noise of two FP64 residual evaluations
+        np.testing.assert_allclose(out["rel"], rels, rtol=0.05, atol=2e-14)
+    return rels
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_workload2_small_batch(prec):
+    """64 instances, N=64, n=12, m=4 (30% non-convex, 5% pivot-indefinite)."""
+    bh = inputs.workload2(count=64, N=64)
+    db = rlqr.DeviceBatch.from_uniform(bh)
+    out = solve_batch(db, prec)
+    _batch_parity(bh, db, prec, out)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_workload2_full_batch(prec):
+    """The full 1024-instance workload (n=12, m=4, N=256), every instance
+    checked: flags byte-identical, oracle rel-resid <= 1e-9."""
+    bh = inputs.workload2()
+    db = rlqr.DeviceBatch.from_uniform(bh)
+    out = solve_batch(db, prec)
+    rels = _batch_parity(bh, db, prec, out)
+    if prec == rlqr.RLQR_MIXED:
+        assert out["iters"].max() <= 3
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ragged_batch(prec):
+    """Instances of different (N, n, m) in one call, including tails of
+    every kernel bucket."""
+    dims = [(5, 3, 1), (64, 12, 4), (1, 1, 1), (33, 6, 2), (17, 24, 8), (9, 48, 16),
+            (100, 4, 2), (2, 16, 5)]
+    probs = [inputs.random_instance(200 + i, N, n, m, 10.0 ** (-1 - i % 6))
+             for i, (N, n, m) in enumerate(dims)]
+    db = rlqr.DeviceBatch.from_problems(probs)
+    out = solve_batch(db, prec)
+    for b, p in enumerate(probs):
+        x, u, y, f = db.instance_view(b)
+        ref = oracle.riccati(p)
+        np.testing.assert_array_equal(f, ref.flags)
+        assert oracle.residual(p, x, u, y).rel <= REL_TOL
+        assert oracle.forward_error((ref.x, ref.u, ref.y), x, u, y) <= FWD_TOL[prec]
