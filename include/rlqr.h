@@ -185,6 +185,36 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
                                int32_t *iters, rlqr_stream_t stream);
 
 /* ------------------------------------------------------------------ *
+ * Allocation-free solve (no counterpart in the paper).                 *
+ * ------------------------------------------------------------------ */
+
+/* Largest scratch the allocation-free entry point can use, in bytes.  The
+ * scratch is a file-scope __device__ array of this size inside the library:
+ * every GPU that loads the library holds it until the process exits. */
+#define RLQR_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* Factor + solve one instance (the same kernels as rlqr_factor and
+ * rlqr_solve, fused) without any workspace argument and without allocating:
+ * for callers that cannot call cudaMalloc -- e.g. a control loop with a fixed
+ * memory budget that forbids allocation after start-up, or code running
+ * inside another runtime that owns the device allocator.  Scratch is the
+ * library's static device array (RLQR_NOALLOC_SCRATCH_BYTES); an instance
+ * whose rlqr_workspace_bytes(N, nx, nu, opts) exceeds it is rejected with
+ * RLQR_ERR_WORKSPACE before anything runs.  The caller passes inputs (prob)
+ * and device outputs x, u, y, pivot_pd (N+1 bytes) and optional device
+ * rel_resid / status (1 element each), exactly as for rlqr_solve.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array, which keeps the last
+ *     call's contents; the per-instance state at its start is cleared by each
+ *     call.  Calls whose executions overlap on the GPU (different streams,
+ *     or host threads) race on the array: serialise them. */
+rlqr_status rlqr_solve_noalloc(const rlqr_problem *prob, const rlqr_opts *opts, double *x,
+                               double *u, double *y, uint8_t *pivot_pd, double *rel_resid,
+                               int32_t *status, rlqr_stream_t stream);
+
+/* ------------------------------------------------------------------ *
  * Instrumentation (no counterpart in the paper): per-kernel timing.    *
  * ------------------------------------------------------------------ */
 

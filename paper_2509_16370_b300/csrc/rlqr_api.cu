@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "launch.cuh"
@@ -277,6 +278,67 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
   if (mixed)
     for (int it = 0; it < opts->max_refine; ++it) {
       e = launch_solve<float, true>(nmax, mmax, uniform, a, s);
+      if (e != cudaSuccess) return RLQR_ERR_CUDA;
+    }
+  return RLQR_OK;
+}
+
+// ---- allocation-free entry point
+// The scratch of rlqr_solve_noalloc: a file-scope device array, so that the
+// call itself never allocates.  Host code only sees a host-side stand-in for
+// the symbol; the device address comes from cudaGetSymbolAddress, taken once
+// per device with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RLQR_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
+rlqr_status rlqr_solve_noalloc(const rlqr_problem *prob, const rlqr_opts *opts, double *x,
+                               double *u, double *y, uint8_t *pivot_pd, double *rel_resid,
+                               int32_t *status, rlqr_stream_t stream) {
+  if (!valid_problem(prob) || !valid_opts(opts) || !x || !u || !y || !pivot_pd)
+    return RLQR_ERR_ARG;
+  const size_t need = rlqr_workspace_bytes(prob->N, prob->nx, prob->nu, opts);
+  if (need == 0) return RLQR_ERR_ARG;
+  if (need > RLQR_NOALLOC_SCRATCH_BYTES) return RLQR_ERR_WORKSPACE;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RLQR_ERR_CUDA;
+  void *ws = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RLQR_ERR_CUDA;
+      g_noalloc_ptr[dev] = p;
+    }
+    ws = g_noalloc_ptr[dev];
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // the per-instance state at the start of the scratch starts from zero
+  if (cudaMemsetAsync(ws, 0, sizeof(InstState), s) != cudaSuccess) return RLQR_ERR_CUDA;
+  BatchArgs a = single_args(prob, opts, ws);
+  a.x = x;
+  a.u = u;
+  a.y = y;
+  a.flags = pivot_pd;
+  a.status = status;
+  a.rel = rel_resid;
+  const bool mixed = opts->prec == RLQR_MIXED;
+  a.want_norms = (mixed || rel_resid) ? 1 : 0;
+  const int n = prob->nx, m = prob->nu;
+  cudaError_t e = mixed ? launch_seq<float, true>(n, m, true, a, s)
+                        : launch_seq<double, true>(n, m, true, a, s);
+  if (e != cudaSuccess) return RLQR_ERR_CUDA;
+  if (mixed || rel_resid) {
+    e = launch_residual(a, 2 * n + m, mixed ? 1 : 0, nullptr, nullptr, 0, 0, s, mixed ? 1 : 0, 1);
+    if (e != cudaSuccess) return RLQR_ERR_CUDA;
+  }
+  if (mixed)
+    for (int it = 0; it < opts->max_refine; ++it) {
+      e = launch_solve<float, true>(n, m, true, a, s);
       if (e != cudaSuccess) return RLQR_ERR_CUDA;
     }
   return RLQR_OK;

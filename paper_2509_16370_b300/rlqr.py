@@ -27,7 +27,9 @@ RLQR_FP64, RLQR_MIXED = 0, 1
 
 EXPORTED = ("rlqr_default_opts", "rlqr_version", "rlqr_status_string", "rlqr_workspace_bytes",
             "rlqr_factor", "rlqr_solve", "rlqr_residual", "rlqr_batched_workspace_bytes",
-            "rlqr_solve_batched", "rlqr_instrument", "rlqr_instrument_report")
+            "rlqr_solve_batched", "rlqr_instrument", "rlqr_instrument_report",
+            "rlqr_solve_noalloc")
+NOALLOC_SCRATCH_BYTES = 8 << 20
 
 _dp = ctypes.c_void_p
 
@@ -76,6 +78,9 @@ def _load():
     lib.rlqr_batched_workspace_bytes.argtypes = [P(rlqr_batch), P(rlqr_opts)]
     lib.rlqr_solve_batched.restype = st
     lib.rlqr_solve_batched.argtypes = [P(rlqr_batch), P(rlqr_opts), _dp, sz, _dp, _dp, _dp, _dp]
+    lib.rlqr_solve_noalloc.restype = st
+    lib.rlqr_solve_noalloc.argtypes = [P(rlqr_problem), P(rlqr_opts), _dp, _dp, _dp, _dp, _dp, _dp,
+                                       _dp]
     lib.rlqr_instrument.restype = st
     lib.rlqr_instrument.argtypes = [ctypes.c_int]
     lib.rlqr_instrument_report.restype = ctypes.c_int
@@ -194,6 +199,17 @@ def rlqr_residual(prob: DeviceProblem, x, u, y, res=None, norms=None, stream=Non
     ps = prob.c_struct()
     _check(lib.rlqr_residual(ctypes.byref(ps), _ptr(x), _ptr(u), _ptr(y), _ptr(res), _ptr(norms),
                              _stream(stream)), "rlqr_residual")
+
+
+def rlqr_solve_noalloc(prob: DeviceProblem, opts: rlqr_opts, x, u, y, pivot_pd, rel_resid=None,
+                       status=None, stream=None):
+    """Factor + solve one instance with the library's static scratch instead
+    of a workspace: for callers that must not allocate device memory (see
+    include/rlqr.h).  Concurrent calls on one device race on that scratch."""
+    ps = prob.c_struct()
+    _check(lib.rlqr_solve_noalloc(ctypes.byref(ps), ctypes.byref(opts), _ptr(x), _ptr(u), _ptr(y),
+                                  _ptr(pivot_pd), _ptr(rel_resid), _ptr(status), _stream(stream)),
+           "rlqr_solve_noalloc")
 
 
 # ------------------------------------------------------------------- batches
