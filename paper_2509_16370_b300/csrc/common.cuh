@@ -88,7 +88,6 @@ struct BatchArgs {
   int32_t *iters;
   double tol;
   int max_refine;
-  int want_norms;
 };
 
 struct Inst {
@@ -172,6 +171,50 @@ struct RegSeg {
   }
 };
 
+// Lane-strided register staging for warp-per-instance kernels: element
+// `lane + 32 i` of the segment goes to v[i].
+template <typename S, int CNT>
+struct LaneSeg {
+  S v[CNT > 0 ? CNT : 1];
+  __device__ __forceinline__ void load(const S *__restrict__ g, int len, int lane) {
+#pragma unroll
+    for (int i = 0; i < CNT; ++i) {
+      const int idx = lane + 32 * i;
+      if (idx < len) v[i] = __ldg(g + idx);
+    }
+  }
+  __device__ __forceinline__ void load_cg(const S *g, int len, int lane) {
+#pragma unroll
+    for (int i = 0; i < CNT; ++i) {
+      const int idx = lane + 32 * i;
+      if (idx < len) v[i] = __ldcg(g + idx);
+    }
+  }
+  template <typename T>
+  __device__ __forceinline__ void store(T *s, int len, int lane) const {
+#pragma unroll
+    for (int i = 0; i < CNT; ++i) {
+      const int idx = lane + 32 * i;
+      if (idx < len) s[idx] = (T)v[i];
+    }
+  }
+  // row-major n x n symmetric matrix given by its upper triangle
+  template <typename T>
+  __device__ __forceinline__ void store_sym(T *s, int n, int lane) const {
+#pragma unroll
+    for (int i = 0; i < CNT; ++i) {
+      const int idx = lane + 32 * i;
+      if (idx < n * n) {
+        const int r = idx / n, c = idx - r * n;
+        if (r <= c) {
+          s[r * n + c] = (T)v[i];
+          s[c * n + r] = (T)v[i];
+        }
+      }
+    }
+  }
+};
+
 // Dimension policies: DynDims reads (n, m) at run time (bounded by NM, MM);
 // FixDims makes them compile-time constants so that every loop bound and
 // index division folds (the common sizes get their own instantiation).
@@ -205,6 +248,19 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
 }
 __device__ __forceinline__ double bits_to_double(unsigned long long b) {
   return __longlong_as_double((long long)b);
+}
+
+// |v| truncated to FP32 with integer operations only (relative error below
+// 2^-23; 0 below the FP32 normal range, +inf above it or for inf / NaN).
+// Used for norms that only scale a backward error: an FP64 -> FP32
+// conversion instruction would take FP64 issue slots on B300.
+__device__ __forceinline__ float abs_f32_trunc(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v) & 0x7fffffffu;
+  const unsigned lo = (unsigned)__double2loint(v);
+  const int e = (int)(hi >> 20);
+  if (e < 897) return 0.f;
+  if (e > 1150) return __uint_as_float(0x7f800000u);
+  return __uint_as_float(((unsigned)(e - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
 }
 
 __device__ __forceinline__ bool finite_nonzero(double d) { return isfinite(d) && d != 0.0; }

@@ -1,80 +1,7 @@
 // launch_fp32.cu -- FP32 (mixed-precision) kernel instantiations.
-#include "launch.cuh"
-#include "refine.cuh"
-#include "seq.cuh"
+#include "launch_impl.cuh"
 
 namespace rlqr {
-
-// Kernel selection.  Sizes that the workloads use get compile-time
-// dimensions (FixDims); everything else runs the bucket kernel whose maxima
-// (NM, MM) cover it (DynDims).
-template <typename T, class D, int TH, bool SOLVE>
-static cudaError_t launch_seq_impl(const BatchArgs &a, cudaStream_t s) {
-  auto kern = k_seq<T, D, TH, SOLVE>;
-  const size_t bytes = SeqSmem<T, D::NM, D::MM>::bytes(sizeof(T) == 4);
-  cudaError_t e = set_smem(kern, bytes);
-  if (e != cudaSuccess) return e;
-  LaunchScope ls(sizeof(T) == 4 ? (SOLVE ? "k_seq_fp32_solve" : "k_seq_fp32_factor")
-                                : (SOLVE ? "k_seq_fp64_solve" : "k_seq_fp64_factor"), s);
-  kern<<<a.count, TH, bytes, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <typename T, class D, int TH, bool FROM_RES>
-static cudaError_t launch_solve_impl(const BatchArgs &a, cudaStream_t s) {
-  auto kern = k_solve<T, D, TH, FROM_RES>;
-  const size_t bytes = SolveSmem<T, D::NM, D::MM>::bytes();
-  cudaError_t e = set_smem(kern, bytes);
-  if (e != cudaSuccess) return e;
-  LaunchScope ls(FROM_RES ? "k_solve_refine" : (sizeof(T) == 4 ? "k_solve_fp32" : "k_solve_fp64"),
-                 s);
-  kern<<<a.count, TH, bytes, s>>>(a);
-  return cudaGetLastError();
-}
-
-// Fixed-size instantiations: (n, m, threads).
-#define RLQR_FIXED_SIZES(X) \
-  X(4, 2, 64)               \
-  X(6, 1, 64)               \
-  X(6, 2, 64)               \
-  X(12, 4, 128)             \
-  X(24, 8, 256)             \
-  X(32, 8, 256)             \
-  X(48, 16, 256)
-
-template <typename T, bool SOLVE>
-cudaError_t launch_seq(int n, int m, bool uniform, const BatchArgs &a, cudaStream_t s) {
-  if (uniform && SOLVE) {
-#define RLQR_SEQ_FIXED(NX, NU, TH) \
-    if (n == NX && m == NU) return launch_seq_impl<T, FixDims<NX, NU>, TH, SOLVE>(a, s);
-    RLQR_FIXED_SIZES(RLQR_SEQ_FIXED)
-#undef RLQR_SEQ_FIXED
-  }
-  switch (bucket_of(n, m)) {
-    case 0: return launch_seq_impl<T, DynDims<8, 4>, 128, SOLVE>(a, s);
-    case 1: return launch_seq_impl<T, DynDims<16, 8>, 128, SOLVE>(a, s);
-    case 2: return launch_seq_impl<T, DynDims<32, 16>, 256, SOLVE>(a, s);
-    case 3: return launch_seq_impl<T, DynDims<48, 16>, 256, SOLVE>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <typename T, bool FROM_RES>
-cudaError_t launch_solve(int n, int m, bool uniform, const BatchArgs &a, cudaStream_t s) {
-  if (uniform && FROM_RES) {
-#define RLQR_SOLVE_FIXED(NX, NU, TH) \
-    if (n == NX && m == NU) return launch_solve_impl<T, FixDims<NX, NU>, TH, FROM_RES>(a, s);
-    RLQR_FIXED_SIZES(RLQR_SOLVE_FIXED)
-#undef RLQR_SOLVE_FIXED
-  }
-  switch (bucket_of(n, m)) {
-    case 0: return launch_solve_impl<T, DynDims<8, 4>, 128, FROM_RES>(a, s);
-    case 1: return launch_solve_impl<T, DynDims<16, 8>, 128, FROM_RES>(a, s);
-    case 2: return launch_solve_impl<T, DynDims<32, 16>, 256, FROM_RES>(a, s);
-    case 3: return launch_solve_impl<T, DynDims<48, 16>, 256, FROM_RES>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
 
 template cudaError_t launch_seq<float, true>(int, int, bool, const BatchArgs &, cudaStream_t);
 template cudaError_t launch_seq<float, false>(int, int, bool, const BatchArgs &, cudaStream_t);

@@ -48,8 +48,10 @@ __global__ void k_residual(BatchArgs a, int store, double *res_out, double *norm
   double *rc = rr + (size_t)N * m;
   double *oq = res_out, *orr = res_out ? res_out + (size_t)(N + 1) * n : nullptr;
   double *oc = res_out ? orr + (size_t)N * m : nullptr;
-  double kmax = 0.0, bmax = 0.0;
-  unsigned long long rbits = 0, zbits = 0;  // max |.| as order-preserving bit patterns
+  // ||K|| row sums in FP32 (they only scale the backward error); the maxima
+  // of |res|, |z| and |b| as order-preserving bit patterns (INT pipe)
+  float kmaxf = 0.f;
+  unsigned long long rbits = 0, zbits = 0, bbits = 0;
 
   if (cert_g) {
     // Control-pivot certificate (mixed path): FP64 LDL^T of every stored
@@ -140,17 +142,17 @@ __global__ void k_residual(BatchArgs a, int store, double *res_out, double *norm
       if (r < n) {
         zv = __ldg(I.x + (size_t)s * n + r);
         bv = __ldg(I.q + (size_t)s * n + r) - __ldg(I.y + (size_t)s * n + r);
-        if (recompute_norms) bmax = fmax(bmax, fabs(__ldg(I.q + (size_t)s * n + r)));
+        if (recompute_norms) bbits = max(bbits, abs_bits(__ldg(I.q + (size_t)s * n + r)));
       } else if (r < n + m) {
         zv = __ldg(I.u + (size_t)s * m + r - n);
         bv = __ldg(I.r + (size_t)s * m + r - n);
-        if (recompute_norms) bmax = fmax(bmax, fabs(bv));
+        if (recompute_norms) bbits = max(bbits, abs_bits(bv));
       } else {
         const size_t o = (size_t)(s + 1) * n + r - n - m;
         zv = __ldg(I.y + o);
         const double cv = __ldg(I.c + o);
         bv = cv - delta * zv - __ldg(I.x + o);
-        if (recompute_norms) bmax = fmax(bmax, fabs(cv));
+        if (recompute_norms) bbits = max(bbits, abs_bits(cv));
       }
       zb[r] = zv;
       base[r] = bv;
@@ -162,9 +164,9 @@ __global__ void k_residual(BatchArgs a, int store, double *res_out, double *norm
       const double *row = Kb + r * ld;
       for (int j = 0; j < rs; ++j) v = fma(row[j], zb[j], v);
       if (recompute_norms) {
-        double ra = (r < n) ? 1.0 : ((r < n + m) ? 0.0 : 1.0 + delta);
-        for (int j = 0; j < rs; ++j) ra += fabs(row[j]);
-        kmax = fmax(kmax, ra);
+        float ra = (r < n) ? 1.f : ((r < n + m) ? 0.f : 1.f + abs_f32_trunc(delta));
+        for (int j = 0; j < rs; ++j) ra += abs_f32_trunc(row[j]);
+        kmaxf = fmaxf(kmaxf, ra);
       }
       rbits = max(rbits, abs_bits(v));
       if (r < n) {
@@ -186,16 +188,16 @@ __global__ void k_residual(BatchArgs a, int store, double *res_out, double *norm
       const double *QN = I.Q + (size_t)N * nn, *xN = I.x + (size_t)N * n;
       const double qv = __ldg(I.q + (size_t)N * n + r), yv = __ldg(I.y + (size_t)N * n + r);
       v = qv - yv;
-      double ra = 1.0;
+      float ra = 1.f;
       for (int j = 0; j < n; ++j) {
         const double q = (r <= j) ? __ldg(QN + r * n + j) : __ldg(QN + j * n + r);
         v = fma(q, __ldg(xN + j), v);
-        ra += fabs(q);
+        ra += abs_f32_trunc(q);
       }
       zbits = max(zbits, max(abs_bits(__ldg(xN + r)), abs_bits(yv)));
       if (recompute_norms) {
-        kmax = fmax(kmax, ra);
-        bmax = fmax(bmax, fabs(qv));
+        kmaxf = fmaxf(kmaxf, ra);
+        bbits = max(bbits, abs_bits(qv));
       }
       if (store) rq[(size_t)N * n + r] = v;
       if (oq) oq[(size_t)N * n + r] = v;
@@ -205,8 +207,8 @@ __global__ void k_residual(BatchArgs a, int store, double *res_out, double *norm
       v = cv - delta * yv - xv;
       zbits = max(zbits, max(abs_bits(xv), abs_bits(yv)));
       if (recompute_norms) {
-        kmax = fmax(kmax, 1.0 + delta);
-        bmax = fmax(bmax, fabs(cv));
+        kmaxf = fmaxf(kmaxf, 1.f + abs_f32_trunc(delta));
+        bbits = max(bbits, abs_bits(cv));
       }
       if (store) rc[i] = v;
       if (oc) oc[i] = v;
@@ -215,9 +217,10 @@ __global__ void k_residual(BatchArgs a, int store, double *res_out, double *norm
   }
   const double rmax = block_max_dyn(bits_to_double(rbits), s_red);
   const double zmax = block_max_dyn(bits_to_double(zbits), s_red);
+  double kmax = 0.0, bmax = 0.0;
   if (recompute_norms) {
-    kmax = block_max_dyn(kmax, s_red);
-    bmax = block_max_dyn(bmax, s_red);
+    kmax = block_max_dyn((double)kmaxf, s_red);
+    bmax = block_max_dyn(bits_to_double(bbits), s_red);
   }
   if (threadIdx.x == 0) {
     InstState local{};

@@ -259,7 +259,6 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
   a.iters = iters;
   a.tol = opts->tol;
   a.max_refine = opts->max_refine;
-  a.want_norms = (mixed || rel_resid) ? 1 : 0;
   cudaError_t e;
   {
     LaunchScope ls("k_plan", s);
@@ -272,7 +271,7 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
             : launch_seq<double, true>(nmax, mmax, uniform, a, s);
   if (e != cudaSuccess) return RLQR_ERR_CUDA;
   if (mixed || rel_resid) {
-    e = launch_residual(a, rs_max, mixed ? 1 : 0, nullptr, nullptr, 0, 0, s, mixed ? 1 : 0, 1);
+    e = launch_residual(a, rs_max, mixed ? 1 : 0, nullptr, nullptr, 1, 0, s, mixed ? 1 : 0, 1);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
   if (mixed)
@@ -327,13 +326,12 @@ rlqr_status rlqr_solve_noalloc(const rlqr_problem *prob, const rlqr_opts *opts, 
   a.status = status;
   a.rel = rel_resid;
   const bool mixed = opts->prec == RLQR_MIXED;
-  a.want_norms = (mixed || rel_resid) ? 1 : 0;
   const int n = prob->nx, m = prob->nu;
   cudaError_t e = mixed ? launch_seq<float, true>(n, m, true, a, s)
                         : launch_seq<double, true>(n, m, true, a, s);
   if (e != cudaSuccess) return RLQR_ERR_CUDA;
   if (mixed || rel_resid) {
-    e = launch_residual(a, 2 * n + m, mixed ? 1 : 0, nullptr, nullptr, 0, 0, s, mixed ? 1 : 0, 1);
+    e = launch_residual(a, 2 * n + m, mixed ? 1 : 0, nullptr, nullptr, 1, 0, s, mixed ? 1 : 0, 1);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
   if (mixed)

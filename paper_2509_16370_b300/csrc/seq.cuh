@@ -13,6 +13,11 @@
 //   P_k = Q_k + A^T WA + H^T K_k,  p_k = q_k + A^T g + H^T k_k
 //                                          (eq. value-fn-formulas)
 //
+// Both eliminations are register-resident: each thread owns a fixed column
+// and a fixed block of rows of the augmented matrix, and only the pivot row
+// and pivot column of each step go through shared memory (double-buffered,
+// one barrier per step).  There is no index arithmetic inside the steps.
+//
 // Certificate (Section "Inertia Certification"): flags[i] bit0 says that the
 // state pivot I + delta P_i is PD, bit1 that the control pivot G_i is PD.
 //  * FP64 sweep: Gauss-Jordan without pivoting meets the pivots of an LDL^T
@@ -32,142 +37,132 @@
 //   y_{k+1} = P_{k+1} x_{k+1} + p_{k+1} = W_{k+1} v + p_{k+1}
 // because (I + delta P)^{-1} = I - delta P (I + delta P)^{-1}.
 //
-// Each pivot reciprocal is computed once (by the thread that finalises the
-// pivot entry).  The next stage's data is prefetched into registers while the
+// Each pivot reciprocal is computed once, by the thread that owns the pivot
+// entry.  The next stage's data is prefetched into registers while the
 // current stage computes, so the HBM latency is off the per-stage critical
-// path.  The common (n, m) get compile-time dimensions (FixDims): all loop
-// bounds and index divisions fold.
+// path.  The common (n, m) get compile-time dimensions (FixDims).
 #pragma once
 
 #include "common.cuh"
 
 namespace rlqr {
 
-template <typename T, int NM, int MM>
-struct SeqSmem {
-  static constexpr int kP = NM * NM, kAug = NM * 2 * NM, kB = NM * MM, kR = MM * MM;
-  static constexpr int kGaug = MM * (2 * MM + NM + 1);
-  static constexpr int kT = kP /*P*/ + kAug + kP /*W*/ + kP /*A*/ + kB /*B*/ + kP /*Q*/ +
-                            kB /*M*/ + kR /*R*/ + kP /*WA*/ + kB /*WB*/ + kB /*H*/ + kGaug +
-                            kB /*K*/ + 8 * NM + 3 * MM;
-  static constexpr int kD = NM * NM;  // FP64 shadow of I + delta P (FP32 sweep)
-  static constexpr size_t bytes(bool shadow) {
-    return align_up(sizeof(T) * kT, 16) + (shadow ? sizeof(double) * kD : 0) + 64;
-  }
-};
-
-// Pivot bookkeeping shared by the CTA.
-template <typename T, int NM, int MM>
-struct PivotShared {
-  T rinv[NM];          // reciprocals of the Gauss-Jordan pivots of [I + delta P | P]
-  T ginv[MM];          // ... of [G | H | h | I]
-  double rinv64[NM];   // ... of the FP64 LDL^T of I + delta P (FP32 sweep fallback)
-  int bit0, bit1, singular, status;
-};
-
-// Records the decision on pivot value d (FP64) into the shared flags.
+// Records the decision on pivot value d (FP64) into shared flags.
 __device__ __forceinline__ void decide(double d, int *bit, int *singular) {
   if (!(d > 0.0)) *bit = 0;
   if (!finite_nonzero(d)) *singular = 1;
 }
 
-// Gauss-Jordan elimination (no pivoting, rows left unscaled) of the `rows` x
-// `w` matrix X in shared memory on its leading rows x rows block.  After it,
-// X = [D | D X_0^{-1} X_right] with D the pivots; rinv[j] = 1 / D_j.  The
-// entry (j+1, j+1) is final after step j, so its reciprocal is taken there.
-// DECIDE: the Gauss-Jordan pivots decide the certificate bit (FP64 sweep).
-// With `shadow` (CTA-uniform) an FP64 LDL^T of the symmetric S (rows x rows,
-// lower triangle) runs under the same barriers and decides it instead.
-// rinv[0] / rinv64[0] must be set by the caller.  RMAX bounds `rows`; with
-// FixDims everything below unrolls to constant index math.
-template <typename T, int THREADS, int RMAX, bool DECIDE, bool HAS_SHADOW>
-__device__ __forceinline__ void gauss_jordan(const int rows, const int w, T *X, T *rinv,
-                                             bool shadow, double *S, double *rinv64, int *bit,
-                                             int *singular) {
-  const int tid = threadIdx.x;
+// Shared state of one register-resident Gauss-Jordan elimination.
+template <typename T, int RMAX, int WMAX>
+struct GJShared {
+  T col[2][RMAX];   // pivot column of the current / next step
+  T row[2][WMAX];   // pivot row of the current / next step
+  T rinv[RMAX];     // reciprocals of the pivots
+  int bit, singular;
+};
+
+// Gauss-Jordan (no pivoting, rows left unscaled) of an R x W matrix spread
+// over the CTA: thread t owns column c = t % WMAX and rows r0 .. r0+RPT-1 with
+// r0 = (t / WMAX) * RPT.  After the R steps the leading block is diag(D) (D the
+// pivots, which are those of an LDL^T of a symmetric leading block) and the
+// trailing columns hold D X_0^{-1} X_right.
+template <typename T, int THREADS, int RMAX, int WMAX>
+struct RegGJ {
+  static constexpr int G = THREADS / WMAX;
+  static constexpr int RPT = (RMAX + (G > 0 ? G : 1) - 1) / (G > 0 ? G : 1);
+  static_assert(G >= 1, "the CTA must have at least one thread per column");
+  using Sh = GJShared<T, RMAX, WMAX>;
+  T v[RPT];
+  int c, r0;
+  bool own;
+
+  __device__ __forceinline__ RegGJ() {
+    c = threadIdx.x % WMAX;
+    const int g = threadIdx.x / WMAX;
+    r0 = g * RPT;
+    own = g < G;
+  }
+
+  // Publish the pivot row / column of step 0 (after v has been filled).
+  template <bool DECIDE>
+  __device__ __forceinline__ void publish0(int rows, int w, Sh &sh) {
+    if (!own || c >= w) return;
 #pragma unroll
-  for (int j = 0; j < RMAX; ++j) {
-    if (j >= rows) break;
-    if (tid == 0) {
-      if (HAS_SHADOW && shadow) decide(S[j * rows + j], bit, singular);
-      else if (DECIDE) decide((double)X[j * w + j], bit, singular);
-    }
-    const T inv = rinv[j];
-    const int cols = w - j - 1;
-    for (int idx = tid; idx < (rows - 1) * cols; idx += THREADS) {
-      const int ii = idx / cols, cc = j + 1 + (idx - ii * cols);
-      const int i = ii < j ? ii : ii + 1;
-      const T v = X[i * w + cc] - X[i * w + j] * (X[j * w + cc] * inv);
-      X[i * w + cc] = v;
-      if (i == j + 1 && cc == j + 1) rinv[j + 1] = (T)1 / v;
-    }
-    if (HAS_SHADOW && shadow) {
-      const double rd = rinv64[j];
-      const int r = rows - j - 1;
-      for (int idx = tid; idx < r * (r + 1) / 2; idx += THREADS) {
-        int i, cc;
-        tri_decode(idx, i, cc);
-        i += j + 1;
-        cc += j + 1;
-        const double v = S[i * rows + cc] - S[i * rows + j] * (S[cc * rows + j] * rd);
-        S[i * rows + cc] = v;
-        if (i == j + 1 && cc == j + 1) rinv64[j + 1] = 1.0 / v;
+    for (int r = 0; r < RPT; ++r) {
+      const int i = r0 + r;
+      if (i < rows && c == 0) sh.col[0][i] = v[r];
+      if (i == 0) {
+        sh.row[0][c] = v[r];
+        if (c == 0) {
+          sh.rinv[0] = (T)1 / v[r];
+          if (DECIDE) decide((double)v[r], &sh.bit, &sh.singular);
+        }
       }
     }
-    __syncthreads();
+  }
+
+  // Step j: eliminate column j from every row but j, then publish the pivot
+  // row / column of step j + 1.  The caller puts a barrier after it.
+  template <bool DECIDE>
+  __device__ __forceinline__ void step(int j, int rows, int w, Sh &sh) {
+    if (!own || c >= w) return;
+    const int cur = j & 1, nxt = cur ^ 1;
+    if (c > j) {
+      const T f = sh.row[cur][c] * sh.rinv[j];
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int i = r0 + r;
+        if (i < rows && i != j) v[r] -= sh.col[cur][i] * f;
+      }
+    }
+    if (j + 1 < rows) {
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int i = r0 + r;
+        if (i < rows && c == j + 1) sh.col[nxt][i] = v[r];
+        if (i == j + 1) {
+          sh.row[nxt][c] = v[r];
+          if (c == j + 1) {
+            sh.rinv[j + 1] = (T)1 / v[r];
+            if (DECIDE) decide((double)v[r], &sh.bit, &sh.singular);
+          }
+        }
+      }
+    }
+  }
+};
+
+// FP64 LDL^T step j of the symmetric rows x rows matrix S (lower triangle),
+// flat over the CTA (fallback certificate of the FP32 sweep).
+template <int THREADS>
+__device__ __forceinline__ void ldlt64_step(int j, int rows, double *S, double *rinv64, int *bit,
+                                            int *singular) {
+  const int tid = threadIdx.x;
+  if (tid == 0) decide(S[j * rows + j], bit, singular);
+  const double rd = rinv64[j];
+  const int r = rows - j - 1;
+  for (int idx = tid; idx < r * (r + 1) / 2; idx += THREADS) {
+    int i, cc;
+    tri_decode(idx, i, cc);
+    i += j + 1;
+    cc += j + 1;
+    const double v = S[i * rows + cc] - S[i * rows + j] * (S[cc * rows + j] * rd);
+    S[i * rows + cc] = v;
+    if (i == j + 1 && cc == j + 1) rinv64[j + 1] = 1.0 / v;
   }
 }
 
-// State pivot of a stage: [I + delta P | P] -> W = (I + delta P)^{-1} P,
-// symmetrized, into sW and gW (global), and the certificate bit of
-// I + delta P into ps.bit0.  Ends with a barrier.
-template <typename T, int NM, int MM, int THREADS, bool FP32SWEEP>
-__device__ __forceinline__ void state_pivot(const int n, T delta, double delta64, const T *sP,
-                                            T *sAug, T *sW, T *gW, double *sS64,
-                                            PivotShared<T, NM, MM> &ps) {
-  const int tid = threadIdx.x, w2 = 2 * n, nn = n * n;
-  for (int idx = tid; idx < n * w2; idx += THREADS) {
-    const int i = idx / w2, j = idx - i * w2;
-    const T v = (j < n) ? (T)(i == j) + delta * sP[i * n + j] : sP[i * n + (j - n)];
-    sAug[idx] = v;
-    if (idx == 0) ps.rinv[0] = (T)1 / v;
+template <typename T, int NM, int MM>
+struct SeqSmem {
+  static constexpr int kP = NM * NM, kB = NM * MM, kR = MM * MM;
+  static constexpr int kT = 5 * kP /*P W A Q WA*/ + 5 * kB /*B M WB H K*/ + kR /*R*/ +
+                            6 * NM + 3 * MM;
+  static constexpr int kD = NM * NM;  // FP64 shadow of I + delta P (FP32 sweep fallback)
+  static constexpr size_t bytes(bool shadow) {
+    return align_up(sizeof(T) * kT, 16) + (shadow ? sizeof(double) * kD : 0) + 64;
   }
-  bool shadow = false;
-  if (FP32SWEEP) {
-    // Gershgorin certificate of I + delta P: sum_{j != i} |P_ij| is taken in
-    // FP32 (non-negative terms: relative error <= (n-1) 2^-24), the test in FP64.
-    int pass = 1;
-    if (tid < n) {
-      float off = 0.f;
-      for (int j = 0; j < n; ++j)
-        if (j != tid) off += fabsf((float)sP[tid * n + j]);
-      const double bound = (double)off * (1.0 + 2.0 * n * 5.960464477539063e-08);
-      const double g = 1.0 + delta64 * ((double)sP[tid * n + tid] - bound);
-      pass = g > 1e-12;
-    }
-    shadow = !__syncthreads_and(pass);
-    if (shadow) {
-      for (int idx = tid; idx < nn; idx += THREADS) {
-        const int i = idx / n, j = idx - i * n;
-        const double v = (double)(i == j) + delta64 * (double)sP[idx];
-        sS64[idx] = v;
-        if (idx == 0) ps.rinv64[0] = 1.0 / v;
-      }
-      __syncthreads();
-    }
-  } else {
-    __syncthreads();
-  }
-  gauss_jordan<T, THREADS, NM, !FP32SWEEP, FP32SWEEP>(n, w2, sAug, ps.rinv, shadow, sS64,
-                                                     ps.rinv64, &ps.bit0, &ps.singular);
-  for (int idx = tid; idx < nn; idx += THREADS) {
-    const int i = idx / n, j = idx - i * n;
-    const T w = (T)0.5 * (sAug[i * w2 + n + j] * ps.rinv[i] + sAug[j * w2 + n + i] * ps.rinv[j]);
-    sW[idx] = w;
-    gW[idx] = w;
-  }
-  __syncthreads();
-}
+};
 
 // Sweep kernel.  SOLVE: also run the vector recursion on (q, r, c) and the
 // forward rollout, writing x, u, y.  T = float is the mixed-precision sweep
@@ -175,7 +170,10 @@ __device__ __forceinline__ void state_pivot(const int n, T delta, double delta64
 template <typename T, class D, int THREADS, bool SOLVE>
 __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
   constexpr bool FP32SWEEP = sizeof(T) == 4;
+  constexpr bool DECIDE = !FP32SWEEP;
   constexpr int NM = D::NM, MM = D::MM;
+  constexpr int WS = 2 * NM;           // columns of [I + delta P | P]
+  constexpr int WC = 2 * MM + NM + 1;  // columns of [G | H | h | I]
   const int b = blockIdx.x;
   if (b >= a.count) return;
   const Inst I = get_inst(a, b);
@@ -188,18 +186,16 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
   T *sP = sm;   sm += S::kP;
-  T *sAug = sm; sm += S::kAug;
   T *sW = sm;   sm += S::kP;
   T *sA = sm;   sm += S::kP;
-  T *sB = sm;   sm += S::kB;
   T *sQ = sm;   sm += S::kP;
-  T *sM = sm;   sm += S::kB;
-  T *sR = sm;   sm += S::kR;
   T *sWA = sm;  sm += S::kP;
+  T *sB = sm;   sm += S::kB;
+  T *sM = sm;   sm += S::kB;
   T *sWB = sm;  sm += S::kB;
   T *sH = sm;   sm += S::kB;
-  T *sG = sm;   sm += S::kGaug;
   T *sK = sm;   sm += S::kB;
+  T *sR = sm;   sm += S::kR;
   T *sp = sm;   sm += NM;
   T *sq = sm;   sm += NM;
   T *sc = sm;   sm += NM;
@@ -210,8 +206,9 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
   T *skk = sm;  sm += MM;
   T *su = sm;   sm += MM;
   double *sS64 = reinterpret_cast<double *>(smem_raw + align_up(sizeof(T) * S::kT, 16));
-  __shared__ PivotShared<T, NM, MM> ps;
-  __shared__ double s_red[THREADS / 32 + 1];
+  __shared__ GJShared<T, NM, WS> shs;   // state pivot elimination
+  __shared__ GJShared<T, MM, WC> shc;   // control pivot elimination
+  __shared__ double rinv64[NM];
 
   T *gW = reinterpret_cast<T *>(I.ws + I.L.W);
   T *gK = reinterpret_cast<T *>(I.ws + I.L.K);
@@ -221,15 +218,17 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
   T *gG = reinterpret_cast<T *>(I.ws + I.L.G);
 
   const int nn = n * n, nm = n * m, mmm = m * m;
-  const int wg = 2 * m + n + 1;  // row length of [G | H | h | I]
+  const int w2 = 2 * n, wg = 2 * m + n + 1;
   constexpr int CP = (NM * NM + THREADS - 1) / THREADS;
   constexpr int CB = (NM * MM + THREADS - 1) / THREADS;
   constexpr int CR = (MM * MM + THREADS - 1) / THREADS;
   constexpr int CV = (NM + THREADS - 1) / THREADS;
   constexpr int CM = (MM + THREADS - 1) / THREADS;
 
-  bool notpd = false;
-  T kmax_loc = 0, bmax_loc = 0;  // norms of the data, working precision (they only scale rel)
+  RegGJ<T, THREADS, NM, WS> gs;  // owner of entries of [I + delta P | P]
+  RegGJ<T, THREADS, MM, WC> gc;  // owner of entries of [G | H | h | I]
+  bool notpd = false, singular = false;
+  int bit1_next = 1;  // stage N has no control pivot
 
   // ---- terminal stage: P_N = Q_N (upper triangle), p_N = q_N
   for (int idx = tid; idx < nn; idx += THREADS) {
@@ -241,22 +240,6 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
       sp[i] = (T)I.q[(size_t)N * n + i];
       gpv[(size_t)N * n + i] = sp[i];
     }
-  if (a.want_norms) {
-    // x_N rows: |Q_N| + 1 (the -y_N); y_0 rows: 1 + delta; entries q_N and c_0 of b
-    for (int i = tid; i < n; i += THREADS) {
-      T s = 1;
-      for (int j = 0; j < n; ++j)
-        s += (T)fabs(i <= j ? I.Q[(size_t)N * nn + i * n + j] : I.Q[(size_t)N * nn + j * n + i]);
-      kmax_loc = fmax(kmax_loc, fmax(s, (T)1 + delta));
-      bmax_loc = fmax(bmax_loc, (T)fmax(fabs(I.q[(size_t)N * n + i]), fabs(I.c[i])));
-    }
-  }
-  if (tid == 0) {
-    ps.bit0 = 1;
-    ps.bit1 = 1;
-    ps.singular = 0;
-  }
-  int bit1_next = 1;  // stage N has no control pivot
 
   RegSeg<double, THREADS, CP> pfA, pfQ;
   RegSeg<double, THREADS, CB> pfB, pfM;
@@ -275,11 +258,7 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
       pfr.load(I.r + (size_t)k * m, m);
     }
   };
-  prefetch(N - 1);
-  __syncthreads();
-
-  for (int k = N - 1; k >= 0; --k) {
-    // ---- (1) commit stage k's data to shared memory, start fetching stage k-1
+  auto commit = [&]() {
     pfA.store(sA, nn);
     pfQ.store_sym(sQ, n);
     pfB.store(sB, nm);
@@ -290,90 +269,136 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
       pfc.store(sc, n);
       pfr.store(sr, m);
     }
-    if (k > 0) prefetch(k - 1);
-    __syncthreads();
-    if (SOLVE)
-      for (int i = tid; i < n; i += THREADS) sv[i] = sc[i] - delta * sp[i];
-    if (a.want_norms) {
-      // row sums of |K| (working precision: they only scale the backward error):
-      // x_k rows |Q_k| + |M_k| + |A_k^T| + 1, u_k rows |M_k^T| + |R_k| + |B_k^T|,
-      // y_{k+1} rows |A_k| + |B_k| + 1 + delta
-      for (int i = tid; i < 2 * n + m; i += THREADS) {
-        T s = 0;
+  };
+  prefetch(N - 1);
+  commit();
+  if (N > 1) prefetch(N - 2);
+  __syncthreads();
+
+  // State pivot elimination of P (in sP): [I + delta P | P] -> W into sW and
+  // gWk; the certificate bit into shs.bit.  Ends with a barrier.
+  auto state_pivot = [&](T *gWk) {
+    if (tid == 0) {
+      shs.bit = 1;
+      shs.singular = 0;
+    }
+    if (gs.own && gs.c < w2) {
+#pragma unroll
+      for (int r = 0; r < gs.RPT; ++r) {
+        const int i = gs.r0 + r;
         if (i < n) {
-          s = 1;
-          for (int j = 0; j < n; ++j) s += fabs(sQ[i * n + j]);
-          for (int j = 0; j < m; ++j) s += fabs(sM[i * m + j]);
-          for (int j = 0; j < n; ++j) s += fabs(sA[j * n + i]);
-          bmax_loc = fmax(bmax_loc, fmax(fabs(sq[i]), fabs(sc[i])));
-        } else if (i < n + m) {
-          const int a2 = i - n;
-          for (int j = 0; j < n; ++j) s += fabs(sM[j * m + a2]);
-          for (int j = 0; j < m; ++j) s += fabs(sR[a2 * m + j]);
-          for (int j = 0; j < n; ++j) s += fabs(sB[j * m + a2]);
-          bmax_loc = fmax(bmax_loc, fabs(sr[a2]));
-        } else {
-          const int a2 = i - n - m;
-          s = (T)1 + delta;
-          for (int j = 0; j < n; ++j) s += fabs(sA[a2 * n + j]);
-          for (int j = 0; j < m; ++j) s += fabs(sB[a2 * m + j]);
+          const int cc = gs.c;
+          gs.v[r] = (cc < n) ? (T)(i == cc) + delta * sP[i * n + cc] : sP[i * n + (cc - n)];
         }
-        kmax_loc = fmax(kmax_loc, s);
       }
     }
+    bool shadow = false;
+    if (FP32SWEEP) {
+      // Gershgorin certificate of I + delta P: sum_{j != i} |P_ij| in FP32
+      // (non-negative terms: relative error <= (n-1) 2^-24), the test in FP64.
+      int pass = 1;
+      if (tid < n) {
+        float off = 0.f;
+        for (int j = 0; j < n; ++j)
+          if (j != tid) off += fabsf((float)sP[tid * n + j]);
+        const double bound = (double)off * (1.0 + 2.0 * n * 5.960464477539063e-08);
+        pass = 1.0 + I.delta * ((double)sP[tid * n + tid] - bound) > 1e-12;
+      }
+      __syncthreads();  // the flag reset by thread 0 precedes every later write
+      gs.template publish0<DECIDE>(n, w2, shs);
+      shadow = !__syncthreads_and(pass);
+      if (shadow) {
+        for (int idx = tid; idx < nn; idx += THREADS) {
+          const int i = idx / n, j = idx - i * n;
+          const double v = (double)(i == j) + I.delta * (double)sP[idx];
+          sS64[idx] = v;
+          if (idx == 0) rinv64[0] = 1.0 / v;
+        }
+        __syncthreads();
+      }
+    } else {
+      __syncthreads();
+      gs.template publish0<DECIDE>(n, w2, shs);
+      __syncthreads();
+    }
+#pragma unroll(NM <= 16 ? NM : 1)
+    for (int j = 0; j < NM; ++j) {
+      if (j >= n) break;
+      gs.template step<DECIDE>(j, n, w2, shs);
+      if (FP32SWEEP && shadow) ldlt64_step<THREADS>(j, n, sS64, rinv64, &shs.bit, &shs.singular);
+      if (j == n - 1 && gs.own && gs.c >= n && gs.c < w2) {
+        // final right block: W[i][c - n] = v / D_i
+#pragma unroll
+        for (int r = 0; r < gs.RPT; ++r) {
+          const int i = gs.r0 + r;
+          if (i < n) {
+            const T w = gs.v[r] * shs.rinv[i];
+            sW[i * n + gs.c - n] = w;
+            gWk[i * n + gs.c - n] = w;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  };
 
-    // ---- (2)-(4) state pivot of stage k+1: W_{k+1}
-    state_pivot<T, NM, MM, THREADS, FP32SWEEP>(n, delta, I.delta, sP, sAug, sW,
-                                              gW + (size_t)(k + 1) * nn, sS64, ps);
+  for (int k = N - 1; k >= 0; --k) {
+    // ---- state pivot of stage k+1: W_{k+1}
+    state_pivot(gW + (size_t)(k + 1) * nn);
 
-    // ---- (5) WA = W A, WB = W B, g = p + W v
+    // ---- WA = W A, WB = W B, g = p + W (c_{k+1} - delta p)
     {
       const int tot = nn + nm + (SOLVE ? n : 0);
       for (int idx = tid; idx < tot; idx += THREADS) {
         if (idx < nn) {
           const int i = idx / n, j = idx - i * n;
           T s = 0;
-#pragma unroll
+#pragma unroll(NM <= 16 ? NM : 8)
           for (int l = 0; l < NM; ++l)
             if (l < n) s += sW[i * n + l] * sA[l * n + j];
           sWA[idx] = s;
         } else if (idx < nn + nm) {
           const int e = idx - nn, i = e / m, j = e - i * m;
           T s = 0;
-#pragma unroll
+#pragma unroll(NM <= 16 ? NM : 8)
           for (int l = 0; l < NM; ++l)
             if (l < n) s += sW[i * n + l] * sB[l * m + j];
           sWB[e] = s;
         } else {
           const int i = idx - nn - nm;
           T s = sp[i];
-#pragma unroll
+#pragma unroll(NM <= 16 ? NM : 8)
           for (int l = 0; l < NM; ++l)
-            if (l < n) s += sW[i * n + l] * sv[l];
+            if (l < n) s += sW[i * n + l] * (sc[l] - delta * sp[l]);
           sg[i] = s;
         }
       }
     }
+    if (tid == 0) {
+      shc.bit = 1;
+      shc.singular = 0;
+    }
     __syncthreads();
 
-    // ---- (6) [G | H | h | I], H copy, P_k <- Q_k + A^T WA (lower), p_k <- q_k + A^T g
-    {
-      const int nlo = n * (n + 1) / 2;
-      const int tot = m * wg + nlo + (SOLVE ? n : 0);
-      for (int idx = tid; idx < tot; idx += THREADS) {
-        if (idx < m * wg) {
-          const int i = idx / wg, j = idx - i * wg;
+    // ---- [G | H | h | I] built directly into its owners' registers;
+    //      P_k <- Q_k + A^T WA (lower triangle, mirrored), p_k <- q_k + A^T g
+    if (gc.own && gc.c < wg) {
+      const int j = gc.c;
+#pragma unroll
+      for (int r = 0; r < gc.RPT; ++r) {
+        const int i = gc.r0 + r;
+        if (i < m) {
           T s;
           if (j < m) {
             s = sR[i * m + j];
-#pragma unroll
+#pragma unroll(NM <= 16 ? NM : 8)
             for (int l = 0; l < NM; ++l)
               if (l < n) s += sB[l * m + i] * sWB[l * m + j];
             if (FP32SWEEP) gG[(size_t)k * mmm + i * m + j] = s;
           } else if (j < m + n) {
             const int jj = j - m;
             s = sM[jj * m + i];
-#pragma unroll
+#pragma unroll(NM <= 16 ? NM : 8)
             for (int l = 0; l < NM; ++l)
               if (l < n) s += sB[l * m + i] * sWA[l * n + jj];
             sH[i * n + jj] = s;
@@ -381,60 +406,73 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
             s = 0;
             if (SOLVE) {
               s = sr[i];
-#pragma unroll
+#pragma unroll(NM <= 16 ? NM : 8)
               for (int l = 0; l < NM; ++l)
                 if (l < n) s += sB[l * m + i] * sg[l];
             }
           } else {
             s = (T)((j - m - n - 1) == i);
           }
-          sG[idx] = s;
-          if (idx == 0) ps.ginv[0] = (T)1 / s;
-        } else if (idx < m * wg + nlo) {
+          gc.v[r] = s;
+        }
+      }
+    }
+    {
+      const int nlo = n * (n + 1) / 2;
+      for (int idx = tid; idx < nlo + (SOLVE ? n : 0); idx += THREADS) {
+        if (idx < nlo) {
           int i, j;
-          tri_decode(idx - m * wg, i, j);
+          tri_decode(idx, i, j);
           T s = sQ[i * n + j];
-#pragma unroll
+#pragma unroll(NM <= 16 ? NM : 8)
           for (int l = 0; l < NM; ++l)
             if (l < n) s += sA[l * n + i] * sWA[l * n + j];
           sP[i * n + j] = s;
           sP[j * n + i] = s;
         } else {
-          const int i = idx - m * wg - nlo;
+          const int i = idx - nlo;
           T s = sq[i];
-#pragma unroll
+#pragma unroll(NM <= 16 ? NM : 8)
           for (int l = 0; l < NM; ++l)
             if (l < n) s += sA[l * n + i] * sg[l];
           sp[i] = s;
         }
       }
     }
+    gc.template publish0<DECIDE>(m, wg, shc);
     __syncthreads();
 
-    // ---- (7) Gauss-Jordan on [G | H | h | I] (FP64 sweep: its pivots decide bit1)
-    gauss_jordan<T, THREADS, MM, !FP32SWEEP, false>(m, wg, sG, ps.ginv, false, nullptr, nullptr,
-                                                     &ps.bit1, &ps.singular);
-
-    // ---- (8) K_k = -G^{-1} H, k_k = -G^{-1} h, G^{-1}; store
-    for (int idx = tid; idx < nm + mmm + (SOLVE ? m : 0); idx += THREADS) {
-      if (idx < nm) {
-        const int i = idx / n, j = idx - i * n;
-        const T kv = -sG[i * wg + m + j] * ps.ginv[i];
-        sK[idx] = kv;
-        gK[(size_t)k * nm + idx] = kv;
-      } else if (idx < nm + mmm) {
-        const int e = idx - nm, i = e / m, j = e - i * m;
-        gGi[(size_t)k * mmm + e] = sG[i * wg + m + n + 1 + j] * ps.ginv[i];
-      } else {
-        const int i = idx - nm - mmm;
-        const T kv = -sG[i * wg + m + n] * ps.ginv[i];
-        skk[i] = kv;
-        gkv[(size_t)k * m + i] = kv;
+    // ---- control pivot elimination; K_k = -G^{-1} H, k_k = -G^{-1} h, G^{-1}
+#pragma unroll(MM <= 16 ? MM : 1)
+    for (int j = 0; j < MM; ++j) {
+      if (j >= m) break;
+      gc.template step<DECIDE>(j, m, wg, shc);
+      if (j == m - 1 && gc.own && gc.c >= m && gc.c < wg) {
+#pragma unroll
+        for (int r = 0; r < gc.RPT; ++r) {
+          const int i = gc.r0 + r;
+          if (i < m) {
+            const T x = gc.v[r] * shc.rinv[i];
+            const int cc = gc.c;
+            if (cc < m + n) {
+              sK[i * n + cc - m] = -x;
+              gK[(size_t)k * nm + i * n + cc - m] = -x;
+            } else if (cc == m + n) {
+              if (SOLVE) {
+                skk[i] = -x;
+                gkv[(size_t)k * m + i] = -x;
+              }
+            } else {
+              gGi[(size_t)k * mmm + i * m + cc - m - n - 1] = x;
+            }
+          }
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
 
-    // ---- (9) P_k += H^T K_k (symmetric), p_k += H^T k_k; store p_k; flags
+    // ---- P_k += H^T K_k (symmetric), p_k += H^T k_k; store p_k; flags;
+    //      commit stage k-1's data and start fetching stage k-2
     {
       const int nlo = n * (n + 1) / 2;
       for (int idx = tid; idx < nlo + (SOLVE ? n : 0); idx += THREADS) {
@@ -459,41 +497,34 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
         }
       }
     }
+    if (k > 0) {
+      commit();
+      if (k > 1) prefetch(k - 2);
+    }
     if (tid == 0) {
       // FP32 sweep: bit1 of stages < N is added by the FP64 control-pivot pass
       const int b1 = FP32SWEEP ? (k + 1 == N) : bit1_next;
-      I.flags[k + 1] = (uint8_t)(ps.bit0 | (b1 << 1));
-      if (!ps.bit0 || (!FP32SWEEP && !b1)) notpd = true;
-      bit1_next = ps.bit1;
-      ps.bit0 = 1;
-      ps.bit1 = 1;
+      I.flags[k + 1] = (uint8_t)(shs.bit | (b1 << 1));
+      if (!shs.bit || (!FP32SWEEP && !b1)) notpd = true;
+      if (shs.singular || (!FP32SWEEP && shc.singular)) singular = true;
+      bit1_next = shc.bit;
     }
     __syncthreads();
   }
 
   // ---- initial-state pivot I + delta P_0: W_0 and bit0 of stage 0
-  state_pivot<T, NM, MM, THREADS, FP32SWEEP>(n, delta, I.delta, sP, sAug, sW, gW, sS64, ps);
+  state_pivot(gW);
   if (tid == 0) {
     const int b1 = FP32SWEEP ? (N == 0) : bit1_next;
-    I.flags[0] = (uint8_t)(ps.bit0 | (b1 << 1));
-    if (!ps.bit0 || (!FP32SWEEP && !b1)) notpd = true;
-    ps.status = ps.singular ? RLQR_ERR_SINGULAR : (notpd ? RLQR_NOT_PD : RLQR_OK);
-  }
-  if (a.want_norms) {
-    const double km = block_max<THREADS>((double)kmax_loc, s_red);
-    const double bm = block_max<THREADS>((double)bmax_loc, s_red);
-    if (tid == 0) {
-      I.st->kmax = km;
-      I.st->bmax = bm;
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    I.st->pivot_status = ps.status;
+    I.flags[0] = (uint8_t)(shs.bit | (b1 << 1));
+    if (!shs.bit || (!FP32SWEEP && !b1)) notpd = true;
+    if (shs.singular) singular = true;
+    const int32_t st = singular ? RLQR_ERR_SINGULAR : (notpd ? RLQR_NOT_PD : RLQR_OK);
+    I.st->pivot_status = st;
     I.st->iters = 0;
     I.st->converged = 0;
     I.st->rel = 0.0;
-    if (a.status) a.status[b] = ps.status;
+    if (a.status) a.status[b] = st;
   }
   if (!SOLVE) return;
 
@@ -506,7 +537,7 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
   __syncthreads();
   for (int i = tid; i < n; i += THREADS) {
     T t = 0;
-#pragma unroll
+#pragma unroll(NM <= 16 ? NM : 8)
     for (int l = 0; l < NM; ++l)
       if (l < n) t += sW[i * n + l] * sv[l];
     const T xv = sv[i] - delta * t, yv = t + sp[i];
@@ -542,7 +573,7 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
     // u_k = K_k x_k + k_k
     for (int i = tid; i < m; i += THREADS) {
       T s = skk[i];
-#pragma unroll
+#pragma unroll(NM <= 16 ? NM : 8)
       for (int l = 0; l < NM; ++l)
         if (l < n) s += sK[i * n + l] * sx[l];
       su[i] = s;
@@ -552,7 +583,7 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
     // v = A x + B u + c_{k+1} - delta p_{k+1}
     for (int i = tid; i < n; i += THREADS) {
       T s = sc[i] - delta * sp[i];
-#pragma unroll
+#pragma unroll(NM <= 16 ? NM : 8)
       for (int l = 0; l < NM; ++l)
         if (l < n) s += sA[i * n + l] * sx[l];
 #pragma unroll
@@ -564,7 +595,7 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
     // x_{k+1} = v - delta W v, y_{k+1} = W v + p_{k+1}
     for (int i = tid; i < n; i += THREADS) {
       T t = 0;
-#pragma unroll
+#pragma unroll(NM <= 16 ? NM : 8)
       for (int l = 0; l < NM; ++l)
         if (l < n) t += sW[i * n + l] * sv[l];
       const T xv = sv[i] - delta * t, yv = t + sp[i];

@@ -36,9 +36,13 @@ def test_workload1_single_instance(prec):
     assert oracle.forward_error((x, u, y), out["x"], out["u"], out["y"]) <= FWD_TOL[prec]
     nxp, nyd = oracle.kkt_dims(p.N, p.n, p.m)
     assert inertia == (nxp, nyd, 0) and (out["flags"] == 3).all()
-    # the GPU's own residual agrees with the oracle's
-    assert out["rel"] == pytest.approx(oracle.residual(p, out["x"], out["u"], out["y"]).rel,
-                                       rel=1e-3, abs=1e-15)
+    # the GPU's own residual agrees with the oracle's (the mixed path updates it
+    # with FP32 products of the corrections: ~1e-12 absolute)
+    want = oracle.residual(p, out["x"], out["u"], out["y"]).rel
+    if prec == rlqr.RLQR_FP64:
+        assert out["rel"] == pytest.approx(want, rel=1e-3, abs=1e-15)
+    else:
+        assert out["rel"] == pytest.approx(want, rel=0.05, abs=1e-11)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -135,7 +139,9 @@ def test_residual_matches_oracle():
     want = np.concatenate([ref.res_q.ravel(), ref.res_r.ravel(), ref.res_c.ravel()])
     np.testing.assert_allclose(res.cpu().numpy(), want, rtol=1e-13, atol=1e-13)
     nv = norms.cpu().numpy()
-    np.testing.assert_allclose(nv, [ref.rmax, ref.kmax, ref.zmax, ref.bmax, ref.rel], rtol=1e-12)
+    np.testing.assert_allclose(nv[[0, 2, 3]], [ref.rmax, ref.zmax, ref.bmax], rtol=1e-12)
+    # ||K||_inf is summed in FP32 on the device (it only scales the backward error)
+    np.testing.assert_allclose(nv[[1, 4]], [ref.kmax, ref.rel], rtol=1e-5)
 
 
 def test_workspace_errors():
@@ -168,8 +174,10 @@ def _batch_parity(batch_host, dbatch, prec, out):
     if out["rel"] is not None:
         # the device's residual bookkeeping agrees with the oracle's
         assert np.all(out["rel"] <= REL_TOL)
-        # equal up to the rounding noise of two FP64 residual evaluations
-        np.testing.assert_allclose(out["rel"], rels, rtol=0.05, atol=2e-14)
+        # equal up to rounding: FP64 path ~1e-14; mixed path, whose residual is
+        # updated with FP32 products of the (small) corrections, ~1e-12
+        atol = 2e-14 if prec == rlqr.RLQR_FP64 else 1e-11
+        np.testing.assert_allclose(out["rel"], rels, rtol=0.05, atol=atol)
     return rels
 
 
