@@ -112,6 +112,9 @@ def kernel_models(n, m, stages):
         "k_seq_fp64_solve": ("hbm", (data + out) * stages, "GB/s"),
         "k_solve_refine": ("hbm", (data + 2 * out) * stages, "GB/s"),
         "k_residual_fp64": ("alu", 2.0 * (3 * n * n + 4 * n * m + m * m) * stages, "TFLOP/s"),
+        # float-float residual + FP64 control-pivot certificate: reads the
+        # data, z and the stored FP32 G_i, writes res
+        "k_residual_ff": ("hbm", (data + 2 * 8 * (2 * n + m) + 4 * m * m + 1) * stages, "GB/s"),
     }
 
 

@@ -11,8 +11,6 @@ PKG = os.path.dirname(HERE)
 OUT_DIR = os.path.join(PKG, "_lib")
 OUT = os.path.join(OUT_DIR, "librlqr.so")
 SOURCES = ["rlqr_api.cu", "launch_fp32.cu", "launch_fp64.cu"]
-DEPS = SOURCES + ["common.cuh", "seq.cuh", "seq_warp.cuh", "refine.cuh", "residual.cuh",
-                  "launch.cuh", "launch_impl.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
          "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-Xptxas", "-v"]
@@ -22,7 +20,7 @@ def _stale():
     if not os.path.exists(OUT):
         return True
     t = os.path.getmtime(OUT)
-    deps = [os.path.join(HERE, d) for d in DEPS]
+    deps = [os.path.join(HERE, d) for d in os.listdir(HERE) if d.endswith((".cu", ".cuh"))]
     deps.append(os.path.join(os.path.dirname(PKG), "include", "rlqr.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 

@@ -41,6 +41,9 @@ struct WsLayout {
   size_t pv;     // (N+1) n     p_i of the last solve
   size_t G;      // N m m       control pivots G_i (mixed path: certified in FP64 later)
   size_t res;    // FP64 residual res_q (N+1)n | res_r N m | res_c (N+1)n
+  size_t Af;     // mixed path: N n n  FP32 copy of A_i (written by the sweep)
+  size_t Bf;     // mixed path: N n m  FP32 copy of B_i
+  size_t cf;     // mixed path: (N+1) n FP32 copy of c_i
   size_t total;
 };
 
@@ -61,6 +64,13 @@ __host__ __device__ inline WsLayout ws_layout(int N, int n, int m, int tsize) {
   o = align_up(o + (size_t)N * m * m * tsize);
   L.res = o;
   o = align_up(o + ((size_t)(N + 1) * n * 2 + (size_t)N * m) * sizeof(double));
+  const size_t ts = tsize == 4 ? 4 : 0;  // the FP32 copies exist in the mixed path only
+  L.Af = o;
+  o = align_up(o + (size_t)N * n * n * ts);
+  L.Bf = o;
+  o = align_up(o + (size_t)N * n * m * ts);
+  L.cf = o;
+  o = align_up(o + (size_t)(N + 1) * n * ts);
   L.total = o;
   return L;
 }
@@ -122,6 +132,148 @@ __device__ __forceinline__ Inst get_inst(const BatchArgs &a, int b) {
   return I;
 }
 
+// FP64 <-> FP32 conversions with integer operations only.  On B300 the
+// conversion instructions share the FP64 pipe (2 results per clock per SM),
+// so an FP32 sweep that converted its FP64 inputs element by element would
+// spend more issue time converting than computing.
+//   f64_to_f32_rz: truncation of the significand (round toward zero, relative
+//   error < 2^-23); magnitudes below 2^-126 give signed zero, at or above
+//   2^128 +-inf; NaN stays NaN.
+//   f32_to_f64: exact for FP32 normals, zero, inf and NaN; FP32 subnormals
+//   (below 2^-126) give signed zero.
+__device__ __forceinline__ float f64_to_f32_rz(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned ahi = hi & 0x7fffffffu, sign = hi & 0x80000000u;
+  unsigned bits = ((ahi - 0x38000000u) << 3) | (lo >> 29);
+  if (ahi < 0x38100000u) bits = 0u;
+  if (ahi >= 0x47f00000u)
+    bits = (ahi > 0x7ff00000u || (ahi == 0x7ff00000u && lo != 0u)) ? 0x7fc00000u : 0x7f800000u;
+  return __uint_as_float(bits | sign);
+}
+
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f), sign = u & 0x80000000u, a = u & 0x7fffffffu;
+  unsigned hi = sign | ((a >> 3) + 0x38000000u), lo = a << 29;
+  if (a < 0x00800000u) {
+    hi = sign;
+    lo = 0u;
+  } else if (a >= 0x7f800000u) {
+    hi = sign | 0x7ff00000u | ((a & 0x7fffffu) >> 3);
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// Float-float (unevaluated sum hi + lo of two FP32 numbers) arithmetic, used
+// to evaluate FP64-accurate residuals on the FP32 pipes: the two-product of
+// Dekker (the FMA gives the exact rounding error of a product) and the
+// two-sum of Knuth (the exact rounding error of a sum).  The __f*_rn
+// intrinsics are never contracted into FMAs, which the error terms rely on.
+//
+// split_f64: v = hi + lo + e with hi = f64_to_f32_rz(v) and |e| < 2^-46 |v|
+// (lo keeps the top 23 of the 29 significand bits that hi drops; lo is zero
+// when |v| < 2^-80, where the absolute error stays below 2^-103).
+__device__ __forceinline__ float2 split_f64(double v) {
+  const unsigned hi_w = (unsigned)__double2hiint(v), lo_w = (unsigned)__double2loint(v);
+  const unsigned ex = (hi_w >> 20) & 0x7ffu;  // biased FP64 exponent
+  // the dropped bits (lo_w & 0x1fffffff) >> 6 as an exact FP32 integer
+  const float rem = __fsub_rn(__uint_as_float(0x4b000000u | ((lo_w & 0x1fffffffu) >> 6)), 8388608.0f);
+  // scale 2^(ex - 1023 - 52 + 6) as an FP32 power of two (ex - 942 = its field)
+  const float scale = (ex >= 943u && ex <= 1196u) ? __uint_as_float((ex - 942u) << 23) : 0.0f;
+  const float lo = __uint_as_float(__float_as_uint(__fmul_rn(rem, scale)) | (hi_w & 0x80000000u));
+  return make_float2(f64_to_f32_rz(v), lo);
+}
+
+// (sh, sl) += (ah + al) (zh + zl), dropping al zl (below 2^-46 of the term)
+__device__ __forceinline__ void ff_fma(float &sh, float &sl, float2 a, float2 z) {
+  const float p = __fmul_rn(a.x, z.x);
+  const float e = fmaf(a.x, z.x, -p);  // a.x z.x = p + e exactly
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));  // sh + p = s + err
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, fmaf(a.x, z.y, fmaf(a.y, z.x, e))));
+}
+
+// (sh, sl) += (bh + bl)
+__device__ __forceinline__ void ff_add(float &sh, float &sl, float2 b) {
+  const float s = __fadd_rn(sh, b.x);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, b.y));
+}
+
+__device__ __forceinline__ float2 ff_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// Packed FP32 pairs (fma/add/mul .f32x2, sm_100 and later): one instruction
+// does two FP32 operations with the latency of one.  The operands are
+// float2 register pairs.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 bcast2(float v) { return make_float2(v, v); }
+
+// Reciprocal of an elimination pivot.  FP32: the hardware approximation
+// refined by one Newton step for 1/d, r <- r + r (1 - d r), which squares
+// its relative error (within about one ulp of 1/d; d = 0, +-inf or an FP32
+// subnormal gives inf or NaN).  It replaces the IEEE division on the
+// critical path of each elimination step.  FP64: the IEEE quotient.
+__device__ __forceinline__ float recip_pivot(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return fmaf(r, fmaf(-d, r, 1.0f), r);
+}
+__device__ __forceinline__ double recip_pivot(double d) { return 1.0 / d; }
+
+// Gershgorin certificate for row i of S = I + delta P (P stored in FP32,
+// delta the FP64 regularization):  1 + delta (P_ii - sum_{j != i} |P_ij|) > 0.
+// `off_ru` is the off-diagonal sum accumulated with round-up additions and
+// delta_up >= delta (FP64 delta rounded up); the difference is rounded down
+// and the product up, so every rounding works against the claim and `true`
+// proves that the row's Gershgorin disc lies in (0, inf).  All rows true
+// proves S positive definite (S is symmetric).  NaN gives false.
+__device__ __forceinline__ bool gershgorin_row_pd(float p_ii, float off_ru, float delta_up) {
+  const float d = __fsub_rd(p_ii, off_ru);
+  return d >= 0.0f || __fmul_ru(delta_up, -d) < 1.0f;
+}
+
+// Working-precision conversion used by the staging helpers.
+template <typename T, typename S>
+__device__ __forceinline__ T to_work(S v) {
+  return (T)v;
+}
+template <>
+__device__ __forceinline__ float to_work<float, double>(double v) {
+  return f64_to_f32_rz(v);
+}
+// Widening of a working-precision value to FP64 (exact).
+__device__ __forceinline__ double widen(float v) { return f32_to_f64(v); }
+__device__ __forceinline__ double widen(double v) { return v; }
+
 // Thread-strided register staging of a contiguous global segment: element
 // `threadIdx.x + i*THREADS` of the segment goes to v[i].  Used to prefetch the
 // next stage's data while the current stage computes.
@@ -150,7 +302,7 @@ struct RegSeg {
 #pragma unroll
     for (int i = 0; i < CNT; ++i) {
       int idx = threadIdx.x + i * THREADS;
-      if (idx < len) s[idx] = (T)v[i];
+      if (idx < len) s[idx] = to_work<T>(v[i]);
     }
   }
   // Store a row-major n x n symmetric matrix given by its upper triangle:
@@ -163,8 +315,9 @@ struct RegSeg {
       if (idx < n * n) {
         const int r = idx / n, c = idx - r * n;
         if (r <= c) {
-          s[r * n + c] = (T)v[i];
-          s[c * n + r] = (T)v[i];
+          const T w = to_work<T>(v[i]);
+          s[r * n + c] = w;
+          s[c * n + r] = w;
         }
       }
     }
@@ -195,7 +348,7 @@ struct LaneSeg {
 #pragma unroll
     for (int i = 0; i < CNT; ++i) {
       const int idx = lane + 32 * i;
-      if (idx < len) s[idx] = (T)v[i];
+      if (idx < len) s[idx] = to_work<T>(v[i]);
     }
   }
   // row-major n x n symmetric matrix given by its upper triangle
@@ -207,8 +360,9 @@ struct LaneSeg {
       if (idx < n * n) {
         const int r = idx / n, c = idx - r * n;
         if (r <= c) {
-          s[r * n + c] = (T)v[i];
-          s[c * n + r] = (T)v[i];
+          const T w = to_work<T>(v[i]);
+          s[r * n + c] = w;
+          s[c * n + r] = w;
         }
       }
     }

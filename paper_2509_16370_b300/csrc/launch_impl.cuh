@@ -6,6 +6,7 @@
 #include "refine.cuh"
 #include "seq.cuh"
 #include "seq_warp.cuh"
+#include "sweep32.cuh"
 
 namespace rlqr {
 
@@ -46,23 +47,35 @@ static cudaError_t launch_solve_impl(const BatchArgs &a, cudaStream_t s) {
   X(32, 8, 256)             \
   X(48, 16, 256)
 
-// One warp per instance for the small sizes (2 n <= 32, 2 m + n + 1 <= 32).
+// One warp per instance for the small sizes (2 n <= 32, 2 m + n + 1 <= 32);
+// the FP32 sweep of even sizes runs the block-pivot kernel of sweep32.cuh.
 template <typename T, int NX, int NU, bool SOLVE>
 static cudaError_t launch_seq_warp(const BatchArgs &a, cudaStream_t s) {
-  constexpr int WPC = 4;
-  auto kern = k_seq_warp<T, NX, NU, WPC, SOLVE>;
-  const size_t bytes = sizeof(WarpSmem<T, NX, NU>) * WPC;
-  cudaError_t e = set_smem(kern, bytes);
-  if (e != cudaSuccess) return e;
-  LaunchScope ls(sizeof(T) == 4 ? (SOLVE ? "k_seq_fp32_solve" : "k_seq_fp32_factor")
-                                : (SOLVE ? "k_seq_fp64_solve" : "k_seq_fp64_factor"), s);
-  kern<<<(a.count + WPC - 1) / WPC, 32 * WPC, bytes, s>>>(a);
-  return cudaGetLastError();
+  const char *name = sizeof(T) == 4 ? (SOLVE ? "k_seq_fp32_solve" : "k_seq_fp32_factor")
+                                    : (SOLVE ? "k_seq_fp64_solve" : "k_seq_fp64_factor");
+  if constexpr (sizeof(T) == 4 && sweep32_fits<NX, NU>()) {
+    auto kern = k_sweep32<NX, NU, SOLVE>;
+    const size_t bytes = sizeof(Sw32<NX, NU>);
+    cudaError_t e = set_smem(kern, bytes);
+    if (e != cudaSuccess) return e;
+    LaunchScope ls(name, s);
+    kern<<<a.count, 32, bytes, s>>>(a);
+    return cudaGetLastError();
+  } else {
+    constexpr int WPC = 1;  // one instance per CTA: spreads the warps evenly over the SMs
+    auto kern = k_seq_warp<T, NX, NU, WPC, SOLVE>;
+    const size_t bytes = sizeof(WarpSmem<T, NX, NU>) * WPC;
+    cudaError_t e = set_smem(kern, bytes);
+    if (e != cudaSuccess) return e;
+    LaunchScope ls(name, s);
+    kern<<<(a.count + WPC - 1) / WPC, 32 * WPC, bytes, s>>>(a);
+    return cudaGetLastError();
+  }
 }
 
 template <typename T, int NX, int NU, bool FROM_RES>
 static cudaError_t launch_solve_warp(const BatchArgs &a, cudaStream_t s) {
-  constexpr int WPC = 4;
+  constexpr int WPC = 1;  // one instance per CTA: spreads the warps evenly over the SMs
   auto kern = k_solve_warp<T, NX, NU, WPC, FROM_RES>;
   const size_t bytes = sizeof(WarpSmem<T, NX, NU>) * WPC;
   cudaError_t e = set_smem(kern, bytes);

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(THREADS) k_solve(BatchArgs a) {
 
   // ---------------- backward: p-recurrence
   for (int i = tid; i < n; i += THREADS) {
-    T v = (T)__ldcg(Rq + (size_t)N * n + i);
+    T v = to_work<T>(__ldcg(Rq + (size_t)N * n + i));
     sp[i] = v;
     gpv[(size_t)N * n + i] = v;
   }
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(THREADS) k_solve(BatchArgs a) {
   T *dx = sdx, *dxn = sdxn, *dy = sdy, *dyn = sdyn;
   // x_0 = v0 - delta W_0 v0, y_0 = W_0 v0 + p_0, v0 = c'_0 - delta p_0
   for (int idx = tid; idx < nn; idx += THREADS) sW[idx] = __ldcg(gW + idx);
-  for (int i = tid; i < n; i += THREADS) sv[i] = (T)__ldcg(Rc + i) - delta * sp[i];
+  for (int i = tid; i < n; i += THREADS) sv[i] = to_work<T>(__ldcg(Rc + i)) - delta * sp[i];
   __syncthreads();
   for (int i = tid; i < n; i += THREADS) {
     T t = 0;
@@ -219,16 +219,16 @@ __global__ void __launch_bounds__(THREADS) k_solve(BatchArgs a) {
     dx[i] = dxv;
     dy[i] = dyv;
     if (FROM_RES) {
-      double xv = I.x[i] + (double)dxv, yv = I.y[i] + (double)dyv;
+      double xv = I.x[i] + widen(dxv), yv = I.y[i] + widen(dyv);
       I.x[i] = xv;
       I.y[i] = yv;
       zbits = max(zbits, max(abs_bits(xv), abs_bits(yv)));
-      double r0 = __ldcg(rc + i) - (double)dxv - delta64 * (double)dyv;  // (K dz) rows of y_0
+      double r0 = __ldcg(rc + i) - widen(dxv) - delta64 * widen(dyv);  // (K dz) rows of y_0
       rc[i] = r0;
       rbits = max(rbits, abs_bits(r0));
     } else {
-      I.x[i] = (double)dxv;
-      I.y[i] = (double)dyv;
+      I.x[i] = widen(dxv);
+      I.y[i] = widen(dyv);
     }
   }
   RegSeg<T, THREADS, CP> fW;
@@ -291,11 +291,11 @@ __global__ void __launch_bounds__(THREADS) k_solve(BatchArgs a) {
         if (l < n) s += sK[i * n + l] * dx[l];
       sdu[i] = s;
       if (FROM_RES) {
-        const double uv = zu[i] + (double)s;
+        const double uv = zu[i] + widen(s);
         I.u[(size_t)k * m + i] = uv;
         zbits = max(zbits, abs_bits(uv));
       } else {
-        I.u[(size_t)k * m + i] = (double)s;
+        I.u[(size_t)k * m + i] = widen(s);
       }
     }
     __syncthreads();
@@ -322,13 +322,13 @@ __global__ void __launch_bounds__(THREADS) k_solve(BatchArgs a) {
       dyn[i] = dyv;
       const size_t o = (size_t)(k + 1) * n + i;
       if (FROM_RES) {
-        const double xv = zx[i] + (double)dxv, yv = zy[i] + (double)dyv;
+        const double xv = zx[i] + widen(dxv), yv = zy[i] + widen(dyv);
         I.x[o] = xv;
         I.y[o] = yv;
         zbits = max(zbits, max(abs_bits(xv), abs_bits(yv)));
       } else {
-        I.x[o] = (double)dxv;
-        I.y[o] = (double)dyv;
+        I.x[o] = widen(dxv);
+        I.y[o] = widen(dyv);
       }
     }
     __syncthreads();
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(THREADS) k_solve(BatchArgs a) {
           old = zc[j];
           dst = rc + (size_t)(k + 1) * n + j;
         }
-        const double nv = old + (double)s;
+        const double nv = old + widen(s);
         *dst = nv;
         rbits = max(rbits, abs_bits(nv));
       }
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(THREADS) k_solve(BatchArgs a) {
   for (int idx = tid; idx < nn; idx += THREADS) {
     const int i = idx / n, j = idx - i * n;
     if (i <= j) {
-      const T v = (T)__ldg(I.Q + (size_t)N * nn + idx);
+      const T v = to_work<T>(__ldg(I.Q + (size_t)N * nn + idx));
       sQ[i * n + j] = v;
       sQ[j * n + i] = v;
     }
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(THREADS) k_solve(BatchArgs a) {
     T s = -dy[i];
     for (int l = 0; l < n; ++l) s += sQ[i * n + l] * dx[l];
     double *dst = rq + (size_t)N * n + i;
-    double nv = __ldcg(dst) + (double)s;
+    double nv = __ldcg(dst) + widen(s);
     *dst = nv;
     rbits = max(rbits, abs_bits(nv));
   }

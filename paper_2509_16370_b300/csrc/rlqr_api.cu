@@ -23,16 +23,18 @@ Instr g_instr;
 // of the largest instance fit in shared memory.
 static cudaError_t launch_residual(const BatchArgs &a, int rs_max, int store, double *res_out,
                                    double *norms_out, int recompute, int standalone,
-                                   cudaStream_t s, int cert_g = 0, int do_residual = 1) {
+                                   cudaStream_t s, int cert_g = 0, int do_residual = 1,
+                                   bool ff = false) {
   const size_t per_warp = residual_warp_bytes(rs_max);
   int warps = (int)std::min<size_t>(8, (200u * 1024u) / per_warp);
   warps = std::max(warps, 1);
   const size_t bytes = per_warp * warps;
-  cudaError_t e = set_smem(k_residual, bytes);
+  auto kern = ff ? k_residual<true> : k_residual<false>;
+  cudaError_t e = set_smem(kern, bytes);
   if (e != cudaSuccess) return e;
-  LaunchScope ls(do_residual ? "k_residual_fp64" : "k_cert_fp64", s);
-  k_residual<<<a.count, 32 * warps, bytes, s>>>(a, store, res_out, norms_out, recompute,
-                                               standalone, rs_max, cert_g, do_residual);
+  LaunchScope ls(!do_residual ? "k_cert_fp64" : (ff ? "k_residual_ff" : "k_residual_fp64"), s);
+  kern<<<a.count, 32 * warps, bytes, s>>>(a, store, res_out, norms_out, recompute, standalone,
+                                         rs_max, cert_g, do_residual);
   return cudaGetLastError();
 }
 
@@ -180,7 +182,8 @@ rlqr_status rlqr_solve(const rlqr_problem *prob, const rlqr_opts *opts, void *ws
                         : launch_solve<double, false>(n, m, true, a, s);
   if (e != cudaSuccess) return RLQR_ERR_CUDA;
   if (mixed || rel_resid) {
-    e = launch_residual(a, 2 * prob->nx + prob->nu, mixed ? 1 : 0, nullptr, nullptr, 1, 0, s);
+    e = launch_residual(a, 2 * prob->nx + prob->nu, mixed ? 1 : 0, nullptr, nullptr, 1, 0, s, 0, 1,
+                        mixed);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
   if (mixed)
@@ -271,7 +274,8 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
             : launch_seq<double, true>(nmax, mmax, uniform, a, s);
   if (e != cudaSuccess) return RLQR_ERR_CUDA;
   if (mixed || rel_resid) {
-    e = launch_residual(a, rs_max, mixed ? 1 : 0, nullptr, nullptr, 1, 0, s, mixed ? 1 : 0, 1);
+    e = launch_residual(a, rs_max, mixed ? 1 : 0, nullptr, nullptr, 1, 0, s, mixed ? 1 : 0, 1,
+                        mixed);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
   if (mixed)
@@ -331,7 +335,8 @@ rlqr_status rlqr_solve_noalloc(const rlqr_problem *prob, const rlqr_opts *opts, 
                         : launch_seq<double, true>(n, m, true, a, s);
   if (e != cudaSuccess) return RLQR_ERR_CUDA;
   if (mixed || rel_resid) {
-    e = launch_residual(a, 2 * n + m, mixed ? 1 : 0, nullptr, nullptr, 1, 0, s, mixed ? 1 : 0, 1);
+    e = launch_residual(a, 2 * n + m, mixed ? 1 : 0, nullptr, nullptr, 1, 0, s, mixed ? 1 : 0, 1,
+                        mixed);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
   if (mixed)

@@ -95,7 +95,7 @@ struct RegGJ {
       if (i == 0) {
         sh.row[0][c] = v[r];
         if (c == 0) {
-          sh.rinv[0] = (T)1 / v[r];
+          sh.rinv[0] = recip_pivot(v[r]);
           if (DECIDE) decide((double)v[r], &sh.bit, &sh.singular);
         }
       }
@@ -124,7 +124,7 @@ struct RegGJ {
         if (i == j + 1) {
           sh.row[nxt][c] = v[r];
           if (c == j + 1) {
-            sh.rinv[j + 1] = (T)1 / v[r];
+            sh.rinv[j + 1] = recip_pivot(v[r]);
             if (DECIDE) decide((double)v[r], &sh.bit, &sh.singular);
           }
         }
@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
   const D dims(I.n, I.m);
   const int N = I.N, n = dims.n, m = dims.m;
   const T delta = (T)I.delta;
+  const float delta_up = __double2float_ru(I.delta);  // Gershgorin test (FP32 sweep)
   const int tid = threadIdx.x;
   using S = SeqSmem<T, NM, MM>;
 
@@ -233,11 +234,11 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
   // ---- terminal stage: P_N = Q_N (upper triangle), p_N = q_N
   for (int idx = tid; idx < nn; idx += THREADS) {
     const int i = idx / n, j = idx - i * n;
-    sP[idx] = (T)((i <= j) ? I.Q[(size_t)N * nn + idx] : I.Q[(size_t)N * nn + j * n + i]);
+    sP[idx] = to_work<T>((i <= j) ? I.Q[(size_t)N * nn + idx] : I.Q[(size_t)N * nn + j * n + i]);
   }
   if (SOLVE)
     for (int i = tid; i < n; i += THREADS) {
-      sp[i] = (T)I.q[(size_t)N * n + i];
+      sp[i] = to_work<T>(I.q[(size_t)N * n + i]);
       gpv[(size_t)N * n + i] = sp[i];
     }
 
@@ -288,21 +289,20 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
         const int i = gs.r0 + r;
         if (i < n) {
           const int cc = gs.c;
-          gs.v[r] = (cc < n) ? (T)(i == cc) + delta * sP[i * n + cc] : sP[i * n + (cc - n)];
+          gs.v[r] = (cc < n) ? (i == cc ? (T)1 : (T)0) + delta * sP[i * n + cc] : sP[i * n + (cc - n)];
         }
       }
     }
     bool shadow = false;
-    if (FP32SWEEP) {
-      // Gershgorin certificate of I + delta P: sum_{j != i} |P_ij| in FP32
-      // (non-negative terms: relative error <= (n-1) 2^-24), the test in FP64.
+    if constexpr (FP32SWEEP) {
+      // Gershgorin proof that I + delta P is PD, in FP32 with directed
+      // rounding; otherwise an FP64 LDL^T decides.
       int pass = 1;
       if (tid < n) {
         float off = 0.f;
         for (int j = 0; j < n; ++j)
-          if (j != tid) off += fabsf((float)sP[tid * n + j]);
-        const double bound = (double)off * (1.0 + 2.0 * n * 5.960464477539063e-08);
-        pass = 1.0 + I.delta * ((double)sP[tid * n + tid] - bound) > 1e-12;
+          if (j != tid) off = __fadd_ru(off, fabsf(sP[tid * n + j]));
+        pass = gershgorin_row_pd(sP[tid * n + tid], off, delta_up);
       }
       __syncthreads();  // the flag reset by thread 0 precedes every later write
       gs.template publish0<DECIDE>(n, w2, shs);
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
       if (shadow) {
         for (int idx = tid; idx < nn; idx += THREADS) {
           const int i = idx / n, j = idx - i * n;
-          const double v = (double)(i == j) + I.delta * (double)sP[idx];
+          const double v = (i == j ? 1.0 : 0.0) + I.delta * widen(sP[idx]);
           sS64[idx] = v;
           if (idx == 0) rinv64[0] = 1.0 / v;
         }
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
                 if (l < n) s += sB[l * m + i] * sg[l];
             }
           } else {
-            s = (T)((j - m - n - 1) == i);
+            s = ((j - m - n - 1) == i) ? (T)1 : (T)0;
           }
           gc.v[r] = s;
         }
@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
   // x_0 = v0 - delta W_0 v0, y_0 = W_0 v0 + p_0 with v0 = c_0 - delta p_0
   for (int i = tid; i < n; i += THREADS) {
     sp[i] = __ldcg(gpv + i);
-    sv[i] = (T)I.c[i] - delta * sp[i];
+    sv[i] = to_work<T>(I.c[i]) - delta * sp[i];
   }
   __syncthreads();
   for (int i = tid; i < n; i += THREADS) {
@@ -542,8 +542,8 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
       if (l < n) t += sW[i * n + l] * sv[l];
     const T xv = sv[i] - delta * t, yv = t + sp[i];
     sx[i] = xv;
-    I.x[i] = (double)xv;
-    I.y[i] = (double)yv;
+    I.x[i] = widen(xv);
+    I.y[i] = widen(yv);
   }
   RegSeg<T, THREADS, CP> fW;
   RegSeg<T, THREADS, CB> fK;
@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
       for (int l = 0; l < NM; ++l)
         if (l < n) s += sK[i * n + l] * sx[l];
       su[i] = s;
-      I.u[(size_t)k * m + i] = (double)s;
+      I.u[(size_t)k * m + i] = widen(s);
     }
     __syncthreads();
     // v = A x + B u + c_{k+1} - delta p_{k+1}
@@ -600,8 +600,8 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
         if (l < n) t += sW[i * n + l] * sv[l];
       const T xv = sv[i] - delta * t, yv = t + sp[i];
       sx[i] = xv;
-      I.x[(size_t)(k + 1) * n + i] = (double)xv;
-      I.y[(size_t)(k + 1) * n + i] = (double)yv;
+      I.x[(size_t)(k + 1) * n + i] = widen(xv);
+      I.y[(size_t)(k + 1) * n + i] = widen(yv);
     }
     __syncthreads();
   }

@@ -99,7 +99,7 @@ __device__ __forceinline__ T warp_gj_step(int j, int lane, bool active, T (&v)[R
 #pragma unroll
   for (int i = 0; i < R; ++i) colj[i] = __shfl_sync(0xffffffffu, v[i], j);
   const T d = colj[j];
-  rinv_j = (T)1 / d;
+  rinv_j = recip_pivot(d);
   if (active && lane > j) {
     const T f = v[j] * rinv_j;
 #pragma unroll
@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(32 * WPC) k_seq_warp(BatchArgs a) {
   const Inst I = get_inst(a, b);
   const int N = I.N;
   const T delta = (T)I.delta;
+  const float delta_up = __double2float_ru(I.delta);  // Gershgorin test (FP32 sweep)
   T *gW = reinterpret_cast<T *>(I.ws + I.L.W);
   T *gK = reinterpret_cast<T *>(I.ws + I.L.K);
   T *gGi = reinterpret_cast<T *>(I.ws + I.L.Gi);
@@ -176,11 +177,11 @@ __global__ void __launch_bounds__(32 * WPC) k_seq_warp(BatchArgs a) {
   // ---- terminal stage: P_N = Q_N (upper triangle), p_N = q_N
   for (int e = lane; e < nn; e += 32) {
     const int i = e / n, j = e - i * n;
-    s.P[e] = (T)((i <= j) ? I.Q[(size_t)N * nn + e] : I.Q[(size_t)N * nn + j * n + i]);
+    s.P[e] = to_work<T>((i <= j) ? I.Q[(size_t)N * nn + e] : I.Q[(size_t)N * nn + j * n + i]);
   }
   if (SOLVE)
     for (int i = lane; i < n; i += 32) {
-      s.p[i] = (T)I.q[(size_t)N * n + i];
+      s.p[i] = to_work<T>(I.q[(size_t)N * n + i]);
       gpv[(size_t)N * n + i] = s.p[i];
     }
   prefetch(N - 1);
@@ -200,29 +201,28 @@ __global__ void __launch_bounds__(32 * WPC) k_seq_warp(BatchArgs a) {
 #pragma unroll
     for (int i = 0; i < n; ++i) {
       T val = 0;
-      if (act) val = (lane < n) ? (T)(i == lane) + delta * s.P[lane * n + i]
+      if (act) val = (lane < n) ? (i == lane ? (T)1 : (T)0) + delta * s.P[lane * n + i]
                                 : s.P[(lane - n) * n + i];
       vs[i] = val;
     }
     int bit = 1;
     bool shadow = false;
-    if (FP32SWEEP) {
-      // FP64 Gershgorin proof that I + delta P is PD (rigorous bound on the
-      // FP32 row sum); otherwise an FP64 LDL^T decides.
-      int pass = 1;
+    if constexpr (FP32SWEEP) {
+      // Gershgorin proof that I + delta P is PD, in FP32 with directed
+      // rounding; otherwise an FP64 LDL^T decides.
+      bool pass = true;
       if (lane < n) {
         float off = 0.f;
 #pragma unroll
         for (int j = 0; j < n; ++j)
-          if (j != lane) off += fabsf((float)s.P[lane * n + j]);
-        const double bound = (double)off * (1.0 + 2.0 * n * 5.960464477539063e-08);
-        pass = 1.0 + I.delta * ((double)s.P[lane * n + lane] - bound) > 1e-12;
+          if (j != lane) off = __fadd_ru(off, fabsf(s.P[lane * n + j]));
+        pass = gershgorin_row_pd(s.P[lane * n + lane], off, delta_up);
       }
       shadow = !__all_sync(0xffffffffu, pass);
       if (shadow) {
         for (int e = lane; e < nn; e += 32) {
           const int i = e / n, j = e - i * n;
-          s.S64[e] = (double)(i == j) + I.delta * (double)s.P[e];
+          s.S64[e] = (i == j ? 1.0 : 0.0) + I.delta * widen(s.P[e]);
         }
         __syncwarp();
         for (int j = 0; j < n; ++j) {
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(32 * WPC) k_seq_warp(BatchArgs a) {
 #pragma unroll
       for (int i = 0; i < m; ++i) {
         T val = 0;
-        if (act) val = (lane < LG) ? s.Ga[i * LG + lane] : (T)(lane - LG == i);
+        if (act) val = (lane < LG) ? s.Ga[i * LG + lane] : (lane - LG == i ? (T)1 : (T)0);
         vc[i] = val;
       }
       T ginv[m];
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(32 * WPC) k_seq_warp(BatchArgs a) {
   // x_0 = v0 - delta W_0 v0, y_0 = W_0 v0 + p_0 with v0 = c_0 - delta p_0
   if (lane < n) {
     s.p[lane] = __ldcg(gpv + lane);
-    s.v[lane] = (T)I.c[lane] - delta * s.p[lane];
+    s.v[lane] = to_work<T>(I.c[lane]) - delta * s.p[lane];
   }
   __syncwarp();
   if (lane < n) {
@@ -478,8 +478,8 @@ __global__ void __launch_bounds__(32 * WPC) k_seq_warp(BatchArgs a) {
     for (int l = 0; l < n; ++l) t += s.W[lane * n + l] * s.v[l];
     const T xv = s.v[lane] - delta * t, yv = t + s.p[lane];
     s.x[lane] = xv;
-    I.x[lane] = (double)xv;
-    I.y[lane] = (double)yv;
+    I.x[lane] = widen(xv);
+    I.y[lane] = widen(yv);
   }
   LaneSeg<T, CP> fW;
   LaneSeg<T, CB> fK;
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(32 * WPC) k_seq_warp(BatchArgs a) {
 #pragma unroll
       for (int l = 0; l < n; ++l) t += s.K[lane * n + l] * s.x[l];
       s.u[lane] = t;
-      I.u[(size_t)k * m + lane] = (double)t;
+      I.u[(size_t)k * m + lane] = widen(t);
     }
     __syncwarp();
     if (lane < n) {
@@ -529,8 +529,8 @@ __global__ void __launch_bounds__(32 * WPC) k_seq_warp(BatchArgs a) {
       for (int l = 0; l < n; ++l) t += s.W[lane * n + l] * s.v[l];
       const T xv = s.v[lane] - delta * t, yv = t + s.p[lane];
       s.x[lane] = xv;
-      I.x[(size_t)(k + 1) * n + lane] = (double)xv;
-      I.y[(size_t)(k + 1) * n + lane] = (double)yv;
+      I.x[(size_t)(k + 1) * n + lane] = widen(xv);
+      I.y[(size_t)(k + 1) * n + lane] = widen(yv);
     }
     __syncwarp();
   }
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(32 * WPC) k_solve_warp(BatchArgs a) {
 
   // ---------------- backward: p-recurrence
   if (lane < n) {
-    const T v = (T)__ldcg(Rq + (size_t)N * n + lane);
+    const T v = to_work<T>(__ldcg(Rq + (size_t)N * n + lane));
     s.p[lane] = v;
     gpv[(size_t)N * n + lane] = v;
   }
@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(32 * WPC) k_solve_warp(BatchArgs a) {
   T *dxn = s.g, *dyn = s.WA;          // dx_{k+1}, dy_{k+1}
   // x_0 = v0 - delta W_0 v0, y_0 = W_0 v0 + p_0, v0 = c'_0 - delta p_0
   for (int e = lane; e < nn; e += 32) s.W[e] = __ldcg(gW + e);
-  if (lane < n) s.c[lane] = (T)__ldcg(Rc + lane) - delta * s.p[lane];
+  if (lane < n) s.c[lane] = to_work<T>(__ldcg(Rc + lane)) - delta * s.p[lane];
   __syncwarp();
   if (lane < n) {
     T t = 0;
@@ -672,16 +672,16 @@ __global__ void __launch_bounds__(32 * WPC) k_solve_warp(BatchArgs a) {
     dx[lane] = dxv;
     dy[lane] = dyv;
     if (FROM_RES) {
-      const double xv = I.x[lane] + (double)dxv, yv = I.y[lane] + (double)dyv;
+      const double xv = I.x[lane] + widen(dxv), yv = I.y[lane] + widen(dyv);
       I.x[lane] = xv;
       I.y[lane] = yv;
       zbits = max(zbits, max(abs_bits(xv), abs_bits(yv)));
-      const double r0 = __ldcg(rc + lane) - (double)dxv - delta64 * (double)dyv;
+      const double r0 = __ldcg(rc + lane) - widen(dxv) - delta64 * widen(dyv);
       rc[lane] = r0;
       rbits = max(rbits, abs_bits(r0));
     } else {
-      I.x[lane] = (double)dxv;
-      I.y[lane] = (double)dyv;
+      I.x[lane] = widen(dxv);
+      I.y[lane] = widen(dyv);
     }
   }
   LaneSeg<T, CP> fW;
@@ -743,11 +743,11 @@ __global__ void __launch_bounds__(32 * WPC) k_solve_warp(BatchArgs a) {
       for (int l = 0; l < n; ++l) t += s.K[lane * n + l] * dx[l];
       du[lane] = t;
       if (FROM_RES) {
-        const double uv = zu[lane] + (double)t;
+        const double uv = zu[lane] + widen(t);
         I.u[(size_t)k * m + lane] = uv;
         zbits = max(zbits, abs_bits(uv));
       } else {
-        I.u[(size_t)k * m + lane] = (double)t;
+        I.u[(size_t)k * m + lane] = widen(t);
       }
     }
     __syncwarp();
@@ -772,13 +772,13 @@ __global__ void __launch_bounds__(32 * WPC) k_solve_warp(BatchArgs a) {
       dyn[lane] = dyv;
       const size_t o = (size_t)(k + 1) * n + lane;
       if (FROM_RES) {
-        const double xv = zx[lane] + (double)dxv, yv = zy[lane] + (double)dyv;
+        const double xv = zx[lane] + widen(dxv), yv = zy[lane] + widen(dyv);
         I.x[o] = xv;
         I.y[o] = yv;
         zbits = max(zbits, max(abs_bits(xv), abs_bits(yv)));
       } else {
-        I.x[o] = (double)dxv;
-        I.y[o] = (double)dyv;
+        I.x[o] = widen(dxv);
+        I.y[o] = widen(dyv);
       }
     }
     __syncwarp();
@@ -813,7 +813,7 @@ __global__ void __launch_bounds__(32 * WPC) k_solve_warp(BatchArgs a) {
           old = zc[j];
           dst = rc + (size_t)(k + 1) * n + j;
         }
-        const double nv = old + (double)t;
+        const double nv = old + widen(t);
         *dst = nv;
         rbits = max(rbits, abs_bits(nv));
       }
@@ -827,7 +827,7 @@ __global__ void __launch_bounds__(32 * WPC) k_solve_warp(BatchArgs a) {
   for (int e = lane; e < nn; e += 32) {
     const int i = e / n, j = e - i * n;
     if (i <= j) {
-      const T v = (T)__ldg(I.Q + (size_t)N * nn + e);
+      const T v = to_work<T>(__ldg(I.Q + (size_t)N * nn + e));
       s.Q[i * n + j] = v;
       s.Q[j * n + i] = v;
     }
@@ -838,7 +838,7 @@ __global__ void __launch_bounds__(32 * WPC) k_solve_warp(BatchArgs a) {
 #pragma unroll
     for (int l = 0; l < n; ++l) t += s.Q[lane * n + l] * dx[l];
     double *dst = rq + (size_t)N * n + lane;
-    const double nv = __ldcg(dst) + (double)t;
+    const double nv = __ldcg(dst) + widen(t);
     *dst = nv;
     rbits = max(rbits, abs_bits(nv));
   }
