@@ -41,9 +41,14 @@ struct WsLayout {
   size_t pv;     // (N+1) n     p_i of the last solve
   size_t G;      // N m m       control pivots G_i (mixed path: certified in FP64 later)
   size_t res;    // FP64 residual res_q (N+1)n | res_r N m | res_c (N+1)n
-  size_t Af;     // mixed path: N n n  FP32 copy of A_i (written by the sweep)
-  size_t Bf;     // mixed path: N n m  FP32 copy of B_i
-  size_t cf;     // mixed path: (N+1) n FP32 copy of c_i
+  // mixed path: FP32 copies of the data written by the sweep (truncated),
+  // read by the forward pass and the refinement instead of the FP64 arrays
+  size_t Af;     // N n n
+  size_t Bf;     // N n m
+  size_t cf;     // (N+1) n
+  size_t Qf;     // N n n (as given; readers take the upper triangle)
+  size_t Mf;     // N n m
+  size_t Rf;     // N m m (as given; readers take the upper triangle)
   size_t total;
 };
 
@@ -71,6 +76,12 @@ __host__ __device__ inline WsLayout ws_layout(int N, int n, int m, int tsize) {
   o = align_up(o + (size_t)N * n * m * ts);
   L.cf = o;
   o = align_up(o + (size_t)(N + 1) * n * ts);
+  L.Qf = o;
+  o = align_up(o + (size_t)N * n * n * ts);
+  L.Mf = o;
+  o = align_up(o + (size_t)N * n * m * ts);
+  L.Rf = o;
+  o = align_up(o + (size_t)N * m * m * ts);
   L.total = o;
   return L;
 }

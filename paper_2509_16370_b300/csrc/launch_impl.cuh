@@ -7,6 +7,7 @@
 #include "seq.cuh"
 #include "seq_warp.cuh"
 #include "sweep32.cuh"
+#include "refine32.cuh"
 
 namespace rlqr {
 
@@ -75,15 +76,27 @@ static cudaError_t launch_seq_warp(const BatchArgs &a, cudaStream_t s) {
 
 template <typename T, int NX, int NU, bool FROM_RES>
 static cudaError_t launch_solve_warp(const BatchArgs &a, cudaStream_t s) {
-  constexpr int WPC = 1;  // one instance per CTA: spreads the warps evenly over the SMs
-  auto kern = k_solve_warp<T, NX, NU, WPC, FROM_RES>;
-  const size_t bytes = sizeof(WarpSmem<T, NX, NU>) * WPC;
-  cudaError_t e = set_smem(kern, bytes);
-  if (e != cudaSuccess) return e;
-  LaunchScope ls(FROM_RES ? "k_solve_refine" : (sizeof(T) == 4 ? "k_solve_fp32" : "k_solve_fp64"),
-                 s);
-  kern<<<(a.count + WPC - 1) / WPC, 32 * WPC, bytes, s>>>(a);
-  return cudaGetLastError();
+  const char *name =
+      FROM_RES ? "k_solve_refine" : (sizeof(T) == 4 ? "k_solve_fp32" : "k_solve_fp64");
+  if constexpr (sizeof(T) == 4 && FROM_RES && sweep32_fits<NX, NU>()) {
+    // the factor and the FP32 data copies come from k_sweep32
+    auto kern = k_refine32<NX, NU>;
+    const size_t bytes = sizeof(Rf32<NX, NU>);
+    cudaError_t e = set_smem(kern, bytes);
+    if (e != cudaSuccess) return e;
+    LaunchScope ls(name, s);
+    kern<<<a.count, 32, bytes, s>>>(a);
+    return cudaGetLastError();
+  } else {
+    constexpr int WPC = 1;  // one instance per CTA: spreads the warps evenly over the SMs
+    auto kern = k_solve_warp<T, NX, NU, WPC, FROM_RES>;
+    const size_t bytes = sizeof(WarpSmem<T, NX, NU>) * WPC;
+    cudaError_t e = set_smem(kern, bytes);
+    if (e != cudaSuccess) return e;
+    LaunchScope ls(name, s);
+    kern<<<(a.count + WPC - 1) / WPC, 32 * WPC, bytes, s>>>(a);
+    return cudaGetLastError();
+  }
 }
 
 #define RLQR_WARP_SIZES(X) \

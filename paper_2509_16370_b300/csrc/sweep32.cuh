@@ -30,8 +30,9 @@
 //    elimination runs.
 // Certificate: FP32 Gershgorin proof with directed rounding for I + delta P
 // (FP64 LDL^T when the proof fails); G_i is stored for the FP64 pass.  The
-// sweep also writes FP32 copies of A_i, B_i and c_i, which the forward pass
-// and the refinement read instead of converting the FP64 data again.
+// sweep also writes FP32 copies of A_i, B_i, Q_i, M_i, R_i (and c_i when it
+// solves), which the forward pass and the refinement read instead of
+// converting the FP64 data again.
 #pragma once
 
 #include "common.cuh"
@@ -133,19 +134,22 @@ __device__ __forceinline__ void commit_rows(const LaneSeg<double, CNT> &pf, int 
   }
 }
 
-// Same for an L x L symmetric matrix given by its upper triangle (mirrored).
+// Same for an L x L symmetric matrix given by its upper triangle (mirrored);
+// the optional global copy receives every element as given.
 template <int CNT, int L, int LD>
-__device__ __forceinline__ void commit_sym(const LaneSeg<double, CNT> &pf, int lane, float *dst) {
+__device__ __forceinline__ void commit_sym(const LaneSeg<double, CNT> &pf, int lane, float *dst,
+                                           float *gdst) {
 #pragma unroll
   for (int i = 0; i < CNT; ++i) {
     const int idx = lane + 32 * i;
     if (idx < L * L) {
       const int row = idx / L, col = idx - row * L;
+      const float f = f64_to_f32_rz(pf.v[i]);
       if (row <= col) {
-        const float f = f64_to_f32_rz(pf.v[i]);
         dst[row * LD + col] = f;
         dst[col * LD + row] = f;
       }
+      if (gdst) gdst[idx] = f;
     }
   }
 }
@@ -177,6 +181,9 @@ __global__ void __launch_bounds__(32) k_sweep32(BatchArgs a) {
   float *gAf = reinterpret_cast<float *>(I.ws + I.L.Af);
   float *gBf = reinterpret_cast<float *>(I.ws + I.L.Bf);
   float *gcf = reinterpret_cast<float *>(I.ws + I.L.cf);
+  float *gQf = reinterpret_cast<float *>(I.ws + I.L.Qf);
+  float *gMf = reinterpret_cast<float *>(I.ws + I.L.Mf);
+  float *gRf = reinterpret_cast<float *>(I.ws + I.L.Rf);
 
   // ---- one stage's FP64 data, prefetched into registers (lane-strided)
   constexpr int CP = (nn + 31) / 32, CB = (nm + 31) / 32, CR = (mmm + 31) / 32;
@@ -199,11 +206,11 @@ __global__ void __launch_bounds__(32) k_sweep32(BatchArgs a) {
     }
   };
   auto commit = [&](int k) {
-    commit_rows<CP, n, N4>(pfA, nn, lane, s.A, SOLVE ? gAf + (size_t)k * nn : nullptr);
-    commit_sym<CP, n, N4>(pfQ, lane, s.Q);
-    commit_rows<CB, m, M4>(pfB, nm, lane, s.B, SOLVE ? gBf + (size_t)k * nm : nullptr);
-    commit_rows<CB, m, M4>(pfM, nm, lane, s.M, nullptr);
-    commit_sym<CR, m, M4>(pfR, lane, s.R);
+    commit_rows<CP, n, N4>(pfA, nn, lane, s.A, gAf + (size_t)k * nn);
+    commit_sym<CP, n, N4>(pfQ, lane, s.Q, gQf + (size_t)k * nn);
+    commit_rows<CB, m, M4>(pfB, nm, lane, s.B, gBf + (size_t)k * nm);
+    commit_rows<CB, m, M4>(pfM, nm, lane, s.M, gMf + (size_t)k * nm);
+    commit_sym<CR, m, M4>(pfR, lane, s.R, gRf + (size_t)k * mmm);
     if (SOLVE) {
       commit_rows<CV, n, N4>(pfq, n, lane, s.q, nullptr);
       commit_rows<CV, n, N4>(pfc, n, lane, s.c, gcf + (size_t)(k + 1) * n);
