@@ -61,5 +61,10 @@ template <typename T, bool SOLVE>
 cudaError_t launch_seq(int n, int m, bool uniform, const BatchArgs &a, cudaStream_t s);
 template <typename T, bool FROM_RES>
 cudaError_t launch_solve(int n, int m, bool uniform, const BatchArgs &a, cudaStream_t s);
+// First residual of the mixed path (stored for the refinement) with the
+// compile-time-size kernel; cudaErrorNotSupported when the sizes have none.
+template <typename T>
+cudaError_t launch_residual32(int n, int m, bool uniform, const BatchArgs &a, int cert_g,
+                              cudaStream_t s);
 
 }  // namespace rlqr

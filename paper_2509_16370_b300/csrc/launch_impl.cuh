@@ -8,6 +8,7 @@
 #include "seq_warp.cuh"
 #include "sweep32.cuh"
 #include "refine32.cuh"
+#include "residual32.cuh"
 
 namespace rlqr {
 
@@ -149,6 +150,28 @@ cudaError_t launch_solve(int n, int m, bool uniform, const BatchArgs &a, cudaStr
     case 3: return launch_solve_impl<T, DynDims<48, 16>, 256, FROM_RES>(a, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <typename T>
+cudaError_t launch_residual32(int n, int m, bool uniform, const BatchArgs &a, int cert_g,
+                              cudaStream_t s) {
+  if (uniform) {
+#define RLQR_RES32(NX, NU)                                                   \
+    if constexpr (sweep32_fits<NX, NU>()) {                                  \
+      if (n == NX && m == NU) {                                              \
+        auto kern = k_res32<NX, NU>;                                         \
+        const size_t bytes = sizeof(Rs32Warp<NX, NU>) * kResWarps;           \
+        cudaError_t e = set_smem(kern, bytes);                               \
+        if (e != cudaSuccess) return e;                                      \
+        LaunchScope ls("k_residual_ff", s);                                  \
+        kern<<<a.count, 32 * kResWarps, bytes, s>>>(a, 1, cert_g);           \
+        return cudaGetLastError();                                           \
+      }                                                                      \
+    }
+    RLQR_WARP_SIZES(RLQR_RES32)
+#undef RLQR_RES32
+  }
+  return cudaErrorNotSupported;
 }
 
 }  // namespace rlqr

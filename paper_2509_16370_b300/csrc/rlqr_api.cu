@@ -38,6 +38,16 @@ static cudaError_t launch_residual(const BatchArgs &a, int rs_max, int store, do
   return cudaGetLastError();
 }
 
+// First residual of a mixed-precision solve (stored for the refinement, norms
+// recomputed, control pivots certified when cert_g): the compile-time-size
+// float-float kernel where it exists, the generic one otherwise.
+static cudaError_t launch_first_residual_mixed(const BatchArgs &a, int n, int m, bool uniform,
+                                               int rs_max, int cert_g, cudaStream_t s) {
+  cudaError_t e = launch_residual32<float>(n, m, uniform, a, cert_g, s);
+  if (e != cudaErrorNotSupported) return e;
+  return launch_residual(a, rs_max, 1, nullptr, nullptr, 1, 0, s, cert_g, 1, true);
+}
+
 // Per-instance workspace offsets of a batch: exclusive prefix sum of
 // ws_layout(...).total, after the header that holds the offsets themselves.
 __global__ void k_plan(int count, const int32_t *dN, const int32_t *dn, const int32_t *dm,
@@ -182,8 +192,9 @@ rlqr_status rlqr_solve(const rlqr_problem *prob, const rlqr_opts *opts, void *ws
                         : launch_solve<double, false>(n, m, true, a, s);
   if (e != cudaSuccess) return RLQR_ERR_CUDA;
   if (mixed || rel_resid) {
-    e = launch_residual(a, 2 * prob->nx + prob->nu, mixed ? 1 : 0, nullptr, nullptr, 1, 0, s, 0, 1,
-                        mixed);
+    e = mixed ? launch_first_residual_mixed(a, prob->nx, prob->nu, true, 2 * prob->nx + prob->nu,
+                                            0, s)
+              : launch_residual(a, 2 * prob->nx + prob->nu, 0, nullptr, nullptr, 1, 0, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
   if (mixed)
@@ -274,8 +285,8 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
             : launch_seq<double, true>(nmax, mmax, uniform, a, s);
   if (e != cudaSuccess) return RLQR_ERR_CUDA;
   if (mixed || rel_resid) {
-    e = launch_residual(a, rs_max, mixed ? 1 : 0, nullptr, nullptr, 1, 0, s, mixed ? 1 : 0, 1,
-                        mixed);
+    e = mixed ? launch_first_residual_mixed(a, nmax, mmax, uniform, rs_max, 1, s)
+              : launch_residual(a, rs_max, 0, nullptr, nullptr, 1, 0, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
   if (mixed)
@@ -335,8 +346,8 @@ rlqr_status rlqr_solve_noalloc(const rlqr_problem *prob, const rlqr_opts *opts, 
                         : launch_seq<double, true>(n, m, true, a, s);
   if (e != cudaSuccess) return RLQR_ERR_CUDA;
   if (mixed || rel_resid) {
-    e = launch_residual(a, 2 * n + m, mixed ? 1 : 0, nullptr, nullptr, 1, 0, s, mixed ? 1 : 0, 1,
-                        mixed);
+    e = mixed ? launch_first_residual_mixed(a, n, m, true, 2 * n + m, 1, s)
+              : launch_residual(a, 2 * n + m, 0, nullptr, nullptr, 1, 0, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
   if (mixed)
