@@ -13,6 +13,7 @@ flush is needed between steps.  The plain FP64 GPU recursion on the same batch
 is timed beside it, and the FP64 CPU oracle is the CPU baseline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --profile-instances K   # profiling case, no bench line
 
 Multi-GPU (torchrun): every rank solves its own copy of the batch (weak
 scaling, no data-path collective); value = all ranks' stage-solves / max time.
@@ -97,6 +98,13 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+# DRAM bytes (read + write) per instance-stage of each kernel, from one ncu
+# capture of the 296-instance case of this workload (the kernels as they are
+# in this source; see profiles/), scaled by the stages a launch processes.
+TRAFFIC_PER_STAGE = {"k_seq_fp32_solve": 7475.0, "k_residual_ff": 3924.0,
+                     "k_solve_refine": 4353.0}
+
+
 def kernel_models(n, m, stages):
     """Algorithmic work per launch of each kernel for the roofline.
 
@@ -134,9 +142,12 @@ def roofline(report, steps, n, m, stages, peaks):
         peak = FP64_PEAK_TFLOPS
         peak_src = "derived (148 SM x 2 FP64 FMA/clk x 2032 MHz)"
     total = sum(v[1] for v in report.values())
+    traffic = TRAFFIC_PER_STAGE.get(name)
     return {"kernel": name, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
             "peak_source": peak_src, "unit": unit, "frac": round(achieved / peak, 4),
-            "traffic": None, "launch_ms": round(ms / cnt, 4), "share": round(ms / total, 3)}
+            "traffic": None if traffic is None else traffic * stages,
+            "algorithmic_bytes": work if bound == "hbm" else None,
+            "launch_ms": round(ms / cnt, 4), "share": round(ms / total, 3)}
 
 
 def load_peaks():
@@ -189,6 +200,26 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "stage-solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_profile_case(args):
+    """The mixed solve alone on the first K instances of the workload: warm-up
+    calls, then one call (the launch an ncu capture selects with -s/-c)."""
+    import torch
+    from paper_2509_16370_b300 import inputs, rlqr
+    bh = inputs.workload2(count=args.profile_instances)
+    db = rlqr.DeviceBatch.from_uniform(bh)
+    opts = rlqr.make_opts(rlqr.RLQR_MIXED, tol=TOL, max_refine=3)
+    ws = rlqr.alloc_workspace(rlqr.rlqr_batched_workspace_bytes(db, opts))
+    B = bh.count
+    st = torch.zeros(B, dtype=torch.int32, device="cuda")
+    rel = torch.zeros(B, dtype=torch.float64, device="cuda")
+    it = torch.zeros(B, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup + 1):
+        rlqr.rlqr_solve_batched(db, opts, ws, st, rel, it)
+    torch.cuda.synchronize()
+    print(f"profile case: {B} instances, max rel {rel.max().item():.3e}, "
+          f"iters {it.max().item()}", flush=True)
 
 
 def run_ours(args):
@@ -321,11 +352,15 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-instances", type=int, default=0,
+                    help="profiling case: the mixed solve on the first K instances only")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_instances > 0:
+        run_profile_case(args)
     else:
         run_ours(args)
 
