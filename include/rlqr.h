@@ -68,8 +68,15 @@ typedef enum {
   RLQR_ERR_CUDA = 7            /* a CUDA launch or runtime call failed */
 } rlqr_status;
 
+/* Algorithm of a single-instance factor / solve.  SCAN (Section "Parallel
+ * Algorithm": interval elements of eq. lqr-gpu-init-running, combination
+ * rule eq. lqr-gpu-combo, chunked reverse scan, p-recurrence and composed
+ * affine x maps) has kernels for (nx, nu) in {(4,2), (6,2), (12,4), (32,8)},
+ * needs delta > 0 and every R_i invertible, and applies to rlqr_factor /
+ * rlqr_solve only (RLQR_ERR_ARG elsewhere or for other sizes).  AUTO takes
+ * SCAN for N >= 4096 where it applies, SEQ otherwise; batches always run SEQ. */
 typedef enum {
-  RLQR_ALGO_AUTO = 0, /* SEQ unless the horizon is long and there are few instances */
+  RLQR_ALGO_AUTO = 0,
   RLQR_ALGO_SEQ = 1,  /* sequential Riccati recursion, O(N) depth (Section "Sequential Algorithm") */
   RLQR_ALGO_SCAN = 2  /* associative-scan recursion, O(log N) depth (Section "Parallel Algorithm") */
 } rlqr_algo;

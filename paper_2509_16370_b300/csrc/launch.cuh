@@ -67,4 +67,19 @@ template <typename T>
 cudaError_t launch_residual32(int n, int m, bool uniform, const BatchArgs &a, int cert_g,
                               cudaStream_t s);
 
+// Associative-scan path of one long-horizon instance (scan_fp32.cu /
+// scan_fp64.cu); cudaErrorNotSupported for sizes without an instantiation.
+struct ScanLayout;
+template <typename T>
+cudaError_t launch_scan_factor(int n, int m, const BatchArgs &a, const ScanLayout &SL,
+                               size_t sbase, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scan_solve(int n, int m, bool from_res, const BatchArgs &a,
+                              const ScanLayout &SL, size_t sbase, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scan_residual(int n, int m, const BatchArgs &a, int cert_g, int do_res,
+                                 cudaStream_t s);
+template <typename T>
+cudaError_t launch_scan_norms(const BatchArgs &a, cudaStream_t s);
+
 }  // namespace rlqr

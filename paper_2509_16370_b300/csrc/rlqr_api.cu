@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "launch.cuh"
 #include "residual.cuh"
+#include "scan.cuh"
 
 namespace rlqr {
 
@@ -79,7 +80,8 @@ __global__ void k_plan(int count, const int32_t *dN, const int32_t *dn, const in
 static bool valid_opts(const rlqr_opts *o) {
   if (!o) return false;
   if (o->prec != RLQR_FP64 && o->prec != RLQR_MIXED) return false;
-  if (o->algo != RLQR_ALGO_AUTO && o->algo != RLQR_ALGO_SEQ) return false;
+  if (o->algo != RLQR_ALGO_AUTO && o->algo != RLQR_ALGO_SEQ && o->algo != RLQR_ALGO_SCAN)
+    return false;
   if (o->max_refine < 0 || o->max_refine > 64) return false;
   if (!(o->tol > 0.0) || !std::isfinite(o->tol)) return false;
   return true;
@@ -112,6 +114,34 @@ static BatchArgs single_args(const rlqr_problem *p, const rlqr_opts *o, void *ws
 }
 
 static rlqr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RLQR_OK : RLQR_ERR_CUDA; }
+
+// ---- algorithm selection for one instance
+// The scan path has kernels for these sizes; it needs delta > 0 and every
+// R_i invertible (the elimination of the controls).
+static bool scan_sizes(int n, int m) {
+  return (n == 4 && m == 2) || (n == 6 && m == 2) || (n == 12 && m == 4) || (n == 32 && m == 8);
+}
+constexpr int kScanAutoN = 4096;  // AUTO takes the scan from this horizon on
+
+// Whether the workspace must hold the scan arrays (delta is not known here).
+static bool scan_sized(int N, int n, int m, const rlqr_opts *o) {
+  if (o->algo == RLQR_ALGO_SCAN) return true;
+  return o->algo == RLQR_ALGO_AUTO && N >= kScanAutoN && scan_sizes(n, m);
+}
+
+// 1: scan, 0: sequential, -1: SCAN requested where it does not apply.
+static int use_scan(const rlqr_problem *p, const rlqr_opts *o) {
+  const bool ok = scan_sizes(p->nx, p->nu) && p->delta > 0.0;
+  if (o->algo == RLQR_ALGO_SCAN) return ok ? 1 : -1;
+  if (o->algo == RLQR_ALGO_AUTO) return (ok && p->N >= kScanAutoN) ? 1 : 0;
+  return 0;
+}
+
+static ScanLayout scan_args(const rlqr_problem *p, const rlqr_opts *o, size_t *sbase) {
+  const int tsize = o->prec == RLQR_MIXED ? 4 : 8;
+  *sbase = ws_layout(p->N, p->nx, p->nu, tsize).total;
+  return scan_layout(p->N, p->nx, scan_chunk_len(p->N), tsize);
+}
 
 }  // namespace rlqr
 
@@ -147,7 +177,9 @@ const char *rlqr_status_string(rlqr_status s) {
 size_t rlqr_workspace_bytes(int32_t N, int32_t nx, int32_t nu, const rlqr_opts *opts) {
   if (!valid_dims(N, nx, nu) || !valid_opts(opts)) return 0;
   int tsize = opts->prec == RLQR_MIXED ? 4 : 8;
-  return ws_layout(N, nx, nu, tsize).total;
+  size_t tot = ws_layout(N, nx, nu, tsize).total;
+  if (scan_sized(N, nx, nu, opts)) tot += scan_layout(N, nx, scan_chunk_len(N), tsize).total;
+  return tot;
 }
 
 rlqr_status rlqr_factor(const rlqr_problem *prob, const rlqr_opts *opts, void *ws,
@@ -162,6 +194,20 @@ rlqr_status rlqr_factor(const rlqr_problem *prob, const rlqr_opts *opts, void *w
   a.status = status;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int n = prob->nx, m = prob->nu;
+  const int scan = use_scan(prob, opts);
+  if (scan < 0) return RLQR_ERR_ARG;
+  if (scan) {
+    size_t sbase;
+    const ScanLayout SL = scan_args(prob, opts, &sbase);
+    const bool mixed = opts->prec == RLQR_MIXED;
+    cudaError_t e = mixed ? launch_scan_factor<float>(n, m, a, SL, sbase, s)
+                          : launch_scan_factor<double>(n, m, a, SL, sbase, s);
+    if (e != cudaSuccess) return RLQR_ERR_CUDA;
+    // mixed: FP64 certificate of the stored control pivots; status out
+    e = mixed ? launch_scan_residual<float>(n, m, a, 1, 0, s)
+              : launch_scan_residual<double>(n, m, a, 0, 0, s);
+    return cuda_status(e);
+  }
   if (opts->prec == RLQR_MIXED) {
     cudaError_t e = launch_seq<float, false>(n, m, true, a, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
@@ -188,6 +234,26 @@ rlqr_status rlqr_solve(const rlqr_problem *prob, const rlqr_opts *opts, void *ws
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int n = prob->nx, m = prob->nu;
   const bool mixed = opts->prec == RLQR_MIXED;
+  const int scan = use_scan(prob, opts);
+  if (scan < 0) return RLQR_ERR_ARG;
+  if (scan) {
+    size_t sbase;
+    const ScanLayout SL = scan_args(prob, opts, &sbase);
+    cudaError_t e = mixed ? launch_scan_solve<float>(n, m, false, a, SL, sbase, s)
+                          : launch_scan_solve<double>(n, m, false, a, SL, sbase, s);
+    if (e != cudaSuccess) return RLQR_ERR_CUDA;
+    const int with_res = (mixed || rel_resid) ? 1 : 0;
+    e = mixed ? launch_scan_residual<float>(n, m, a, 0, with_res, s)
+              : launch_scan_residual<double>(n, m, a, 0, with_res, s);
+    if (e != cudaSuccess) return RLQR_ERR_CUDA;
+    if (mixed)
+      for (int it = 0; it < opts->max_refine; ++it) {
+        e = launch_scan_solve<float>(n, m, true, a, SL, sbase, s);
+        if (e == cudaSuccess) e = launch_scan_norms<float>(a, s);
+        if (e != cudaSuccess) return RLQR_ERR_CUDA;
+      }
+    return RLQR_OK;
+  }
   cudaError_t e = mixed ? launch_solve<float, false>(n, m, true, a, s)
                         : launch_solve<double, false>(n, m, true, a, s);
   if (e != cudaSuccess) return RLQR_ERR_CUDA;
@@ -234,6 +300,7 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
                                size_t ws_bytes, int32_t *status, double *rel_resid,
                                int32_t *iters, rlqr_stream_t stream) {
   if (!batch || batch->count < 1 || !valid_opts(opts)) return RLQR_ERR_ARG;
+  if (opts->algo == RLQR_ALGO_SCAN) return RLQR_ERR_ARG;  // batches use the sequential recursion
   const rlqr_batch &B = *batch;
   if (!B.N || !B.nx || !B.nu || !B.delta || !B.off_Q || !B.off_M || !B.off_R || !B.off_q ||
       !B.off_r || !B.off_A || !B.off_B || !B.off_c || !B.off_x || !B.off_u || !B.off_y ||
@@ -315,8 +382,9 @@ rlqr_status rlqr_solve_noalloc(const rlqr_problem *prob, const rlqr_opts *opts, 
                                int32_t *status, rlqr_stream_t stream) {
   if (!valid_problem(prob) || !valid_opts(opts) || !x || !u || !y || !pivot_pd)
     return RLQR_ERR_ARG;
-  const size_t need = rlqr_workspace_bytes(prob->N, prob->nx, prob->nu, opts);
-  if (need == 0) return RLQR_ERR_ARG;
+  if (opts->algo == RLQR_ALGO_SCAN) return RLQR_ERR_ARG;  // sequential recursion only
+  const size_t need = ws_layout(prob->N, prob->nx, prob->nu,
+                                opts->prec == RLQR_MIXED ? 4 : 8).total;
   if (need > RLQR_NOALLOC_SCRATCH_BYTES) return RLQR_ERR_WORKSPACE;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RLQR_ERR_CUDA;

@@ -1,0 +1,618 @@
+// scan.cuh -- the associative-scan form of the dual-regularized Riccati
+// recursion (Section "Parallel Algorithm") for one long-horizon instance.
+//
+// The N stages are cut into C chunks of L stages (chunk c: stages
+// [cL, min(cL + L, N))).  With the interval elements (P, A, C)_{i->i+1} of eq.
+// lqr-gpu-init-running (the controls eliminated through R_i^{-1}) and the
+// combination rule of eq. lqr-gpu-combo, written with the single inverse
+// T = (I + C_ij P_jk)^{-1}:
+//   A_ik = A_jk T A_ij,  C_ik = A_jk T C_ij A_jk^T + C_jk,
+//   P_ik = A_ij^T P_jk T A_ij + P_ij          (Corollary inverse-helper-corollary)
+// the path is
+//   k_scan_reduce    one CTA per chunk: the chunk's element, folded from the
+//                    right (acc <- e_i (+) acc); block C writes the terminal
+//                    element (Q_N, 0, 0) of eq. lqr-gpu-init-terminal;
+//   k_scan_level     one level of a Hillis-Steele suffix scan over the C + 1
+//                    elements: after ceil(log2(C+1)) levels element c holds the
+//                    composition of chunks c..C-1 and the terminal, whose P is
+//                    P_{cL} (the value function at the chunk's first stage);
+//   k_scan_finalize  one CTA per chunk: from P at the chunk's end, the
+//                    sequential step of Theorem main-seq-theorem for every
+//                    stage of the chunk (W, G, H, K, P, the pivot certificate),
+//                    and the product Phi_c = F_s ... F_{e-1} of the maps of
+//                    Corollary p-recurrence, F_i = (A_i + B_i K_i)^T (I - delta W_{i+1}).
+// Accuracy of the FP32 scan: composing a chunk's elements in FP32 loses about
+// three digits (I + C_ij P_jk of a chunk interval has condition ~1e4-1e5 on
+// the test problems), while the sequential recursion contracts an error in
+// its starting P strongly (1e-3 -> 3e-6 over 8 stages there).  The mixed path
+// therefore runs the finalize twice: a P-only pass from the scanned
+// boundaries gives every chunk's P at its first stage, and the full pass of
+// chunk c starts from chunk c+1's value, so that each boundary error has been
+// contracted by one chunk of the sequential recursion.  The FP64 scan is
+// accurate to ~1e-11 and finalizes directly.
+// The vector passes (scan_vec.cuh) use Phi_c for p (p_s = Phi_c p_e + phi_c)
+// and Phi_c^T for x (x_e = Phi_c^T x_s + psi_c, since the x map of a stage,
+// (I - delta W_{i+1})(A_i + B_i K_i), is F_i^T for symmetric W).
+//
+// The factor is written in the workspace layout of the sequential path
+// (W, K, G^{-1}, G, the FP32 data copies in the mixed path) so that the
+// residual and the refinement see the same arrays.
+#pragma once
+
+#include "common.cuh"
+
+namespace rlqr {
+
+// Scan-specific arrays after the common workspace of the instance.
+struct ScanLayout {
+  int C, L;        // chunks, stages per chunk
+  size_t S0, S1;   // (C+1) x 3 n^2 elements (P, A, C), ping-pong
+  size_t Phi;      // C x n^2
+  size_t phi;      // C x n      p offsets of the chunks
+  size_t psi;      // C x n      x offsets of the chunks
+  size_t pb;       // (C+1) x n  p at the chunk starts (index C: p_N)
+  size_t xb;       // (C+1) x n  x at the chunk starts (index C: x_N)
+  size_t PstA;     // C x n^2    P at the chunk starts from the P-only pass (mixed path)
+  size_t PstB;     // C x n^2    P at the chunk starts from the final pass
+  size_t total;    // bytes after `base`
+};
+
+__host__ __device__ inline ScanLayout scan_layout(int N, int n, int L, int tsize) {
+  ScanLayout S;
+  S.L = L;
+  S.C = (N + L - 1) / L;
+  const size_t C = (size_t)S.C, nn = (size_t)n * n;
+  size_t o = 0;
+  S.S0 = o;
+  o = align_up(o + (C + 1) * 3 * nn * tsize);
+  S.S1 = o;
+  o = align_up(o + (C + 1) * 3 * nn * tsize);
+  S.Phi = o;
+  o = align_up(o + C * nn * tsize);
+  S.phi = o;
+  o = align_up(o + C * n * tsize);
+  S.psi = o;
+  o = align_up(o + C * n * tsize);
+  S.pb = o;
+  o = align_up(o + (C + 1) * n * tsize);
+  S.xb = o;
+  o = align_up(o + (C + 1) * n * tsize);
+  S.PstA = o;
+  o = align_up(o + C * nn * tsize);
+  S.PstB = o;
+  o = align_up(o + C * nn * tsize);
+  S.total = o;
+  return S;
+}
+
+// Chunk length: enough chunks for one wave of CTAs on a 148-SM part (a few
+// CTAs per SM), at least 8 stages per chunk.
+__host__ __device__ inline int scan_chunk_len(int N) {
+  int L = (N + 443) / 444;
+  return L < 8 ? 8 : L;
+}
+
+namespace scan {
+
+constexpr int kTH = 256;  // threads of the scan CTAs
+
+// D[r][c] = alpha * sum_k op(A)[r][k] op(B)[k][c] (+ Add[r][c]); op = transpose
+// when TA / TB.  D must not alias A or B (it may alias Add).  No barrier.
+template <typename T, bool TA, bool TB>
+__device__ __forceinline__ void mm(int R, int Cc, int K, T *D, int ldd, const T *A, int lda,
+                                   const T *B, int ldb, const T *Add, int ldadd, T alpha) {
+  for (int e = threadIdx.x; e < R * Cc; e += blockDim.x) {
+    const int r = e / Cc, c = e - r * Cc;
+    T acc = 0;
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+      const T a = TA ? A[k * lda + r] : A[r * lda + k];
+      const T b = TB ? B[c * ldb + k] : B[k * ldb + c];
+      acc = fma(a, b, acc);
+    }
+    acc *= alpha;
+    if (Add) acc += Add[r * ldadd + c];
+    D[r * ldd + c] = acc;
+  }
+}
+
+// Gauss-Jordan without pivoting on the R x Wd matrix M (left block R x R):
+// afterwards the right block holds (left)^{-1} (right).  Records the pivots'
+// decisions in *bit (all pivots > 0) and *sing (a zero or non-finite pivot)
+// when the pointers are given (thread 0 writes them).  Barriers inside;
+// `fcol` is R entries of scratch.
+template <typename T>
+__device__ __forceinline__ void gj(int R, int Wd, T *M, int ld, T *fcol, int *bit, int *sing) {
+  const int tid = threadIdx.x;
+  for (int j = 0; j < R; ++j) {
+    __syncthreads();
+    const T d = M[j * ld + j];
+    if (tid == 0 && bit) {
+      if (!((double)d > 0.0)) *bit = 0;
+      if (!finite_nonzero((double)d)) *sing = 1;
+    }
+    if (tid < R) fcol[tid] = (tid == j) ? (T)0 : M[tid * ld + j] * recip_pivot(d);
+    __syncthreads();
+    const int w = Wd - j - 1;
+    for (int e = tid; e < R * w; e += blockDim.x) {
+      const int i = e / w, c = j + 1 + (e - i * w);
+      if (i != j) M[i * ld + c] = fma(-fcol[i], M[j * ld + c], M[i * ld + c]);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < R * (Wd - R); e += blockDim.x) {
+    const int i = e / (Wd - R), c = R + (e - i * (Wd - R));
+    M[i * ld + c] *= recip_pivot(M[i * ld + i]);
+  }
+  __syncthreads();
+}
+
+// Lower triangle mirrored onto the upper one (exact symmetry).  No barrier.
+template <typename T>
+__device__ __forceinline__ void mirror_lower(int n, T *M, int ld) {
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    if (i < j) M[i * ld + j] = M[j * ld + i];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T to_T(double v) {
+  return to_work<T>(v);
+}
+
+// Shared memory of the reduce / level kernels (row stride n + 1).
+template <typename T, int NX, int NU>
+struct CombSmem {
+  static constexpr int LD = NX + 1, LD3 = 3 * NX + 1, LDR = NU + 2 * NX + 1;
+  T P1[NX * LD], A1[NX * LD], C1[NX * LD];   // earlier element
+  T P2[NX * LD], A2[NX * LD], C2[NX * LD];   // later element (the accumulator)
+  T Pn[NX * LD], An[NX * LD], Cn[NX * LD];   // result
+  T G3[NX * LD3];                            // [I + C1 P2 | A1 | C1]
+  T T1[NX * LD], T2[NX * LD];
+  T Q[NX * LD], A[NX * LD], B[NX * NU], M[NX * NU];
+  T RX[NU * LDR];                            // [R | M^T | B^T]
+  T fcol[NX > NU ? NX : NU];
+};
+
+// The stage element (P, A, C)_{i->i+1} into (P1, A1, C1); eq. lqr-gpu-init-running.
+template <typename T, int NX, int NU>
+__device__ void stage_element(const Inst &I, int i, CombSmem<T, NX, NU> &s) {
+  constexpr int n = NX, m = NU, LD = CombSmem<T, NX, NU>::LD, LDR = CombSmem<T, NX, NU>::LDR;
+  const int tid = threadIdx.x;
+  const double *Q = I.Q + (size_t)i * n * n, *A = I.A + (size_t)i * n * n;
+  const double *B = I.B + (size_t)i * n * m, *M = I.M + (size_t)i * n * m;
+  const double *R = I.R + (size_t)i * m * m;
+  __syncthreads();
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int r = e / n, c = e - r * n;
+    s.Q[r * LD + c] = to_T<T>(__ldg(Q + (r <= c ? e : c * n + r)));
+    s.A[r * LD + c] = to_T<T>(__ldg(A + e));
+  }
+  for (int e = tid; e < n * m; e += blockDim.x) {
+    const int r = e / m, c = e - r * m;
+    const T bv = to_T<T>(__ldg(B + e)), mv = to_T<T>(__ldg(M + e));
+    s.B[e] = bv;
+    s.M[e] = mv;
+    s.RX[c * LDR + m + r] = mv;       // M^T
+    s.RX[c * LDR + m + n + r] = bv;   // B^T
+  }
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int r = e / m, c = e - r * m;
+    s.RX[r * LDR + c] = to_T<T>(__ldg(R + (r <= c ? e : c * m + r)));
+  }
+  gj<T>(m, m + 2 * n, s.RX, LDR, s.fcol, nullptr, nullptr);  // R^{-1} [M^T | B^T]
+  // P = Q - M (R^{-1} M^T), A = A - B (R^{-1} M^T), C = delta I + B (R^{-1} B^T)
+  mm<T, false, false>(n, n, m, s.P1, LD, s.M, m, s.RX + m, LDR, s.Q, LD, (T)-1);
+  mm<T, false, false>(n, n, m, s.A1, LD, s.B, m, s.RX + m, LDR, s.A, LD, (T)-1);
+  mm<T, false, false>(n, n, m, s.C1, LD, s.B, m, s.RX + m + n, LDR, nullptr, 0, (T)1);
+  __syncthreads();
+  const T delta = (T)I.delta;
+  for (int r = tid; r < n; r += blockDim.x) s.C1[r * LD + r] += delta;
+  mirror_lower<T>(n, s.P1, LD);
+  mirror_lower<T>(n, s.C1, LD);
+  __syncthreads();
+}
+
+// (Pn, An, Cn) = (P1, A1, C1) (+) (P2, A2, C2); eq. lqr-gpu-combo with one
+// elimination of I + C1 P2 on [A1 | C1].
+template <typename T, int NX, int NU>
+__device__ void combine(CombSmem<T, NX, NU> &s) {
+  constexpr int n = NX, LD = CombSmem<T, NX, NU>::LD, LD3 = CombSmem<T, NX, NU>::LD3;
+  const int tid = threadIdx.x;
+  __syncthreads();
+  mm<T, false, false>(n, n, n, s.G3, LD3, s.C1, LD, s.P2, LD, nullptr, 0, (T)1);  // C1 P2
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int r = e / n, c = e - r * n;
+    s.G3[r * LD3 + n + c] = s.A1[r * LD + c];
+    s.G3[r * LD3 + 2 * n + c] = s.C1[r * LD + c];
+  }
+  __syncthreads();
+  for (int r = tid; r < n; r += blockDim.x) s.G3[r * LD3 + r] += (T)1;
+  gj<T>(n, 3 * n, s.G3, LD3, s.fcol, nullptr, nullptr);   // XA = T A1, XC = T C1
+  const T *XA = s.G3 + n, *XC = s.G3 + 2 * n;
+  mm<T, false, false>(n, n, n, s.An, LD, s.A2, LD, XA, LD3, nullptr, 0, (T)1);   // A2 XA
+  mm<T, false, false>(n, n, n, s.T1, LD, s.A2, LD, XC, LD3, nullptr, 0, (T)1);   // A2 XC
+  mm<T, false, false>(n, n, n, s.T2, LD, s.P2, LD, XA, LD3, nullptr, 0, (T)1);   // P2 XA
+  __syncthreads();
+  mm<T, false, true>(n, n, n, s.Cn, LD, s.T1, LD, s.A2, LD, s.C2, LD, (T)1);     // (A2 XC) A2^T + C2
+  mm<T, true, false>(n, n, n, s.Pn, LD, s.A1, LD, s.T2, LD, s.P1, LD, (T)1);     // A1^T (P2 XA) + P1
+  __syncthreads();
+  mirror_lower<T>(n, s.Pn, LD);
+  mirror_lower<T>(n, s.Cn, LD);
+  __syncthreads();
+}
+
+template <typename T, int NX>
+__device__ __forceinline__ void load_elem(const T *g, T *P, T *A, T *C, int LD) {
+  constexpr int n = NX, nn = n * n;
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    const int r = e / n, c = e - r * n;
+    P[r * LD + c] = g[e];
+    A[r * LD + c] = g[nn + e];
+    C[r * LD + c] = g[2 * nn + e];
+  }
+}
+
+template <typename T, int NX>
+__device__ __forceinline__ void store_elem(T *g, const T *P, const T *A, const T *C, int LD) {
+  constexpr int n = NX, nn = n * n;
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    const int r = e / n, c = e - r * n;
+    g[e] = P[r * LD + c];
+    g[nn + e] = A[r * LD + c];
+    g[2 * nn + e] = C[r * LD + c];
+  }
+}
+
+}  // namespace scan
+
+// Chunk elements into S0 (blocks 0..C-1) and the terminal element (block C).
+template <typename T, int NX, int NU>
+__global__ void __launch_bounds__(scan::kTH) k_scan_reduce(BatchArgs a, ScanLayout SL,
+                                                           size_t sbase) {
+  using SM = scan::CombSmem<T, NX, NU>;
+  constexpr int n = NX, nn = n * n, LD = SM::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &s = *reinterpret_cast<SM *>(smem_raw);
+  const Inst I = get_inst(a, 0);
+  const int N = I.N, c = blockIdx.x;
+  T *S0 = reinterpret_cast<T *>(I.ws + sbase + SL.S0);
+  T *out = S0 + (size_t)c * 3 * nn;
+  if (c == SL.C) {  // terminal element (Q_N, 0, 0); instance state reset
+    if (threadIdx.x == 0) {
+      I.st->pivot_status = RLQR_OK;
+      I.st->iters = 0;
+      I.st->converged = 0;
+      I.st->rel = 0.0;
+    }
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+      const int r = e / n, col = e - r * n;
+      out[e] = scan::to_T<T>(__ldg(I.Q + (size_t)N * nn + (r <= col ? e : col * n + r)));
+      out[nn + e] = (T)0;
+      out[2 * nn + e] = (T)0;
+    }
+    return;
+  }
+  const int s0 = c * SL.L, e0 = min(s0 + SL.L, N);
+  // acc (P2, A2, C2) = e_{e0-1}
+  scan::stage_element<T, NX, NU>(I, e0 - 1, s);
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    const int r = e / n, col = e - r * n, o = r * LD + col;
+    s.P2[o] = s.P1[o];
+    s.A2[o] = s.A1[o];
+    s.C2[o] = s.C1[o];
+  }
+  for (int i = e0 - 2; i >= s0; --i) {
+    scan::stage_element<T, NX, NU>(I, i, s);
+    scan::combine<T, NX, NU>(s);
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+      const int r = e / n, col = e - r * n, o = r * LD + col;
+      s.P2[o] = s.Pn[o];
+      s.A2[o] = s.An[o];
+      s.C2[o] = s.Cn[o];
+    }
+  }
+  __syncthreads();
+  scan::store_elem<T, NX>(out, s.P2, s.A2, s.C2, LD);
+}
+
+// One level of the suffix scan: dst[c] = src[c] (+) src[c + d] (c + d <= C),
+// otherwise src[c].
+template <typename T, int NX, int NU>
+__global__ void __launch_bounds__(scan::kTH) k_scan_level(BatchArgs a, ScanLayout SL, size_t sbase,
+                                                          int d, int from1) {
+  using SM = scan::CombSmem<T, NX, NU>;
+  constexpr int nn = NX * NX, LD = SM::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &s = *reinterpret_cast<SM *>(smem_raw);
+  const Inst I = get_inst(a, 0);
+  const int c = blockIdx.x;
+  const T *src = reinterpret_cast<const T *>(I.ws + sbase + (from1 ? SL.S1 : SL.S0));
+  T *dst = reinterpret_cast<T *>(I.ws + sbase + (from1 ? SL.S0 : SL.S1));
+  if (c + d > SL.C) {
+    for (int e = threadIdx.x; e < 3 * nn; e += blockDim.x)
+      dst[(size_t)c * 3 * nn + e] = src[(size_t)c * 3 * nn + e];
+    return;
+  }
+  scan::load_elem<T, NX>(src + (size_t)c * 3 * nn, s.P1, s.A1, s.C1, LD);
+  scan::load_elem<T, NX>(src + (size_t)(c + d) * 3 * nn, s.P2, s.A2, s.C2, LD);
+  scan::combine<T, NX, NU>(s);
+  scan::store_elem<T, NX>(dst + (size_t)c * 3 * nn, s.Pn, s.An, s.Cn, LD);
+}
+
+// Shared memory of the finalize kernel (row stride n + 1).
+template <typename T, int NX, int NU>
+struct FinSmem {
+  static constexpr int LD = NX + 1, LD2 = 2 * NX + 1, LDG = 2 * NU + NX + 1;
+  T P[NX * LD], W[NX * LD], Q[NX * LD], A[NX * LD], WA[NX * LD], ABK[NX * LD], Ft[NX * LD];
+  T T1[NX * LD], PhiA[NX * LD], PhiB[NX * LD];
+  T S2[NX * LD2];                  // [I + delta P | P]
+  T B[NX * NU], M[NX * NU], WB[NX * NU], K[NU * NX], H[NU * NX];
+  T GH[NU * LDG];                  // [G | H | I]
+  T fcol[NX];
+  double S64[NX * NX];             // FP64 LDL^T of I + delta P (FP32 certificate fallback)
+  int bit, sing, pass;
+};
+
+// PASS 1: P-only pass from the scanned boundaries, writes PstA[c] = P at the
+// chunk's first stage.  PASS 0 (from the scanned boundaries) / PASS 2 (from
+// PstA[c+1]; the terminal Q_N for the last chunk): the full pass below, which
+// also writes PstB[c].
+// From P at the chunk's end: the sequential step (Theorem main-seq-theorem,
+// eq. value-fn-formulas) for every stage i of the chunk, writing W_{i+1},
+// K_i, G_i^{-1}, flags[i+1] (bit0; bit1 set at N), G_i (mixed path: for the
+// FP64 certificate; plain FP64 path: the pivot decision of G_i, merged by
+// k_scan_flags) and the FP32 data copies (mixed path); P_i and Phi_c.  Chunk 0
+// also pivots P_0 (W_0, flags[0]).  The instance's pivot status is the worst
+// over the chunks (atomicMax).
+template <typename T, int NX, int NU, int PASS>
+__global__ void __launch_bounds__(scan::kTH) k_scan_finalize(BatchArgs a, ScanLayout SL,
+                                                             size_t sbase, int from1) {
+  constexpr bool FULL = PASS != 1;
+  using SM = FinSmem<T, NX, NU>;
+  constexpr bool FP32 = sizeof(T) == 4;
+  constexpr int n = NX, m = NU, nn = n * n, nm = n * m, mmm = m * m;
+  constexpr int LD = SM::LD, LD2 = SM::LD2, LDG = SM::LDG;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &s = *reinterpret_cast<SM *>(smem_raw);
+  const int tid = threadIdx.x;
+  const Inst I = get_inst(a, 0);
+  const int N = I.N, c = blockIdx.x;
+  const int s0 = c * SL.L, e0 = min(s0 + SL.L, N);
+  const T delta = (T)I.delta;
+  const float delta_up = __double2float_ru(I.delta);
+  const T *Sfin = reinterpret_cast<const T *>(I.ws + sbase + (from1 ? SL.S1 : SL.S0));
+  T *gPhi = reinterpret_cast<T *>(I.ws + sbase + SL.Phi) + (size_t)c * nn;
+  T *gW = reinterpret_cast<T *>(I.ws + I.L.W);
+  T *gK = reinterpret_cast<T *>(I.ws + I.L.K);
+  T *gGi = reinterpret_cast<T *>(I.ws + I.L.Gi);
+  T *gG = reinterpret_cast<T *>(I.ws + I.L.G);
+  uint8_t *gpd = reinterpret_cast<uint8_t *>(I.ws + I.L.G);  // plain FP64: G_i decisions
+  float *gAf = reinterpret_cast<float *>(I.ws + I.L.Af);
+  float *gBf = reinterpret_cast<float *>(I.ws + I.L.Bf);
+  float *gQf = reinterpret_cast<float *>(I.ws + I.L.Qf);
+  float *gMf = reinterpret_cast<float *>(I.ws + I.L.Mf);
+  float *gRf = reinterpret_cast<float *>(I.ws + I.L.Rf);
+  float *gcf = reinterpret_cast<float *>(I.ws + I.L.cf);
+  T *Phi = s.PhiA, *Phi2 = s.PhiB;
+  T *PstA = reinterpret_cast<T *>(I.ws + sbase + SL.PstA);
+  T *PstB = reinterpret_cast<T *>(I.ws + sbase + SL.PstB);
+
+  // P at the chunk's end: the P of suffix element c + 1 (for the last chunk
+  // the terminal element's Q_N), or in PASS 2 chunk c+1's P-only result
+  const T *Pend = (PASS == 2 && c + 1 < SL.C) ? PstA + (size_t)(c + 1) * nn
+                                              : Sfin + (size_t)(c + 1) * 3 * nn;
+  for (int e = tid; e < nn; e += blockDim.x) {
+    const int r = e / n, col = e - r * n;
+    s.P[r * LD + col] = Pend[e];
+    Phi[r * LD + col] = (r == col) ? (T)1 : (T)0;
+  }
+  int notpd = 0, singular = 0;
+
+  // state pivot of the P in s.P: W into s.W and gWk; returns bit0
+  auto state_pivot = [&](T *gWk) -> int {
+    __syncthreads();
+    if (tid == 0) {
+      s.bit = 1;
+      s.sing = 0;
+      s.pass = 1;
+    }
+    for (int e = tid; e < nn; e += blockDim.x) {
+      const int r = e / n, col = e - r * n;
+      const T pv = s.P[r * LD + col];
+      s.S2[r * LD2 + col] = (r == col ? (T)1 : (T)0) + delta * pv;
+      s.S2[r * LD2 + n + col] = pv;
+    }
+    __syncthreads();
+    if constexpr (!FULL) {
+      scan::gj<T>(n, 2 * n, s.S2, LD2, s.fcol, nullptr, nullptr);
+    } else if constexpr (FP32) {
+      // Gershgorin proof in FP32 with directed rounding; FP64 LDL^T otherwise
+      if (tid < n) {
+        float off = 0.f;
+        for (int j = 0; j < n; ++j)
+          if (j != tid) off = __fadd_ru(off, fabsf((float)s.P[tid * LD + j]));
+        if (!gershgorin_row_pd((float)s.P[tid * LD + tid], off, delta_up)) atomicAnd(&s.pass, 0);
+      }
+      __syncthreads();
+      if (!s.pass) {
+        for (int e = tid; e < nn; e += blockDim.x) {
+          const int r = e / n, col = e - r * n;
+          s.S64[e] = (r == col ? 1.0 : 0.0) + I.delta * widen((float)s.P[r * LD + col]);
+        }
+        for (int j = 0; j < n; ++j) {
+          __syncthreads();
+          const double d = s.S64[j * n + j];
+          if (tid == 0) {
+            if (!(d > 0.0)) s.bit = 0;
+            if (!finite_nonzero(d)) s.sing = 1;
+          }
+          const double rd = 1.0 / d;
+          const int r = n - j - 1;
+          __syncthreads();
+          for (int idx = tid; idx < r * (r + 1) / 2; idx += blockDim.x) {
+            int i, cc;
+            tri_decode(idx, i, cc);
+            i += j + 1;
+            cc += j + 1;
+            s.S64[i * n + cc] -= s.S64[i * n + j] * (s.S64[cc * n + j] * rd);
+          }
+        }
+        __syncthreads();
+      }
+      scan::gj<T>(n, 2 * n, s.S2, LD2, s.fcol, nullptr, nullptr);
+    } else {
+      scan::gj<T>(n, 2 * n, s.S2, LD2, s.fcol, &s.bit, &s.sing);
+    }
+    // W = right block, exactly symmetric (lower triangle mirrored)
+    for (int e = tid; e < nn; e += blockDim.x) {
+      const int r = e / n, col = e - r * n;
+      const int lo = r >= col ? r : col, hi = r >= col ? col : r;
+      const T w = s.S2[lo * LD2 + n + hi];
+      s.W[r * LD + col] = w;
+      if (FULL) gWk[e] = w;
+    }
+    __syncthreads();
+    if (s.sing) singular = 1;
+    return s.bit;
+  };
+
+  for (int i = e0 - 1; i >= s0; --i) {
+    const int bit0 = state_pivot(gW + (size_t)(i + 1) * nn);
+    // the stage's data (and its FP32 copies in the mixed path)
+    const double *Q = I.Q + (size_t)i * nn, *A = I.A + (size_t)i * nn;
+    const double *B = I.B + (size_t)i * nm, *M = I.M + (size_t)i * nm;
+    const double *R = I.R + (size_t)i * mmm;
+    for (int e = tid; e < nn; e += blockDim.x) {
+      const int r = e / n, col = e - r * n;
+      const T av = scan::to_T<T>(__ldg(A + e));
+      s.Q[r * LD + col] = scan::to_T<T>(__ldg(Q + (r <= col ? e : col * n + r)));
+      s.A[r * LD + col] = av;
+      if (FP32 && FULL) {
+        gAf[(size_t)i * nn + e] = (float)av;
+        gQf[(size_t)i * nn + e] = f64_to_f32_rz(__ldg(Q + e));
+      }
+    }
+    for (int e = tid; e < nm; e += blockDim.x) {
+      const T bv = scan::to_T<T>(__ldg(B + e)), mv = scan::to_T<T>(__ldg(M + e));
+      s.B[e] = bv;
+      s.M[e] = mv;
+      if (FP32 && FULL) {
+        gBf[(size_t)i * nm + e] = (float)bv;
+        gMf[(size_t)i * nm + e] = (float)mv;
+      }
+    }
+    for (int e = tid; e < mmm; e += blockDim.x) {
+      const int r = e / m, col = e - r * m;
+      s.GH[r * LDG + col] = scan::to_T<T>(__ldg(R + (r <= col ? e : col * m + r)));
+      s.GH[r * LDG + m + n + col] = (r == col) ? (T)1 : (T)0;
+      if (FP32 && FULL) gRf[(size_t)i * mmm + e] = f64_to_f32_rz(__ldg(R + e));
+    }
+    if (FP32 && FULL && tid < n)
+      gcf[(size_t)(i + 1) * n + tid] = f64_to_f32_rz(__ldg(I.c + (size_t)(i + 1) * n + tid));
+    __syncthreads();
+    // WA = W A, WB = W B
+    scan::mm<T, false, false>(n, n, n, s.WA, LD, s.W, LD, s.A, LD, nullptr, 0, (T)1);
+    scan::mm<T, false, false>(n, m, n, s.WB, m, s.W, LD, s.B, m, nullptr, 0, (T)1);
+    __syncthreads();
+    // G = R + B^T WB, H = M^T + B^T WA
+    scan::mm<T, true, false>(m, m, n, s.GH, LDG, s.B, m, s.WB, m, s.GH, LDG, (T)1);
+    scan::mm<T, true, false>(m, n, n, s.H, n, s.B, m, s.WA, LD, nullptr, 0, (T)1);
+    __syncthreads();
+    for (int e = tid; e < m * n; e += blockDim.x) {
+      const int r = e / n, col = e - r * n;
+      const T h = s.H[e] + s.M[col * m + r];
+      s.H[e] = h;
+      s.GH[r * LDG + m + col] = h;
+    }
+    __syncthreads();
+    if (FP32 && FULL)
+      for (int e = tid; e < mmm; e += blockDim.x) {
+        const int r = e / m, col = e - r * m;
+        gG[(size_t)i * mmm + e] = s.GH[r * LDG + col];
+      }
+    if (tid == 0) {
+      s.bit = 1;
+      s.sing = 0;
+    }
+    scan::gj<T>(m, 2 * m + n, s.GH, LDG, s.fcol, (FP32 || !FULL) ? nullptr : &s.bit,
+                (FP32 || !FULL) ? nullptr : &s.sing);
+    const int bit1 = s.bit;
+    if (!FP32 && s.sing) singular = 1;
+    // K = -G^{-1} H, G^{-1}
+    for (int e = tid; e < m * n; e += blockDim.x) {
+      const int r = e / n, col = e - r * n;
+      const T kv = -s.GH[r * LDG + m + col];
+      s.K[e] = kv;
+      if (FULL) gK[(size_t)i * nm + e] = kv;
+    }
+    if (FULL)
+      for (int e = tid; e < mmm; e += blockDim.x) {
+        const int r = e / m, col = e - r * m;
+        gGi[(size_t)i * mmm + e] = s.GH[r * LDG + m + n + col];
+      }
+    __syncthreads();
+    // P_i = Q + A^T WA + H^T K (exactly symmetric), A + B K
+    scan::mm<T, true, false>(n, n, n, s.T1, LD, s.A, LD, s.WA, LD, s.Q, LD, (T)1);
+    scan::mm<T, false, false>(n, n, m, s.ABK, LD, s.B, m, s.K, n, s.A, LD, (T)1);
+    __syncthreads();
+    scan::mm<T, true, false>(n, n, m, s.Ft, LD, s.H, n, s.K, n, s.T1, LD, (T)1);
+    __syncthreads();
+    for (int e = tid; e < nn; e += blockDim.x) {
+      const int r = e / n, col = e - r * n;
+      const int lo = r >= col ? r : col, hi = r >= col ? col : r;
+      s.P[r * LD + col] = s.Ft[lo * LD + hi];
+    }
+    __syncthreads();
+    if constexpr (FULL) {
+      // Ft = (I - delta W)(A + B K) = F_i^T;  Phi <- F_i Phi = Ft^T Phi
+      scan::mm<T, false, false>(n, n, n, s.Ft, LD, s.W, LD, s.ABK, LD, s.ABK, LD, -delta);
+      __syncthreads();
+      scan::mm<T, true, false>(n, n, n, Phi2, LD, s.Ft, LD, Phi, LD, nullptr, 0, (T)1);
+      T *tmp = Phi;
+      Phi = Phi2;
+      Phi2 = tmp;
+    }
+    if (FULL && tid == 0) {
+      I.flags[i + 1] = (uint8_t)(bit0 | (i + 1 == N ? 2 : 0));
+      if (!FP32) gpd[i] = (uint8_t)bit1;
+      if (!bit0 || (!FP32 && !bit1)) notpd = 1;
+    }
+    __syncthreads();
+  }
+  if constexpr (!FULL) {
+    for (int e = tid; e < nn; e += blockDim.x) {
+      const int r = e / n, col = e - r * n;
+      PstA[(size_t)c * nn + e] = s.P[r * LD + col];
+    }
+    return;
+  }
+  for (int e = tid; e < nn; e += blockDim.x) {
+    const int r = e / n, col = e - r * n;
+    gPhi[e] = Phi[r * LD + col];
+    PstB[(size_t)c * nn + e] = s.P[r * LD + col];
+  }
+  if (c == 0) {
+    const int bit0 = state_pivot(gW);
+    if (FP32 && tid < n) gcf[tid] = f64_to_f32_rz(__ldg(I.c + tid));
+    if (tid == 0) {
+      I.flags[0] = (uint8_t)bit0;
+      if (!bit0) notpd = 1;
+    }
+  }
+  if (tid == 0) {
+    const int st = singular ? RLQR_ERR_SINGULAR : (notpd ? RLQR_NOT_PD : RLQR_OK);
+    atomicMax(&I.st->pivot_status, st);
+  }
+}
+
+// Plain FP64 path: bit1 of flags[i] from the stored decisions of the G_i.
+static __global__ void k_scan_flags(BatchArgs a) {
+  const Inst I = get_inst(a, 0);
+  const uint8_t *gpd = reinterpret_cast<const uint8_t *>(I.ws + I.L.G);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I.N; i += gridDim.x * blockDim.x)
+    I.flags[i] = (uint8_t)(I.flags[i] | (gpd[i] << 1));
+}
+
+}  // namespace rlqr

@@ -18,9 +18,9 @@ REL_TOL = 1e-9
 FWD_TOL = {rlqr.RLQR_FP64: 1e-8, rlqr.RLQR_MIXED: 1e-6}
 
 
-def solve_single(p, prec, max_refine=3, factor_only=False, tol=1e-9):
+def solve_single(p, prec, max_refine=3, factor_only=False, tol=1e-9, algo=rlqr.RLQR_ALGO_AUTO):
     dp = rlqr.DeviceProblem.from_host(p)
-    opts = rlqr.make_opts(prec, tol=tol, max_refine=max_refine)
+    opts = rlqr.make_opts(prec, algo=algo, tol=tol, max_refine=max_refine)
     nb = rlqr.rlqr_workspace_bytes(p.N, p.n, p.m, opts)
     ws = rlqr.alloc_workspace(nb)
     flags = torch.zeros(p.N + 1, dtype=torch.uint8, device="cuda")

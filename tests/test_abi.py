@@ -41,7 +41,16 @@ def test_host_side_validation_and_sizes():
     a = rlqr.rlqr_workspace_bytes(64, 4, 2, o)
     om = rlqr.make_opts(rlqr.RLQR_MIXED)
     b = rlqr.rlqr_workspace_bytes(64, 4, 2, om)
-    assert a > 0 and b > 0 and b < a and a % 256 == 0
+    assert a > 0 and b > 0 and a % 256 == 0 and b % 256 == 0
+    # the scan path adds its chunk arrays; AUTO sizes for the scan from N = 4096 on
+    seq = rlqr.make_opts(rlqr.RLQR_FP64, algo=rlqr.RLQR_ALGO_SEQ)
+    scan = rlqr.make_opts(rlqr.RLQR_FP64, algo=rlqr.RLQR_ALGO_SCAN)
+    assert rlqr.rlqr_workspace_bytes(64, 4, 2, scan) > rlqr.rlqr_workspace_bytes(64, 4, 2, seq)
+    assert rlqr.rlqr_workspace_bytes(64, 4, 2, o) == rlqr.rlqr_workspace_bytes(64, 4, 2, seq)
+    assert (rlqr.rlqr_workspace_bytes(4096, 32, 8, o) ==
+            rlqr.rlqr_workspace_bytes(4096, 32, 8, scan))
+    assert (rlqr.rlqr_workspace_bytes(4096, 5, 2, o) ==
+            rlqr.rlqr_workspace_bytes(4096, 5, 2, seq))   # no scan kernel for (5, 2)
     bad = rlqr.make_opts(rlqr.RLQR_FP64, tol=-1.0)
     assert rlqr.rlqr_workspace_bytes(8, 4, 2, bad) == 0
     # invalid problem: rejected before any device work
