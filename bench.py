@@ -14,6 +14,13 @@ is timed beside it, and the FP64 CPU oracle is the CPU baseline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --profile-instances K   # profiling case, no bench line
+    python bench.py --long-horizon          # the single long-horizon instance
+
+--long-horizon measures the other workload of the path: one instance with
+n_x = 32, n_u = 8, N = 65536 (delta = 1e-7, rho(A) = 0.99, Q and R with
+condition number 1e4), rlqr_factor + rlqr_solve with the associative scan in
+mixed precision (FP64 residual and refinement), beside the plain FP64
+sequential recursion on the GPU.
 
 Multi-GPU (torchrun): every rank solves its own copy of the batch (weak
 scaling, no data-path collective); value = all ranks' stage-solves / max time.
@@ -222,6 +229,73 @@ def run_profile_case(args):
           f"iters {it.max().item()}", flush=True)
 
 
+def run_long_horizon(args):
+    """One JSON line for the long-horizon instance (stage-solves/s of factor +
+    solve + refinement; SCAN mixed vs SEQ FP64 on the GPU)."""
+    import torch
+    from paper_2509_16370_b300 import inputs, rlqr
+    p = inputs.workload3()
+    dp = rlqr.DeviceProblem.from_host(p)
+    N, n, m = p.N, p.n, p.m
+
+    def make(prec, algo):
+        opts = rlqr.make_opts(prec, algo=algo, tol=TOL, max_refine=3)
+        ws = rlqr.alloc_workspace(rlqr.rlqr_workspace_bytes(N, n, m, opts))
+        bufs = dict(flags=torch.zeros(N + 1, dtype=torch.uint8, device="cuda"),
+                    x=torch.zeros(N + 1, n, dtype=torch.float64, device="cuda"),
+                    u=torch.zeros(N, m, dtype=torch.float64, device="cuda"),
+                    y=torch.zeros(N + 1, n, dtype=torch.float64, device="cuda"),
+                    rel=torch.zeros(1, dtype=torch.float64, device="cuda"),
+                    it=torch.zeros(1, dtype=torch.int32, device="cuda"),
+                    st=torch.zeros(1, dtype=torch.int32, device="cuda"))
+
+        def step():
+            rlqr.rlqr_factor(dp, opts, ws, bufs["flags"], bufs["st"])
+            rlqr.rlqr_solve(dp, opts, ws, bufs["x"], bufs["u"], bufs["y"], bufs["rel"],
+                            bufs["it"], bufs["st"])
+        return step, bufs
+
+    def timed(step, steps, warmup):
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    step, bufs = make(rlqr.RLQR_MIXED, rlqr.RLQR_ALGO_SCAN)
+    rlqr.rlqr_instrument(True)
+    with ClockSampler(0) as clk:
+        ms = timed(step, args.steps, args.warmup)
+    report = rlqr.rlqr_instrument_report()
+    rlqr.rlqr_instrument(False)
+    rel = float(bufs["rel"].item())
+    step64, bufs64 = make(rlqr.RLQR_FP64, rlqr.RLQR_ALGO_SEQ)
+    ms64 = timed(step64, 1, 1)
+    value = N / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": "stage-solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64 (FP32 scan; FP64 certificate, residual, correction)",
+            "data": "synthetic",
+            "config": {"workload": "one dual-regularized LQR, n_x=32, n_u=8, N=65536, delta=1e-7, "
+                                   "rho(A)=0.99, cond(Q)=cond(R)=1e4", "algo": "scan",
+                       "chunks": int((N + max(8, (N + 443) // 444) - 1) // max(8, (N + 443) // 444)),
+                       "l2": "inputs 1.4 GB > L2 (no flush needed)"},
+            "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in report.items()},
+            "accuracy": {"rel_resid": rel, "all_le_tol": rel <= TOL,
+                         "iters": int(bufs["it"].item()), "status": int(bufs["st"].item())},
+            "fp64_plain_seq": {"value": N / (ms64 / 1e3), "ms_per_step": ms64,
+                               "rel_resid": None},
+            "speedup_vs_fp64_plain": ms64 / ms,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     rank, world, local = _dist()
@@ -354,6 +428,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-instances", type=int, default=0,
                     help="profiling case: the mixed solve on the first K instances only")
+    ap.add_argument("--long-horizon", action="store_true",
+                    help="the single long-horizon instance (associative scan)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -361,6 +437,8 @@ def main():
         run_reference(args)
     elif args.profile_instances > 0:
         run_profile_case(args)
+    elif args.long_horizon:
+        run_long_horizon(args)
     else:
         run_ours(args)
 

@@ -100,3 +100,14 @@ def test_long_horizon_n32(prec):
     out = solve_single(p, prec, algo=SCAN)
     assert out["status"] in (rlqr.RLQR_OK, rlqr.RLQR_NOT_PD)
     check_against_oracle(p, out, prec)
+
+
+def test_long_horizon_full_size_mixed():
+    """The long-horizon workload at full size (n=32, m=8, N=65536, 444
+    chunks): mixed-precision scan, one refinement pass, flags identical to
+    the oracle's and the oracle's backward error of the solution <= 1e-9."""
+    p = inputs.workload3()
+    out = solve_single(p, rlqr.RLQR_MIXED, algo=SCAN)
+    assert out["status"] in (rlqr.RLQR_OK, rlqr.RLQR_NOT_PD)
+    assert out["rel"] <= REL_TOL
+    check_against_oracle(p, out, rlqr.RLQR_MIXED)
