@@ -96,53 +96,140 @@ namespace scan {
 
 constexpr int kTH = 256;  // threads of the scan CTAs
 
-// D[r][c] = alpha * sum_k op(A)[r][k] op(B)[k][c] (+ Add[r][c]); op = transpose
-// when TA / TB.  D must not alias A or B (it may alias Add).  No barrier.
-template <typename T, bool TA, bool TB>
-__device__ __forceinline__ void mm(int R, int Cc, int K, T *D, int ldd, const T *A, int lda,
-                                   const T *B, int ldb, const T *Add, int ldadd, T alpha) {
-  for (int e = threadIdx.x; e < R * Cc; e += blockDim.x) {
-    const int r = e / Cc, c = e - r * Cc;
-    T acc = 0;
-#pragma unroll 4
-    for (int k = 0; k < K; ++k) {
-      const T a = TA ? A[k * lda + r] : A[r * lda + k];
-      const T b = TB ? B[c * ldb + k] : B[k * ldb + c];
-      acc = fma(a, b, acc);
+// Compile-time-size product with 2x2 register tiles: D (R x C) = alpha *
+// op(A) op(B) (+ Add), K inner; R, C even; leading dimensions even so that
+// pairs load as one 8-byte access.  FP32 pairs use fma.rn.f32x2.  D must not
+// alias A or B (it may alias Add).  No barrier.
+template <typename T, int R, int C, int K, bool TA, bool TB>
+__device__ __forceinline__ void mmt(T *D, int ldd, const T *A, int lda, const T *B, int ldb,
+                                    const T *Add, int ldadd, T alpha) {
+  static_assert(R % 2 == 0 && C % 2 == 0, "even tile dimensions");
+  constexpr int TC = C / 2, NT = (R / 2) * TC;
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+    const int tr = t / TC, tc = t - tr * TC, r0 = 2 * tr, c0 = 2 * tc;
+    if constexpr (sizeof(T) == 4) {
+      float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+#pragma unroll 8
+      for (int k = 0; k < K; ++k) {
+        float x0, x1;
+        float2 y;
+        if (TA) {
+          const float2 xa = *reinterpret_cast<const float2 *>(A + k * lda + r0);
+          x0 = xa.x;
+          x1 = xa.y;
+        } else {
+          x0 = A[r0 * lda + k];
+          x1 = A[(r0 + 1) * lda + k];
+        }
+        if (TB) {
+          y = make_float2(B[c0 * ldb + k], B[(c0 + 1) * ldb + k]);
+        } else {
+          y = *reinterpret_cast<const float2 *>(B + k * ldb + c0);
+        }
+        s0 = fma2(bcast2(x0), y, s0);
+        s1 = fma2(bcast2(x1), y, s1);
+      }
+      const float al = (float)alpha;
+      float2 o0 = make_float2(s0.x * al, s0.y * al), o1 = make_float2(s1.x * al, s1.y * al);
+      if (Add) {
+        o0.x += Add[r0 * ldadd + c0];
+        o0.y += Add[r0 * ldadd + c0 + 1];
+        o1.x += Add[(r0 + 1) * ldadd + c0];
+        o1.y += Add[(r0 + 1) * ldadd + c0 + 1];
+      }
+      *reinterpret_cast<float2 *>(D + r0 * ldd + c0) = o0;
+      *reinterpret_cast<float2 *>(D + (r0 + 1) * ldd + c0) = o1;
+    } else {
+      T a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+#pragma unroll 8
+      for (int k = 0; k < K; ++k) {
+        const T x0 = TA ? A[k * lda + r0] : A[r0 * lda + k];
+        const T x1 = TA ? A[k * lda + r0 + 1] : A[(r0 + 1) * lda + k];
+        const T y0 = TB ? B[c0 * ldb + k] : B[k * ldb + c0];
+        const T y1 = TB ? B[(c0 + 1) * ldb + k] : B[k * ldb + c0 + 1];
+        a00 = fma(x0, y0, a00);
+        a01 = fma(x0, y1, a01);
+        a10 = fma(x1, y0, a10);
+        a11 = fma(x1, y1, a11);
+      }
+      T o00 = a00 * alpha, o01 = a01 * alpha, o10 = a10 * alpha, o11 = a11 * alpha;
+      if (Add) {
+        o00 += Add[r0 * ldadd + c0];
+        o01 += Add[r0 * ldadd + c0 + 1];
+        o10 += Add[(r0 + 1) * ldadd + c0];
+        o11 += Add[(r0 + 1) * ldadd + c0 + 1];
+      }
+      D[r0 * ldd + c0] = o00;
+      D[r0 * ldd + c0 + 1] = o01;
+      D[(r0 + 1) * ldd + c0] = o10;
+      D[(r0 + 1) * ldd + c0 + 1] = o11;
     }
-    acc *= alpha;
-    if (Add) acc += Add[r * ldadd + c];
-    D[r * ldd + c] = acc;
   }
 }
 
-// Gauss-Jordan without pivoting on the R x Wd matrix M (left block R x R):
-// afterwards the right block holds (left)^{-1} (right).  Records the pivots'
-// decisions in *bit (all pivots > 0) and *sing (a zero or non-finite pivot)
-// when the pointers are given (thread 0 writes them).  Barriers inside;
-// `fcol` is R entries of scratch.
-template <typename T>
-__device__ __forceinline__ void gj(int R, int Wd, T *M, int ld, T *fcol, int *bit, int *sing) {
-  const int tid = threadIdx.x;
+// Threads per row of gjr: a power of two <= 32 (a row's threads share a warp).
+template <int R, int TH>
+constexpr int gj_tpr() {
+  int t = 1;
+  while (t * 2 <= 32 && t * 2 * R <= TH) t *= 2;
+  return t;
+}
+
+// Gauss-Jordan without pivoting on the R x W matrix M (left block R x R),
+// register-resident: thread (i, g) holds columns g, g + TPR, ... of row i.
+// Step j: the threads of row j publish it in `rowbuf` (2 W entries,
+// double-buffered), one barrier, and every row takes its own entry of column
+// j from the thread holding it by a shuffle.  Afterwards the right block of M
+// holds (left)^{-1} (right).  Pivot decisions into *bit / *sing (thread 0)
+// when given.  The caller puts a barrier before (M written by others).
+template <typename T, int R, int W, int TH>
+__device__ __forceinline__ void gjr(T *M, int ld, T *rowbuf, int *bit, int *sing) {
+  constexpr int TPR = gj_tpr<R, TH>(), CPT = (W + TPR - 1) / TPR;
+  const int tid = threadIdx.x, i = tid / TPR, g = tid - (tid / TPR) * TPR;
+  const bool act = i < R;
+  const int lane = tid & 31, base = lane & ~(TPR - 1);
+  T v[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int c = g + k * TPR;
+    v[k] = (act && c < W) ? M[i * ld + c] : (T)0;
+  }
+#pragma unroll
   for (int j = 0; j < R; ++j) {
+    T *rb = rowbuf + (j & 1) * W;
+    if (act && i == j) {
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        const int c = g + k * TPR;
+        if (c < W) rb[c] = v[k];
+      }
+    }
     __syncthreads();
-    const T d = M[j * ld + j];
+    const T d = rb[j];
     if (tid == 0 && bit) {
       if (!((double)d > 0.0)) *bit = 0;
       if (!finite_nonzero((double)d)) *sing = 1;
     }
-    if (tid < R) fcol[tid] = (tid == j) ? (T)0 : M[tid * ld + j] * recip_pivot(d);
-    __syncthreads();
-    const int w = Wd - j - 1;
-    for (int e = tid; e < R * w; e += blockDim.x) {
-      const int i = e / w, c = j + 1 + (e - i * w);
-      if (i != j) M[i * ld + c] = fma(-fcol[i], M[j * ld + c], M[i * ld + c]);
+    const T f = __shfl_sync(0xffffffffu, v[j / TPR], base | (j % TPR)) * recip_pivot(d);
+    if (act && i != j) {
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        const int c = g + k * TPR;
+        if (c > j && c < W) v[k] = fma(-f, rb[c], v[k]);
+      }
     }
   }
+  // scale the right block by 1 / d_i and store it
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int c = g + k * TPR;
+    if (act && c < W) M[i * ld + c] = v[k];
+  }
   __syncthreads();
-  for (int e = tid; e < R * (Wd - R); e += blockDim.x) {
-    const int i = e / (Wd - R), c = R + (e - i * (Wd - R));
-    M[i * ld + c] *= recip_pivot(M[i * ld + i]);
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int c = g + k * TPR;
+    if (act && c >= R && c < W) M[i * ld + c] = v[k] * recip_pivot(M[i * ld + i]);
   }
   __syncthreads();
 }
@@ -164,7 +251,7 @@ __device__ __forceinline__ T to_T(double v) {
 // Shared memory of the reduce / level kernels (row stride n + 1).
 template <typename T, int NX, int NU>
 struct CombSmem {
-  static constexpr int LD = NX + 1, LD3 = 3 * NX + 1, LDR = NU + 2 * NX + 1;
+  static constexpr int LD = NX + 2, LD3 = 3 * NX + 2, LDR = NU + 2 * NX + 2;  // even strides
   T P1[NX * LD], A1[NX * LD], C1[NX * LD];   // earlier element
   T P2[NX * LD], A2[NX * LD], C2[NX * LD];   // later element (the accumulator)
   T Pn[NX * LD], An[NX * LD], Cn[NX * LD];   // result
@@ -172,7 +259,7 @@ struct CombSmem {
   T T1[NX * LD], T2[NX * LD];
   T Q[NX * LD], A[NX * LD], B[NX * NU], M[NX * NU];
   T RX[NU * LDR];                            // [R | M^T | B^T]
-  T fcol[NX > NU ? NX : NU];
+  T rowbuf[2 * (3 * NX + 2)];                // pivot rows of the eliminations
 };
 
 // The stage element (P, A, C)_{i->i+1} into (P1, A1, C1); eq. lqr-gpu-init-running.
@@ -201,11 +288,12 @@ __device__ void stage_element(const Inst &I, int i, CombSmem<T, NX, NU> &s) {
     const int r = e / m, c = e - r * m;
     s.RX[r * LDR + c] = to_T<T>(__ldg(R + (r <= c ? e : c * m + r)));
   }
-  gj<T>(m, m + 2 * n, s.RX, LDR, s.fcol, nullptr, nullptr);  // R^{-1} [M^T | B^T]
+  __syncthreads();
+  gjr<T, NU, NU + 2 * NX, kTH>(s.RX, LDR, s.rowbuf, nullptr, nullptr);  // R^{-1} [M^T | B^T]
   // P = Q - M (R^{-1} M^T), A = A - B (R^{-1} M^T), C = delta I + B (R^{-1} B^T)
-  mm<T, false, false>(n, n, m, s.P1, LD, s.M, m, s.RX + m, LDR, s.Q, LD, (T)-1);
-  mm<T, false, false>(n, n, m, s.A1, LD, s.B, m, s.RX + m, LDR, s.A, LD, (T)-1);
-  mm<T, false, false>(n, n, m, s.C1, LD, s.B, m, s.RX + m + n, LDR, nullptr, 0, (T)1);
+  mmt<T, NX, NX, NU, false, false>(s.P1, LD, s.M, m, s.RX + m, LDR, s.Q, LD, (T)-1);
+  mmt<T, NX, NX, NU, false, false>(s.A1, LD, s.B, m, s.RX + m, LDR, s.A, LD, (T)-1);
+  mmt<T, NX, NX, NU, false, false>(s.C1, LD, s.B, m, s.RX + m + n, LDR, nullptr, 0, (T)1);
   __syncthreads();
   const T delta = (T)I.delta;
   for (int r = tid; r < n; r += blockDim.x) s.C1[r * LD + r] += delta;
@@ -221,7 +309,7 @@ __device__ void combine(CombSmem<T, NX, NU> &s) {
   constexpr int n = NX, LD = CombSmem<T, NX, NU>::LD, LD3 = CombSmem<T, NX, NU>::LD3;
   const int tid = threadIdx.x;
   __syncthreads();
-  mm<T, false, false>(n, n, n, s.G3, LD3, s.C1, LD, s.P2, LD, nullptr, 0, (T)1);  // C1 P2
+  mmt<T, NX, NX, NX, false, false>(s.G3, LD3, s.C1, LD, s.P2, LD, nullptr, 0, (T)1);  // C1 P2
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int r = e / n, c = e - r * n;
     s.G3[r * LD3 + n + c] = s.A1[r * LD + c];
@@ -229,14 +317,15 @@ __device__ void combine(CombSmem<T, NX, NU> &s) {
   }
   __syncthreads();
   for (int r = tid; r < n; r += blockDim.x) s.G3[r * LD3 + r] += (T)1;
-  gj<T>(n, 3 * n, s.G3, LD3, s.fcol, nullptr, nullptr);   // XA = T A1, XC = T C1
-  const T *XA = s.G3 + n, *XC = s.G3 + 2 * n;
-  mm<T, false, false>(n, n, n, s.An, LD, s.A2, LD, XA, LD3, nullptr, 0, (T)1);   // A2 XA
-  mm<T, false, false>(n, n, n, s.T1, LD, s.A2, LD, XC, LD3, nullptr, 0, (T)1);   // A2 XC
-  mm<T, false, false>(n, n, n, s.T2, LD, s.P2, LD, XA, LD3, nullptr, 0, (T)1);   // P2 XA
   __syncthreads();
-  mm<T, false, true>(n, n, n, s.Cn, LD, s.T1, LD, s.A2, LD, s.C2, LD, (T)1);     // (A2 XC) A2^T + C2
-  mm<T, true, false>(n, n, n, s.Pn, LD, s.A1, LD, s.T2, LD, s.P1, LD, (T)1);     // A1^T (P2 XA) + P1
+  gjr<T, NX, 3 * NX, kTH>(s.G3, LD3, s.rowbuf, nullptr, nullptr);   // XA = T A1, XC = T C1
+  const T *XA = s.G3 + n, *XC = s.G3 + 2 * n;
+  mmt<T, NX, NX, NX, false, false>(s.An, LD, s.A2, LD, XA, LD3, nullptr, 0, (T)1);   // A2 XA
+  mmt<T, NX, NX, NX, false, false>(s.T1, LD, s.A2, LD, XC, LD3, nullptr, 0, (T)1);   // A2 XC
+  mmt<T, NX, NX, NX, false, false>(s.T2, LD, s.P2, LD, XA, LD3, nullptr, 0, (T)1);   // P2 XA
+  __syncthreads();
+  mmt<T, NX, NX, NX, false, true>(s.Cn, LD, s.T1, LD, s.A2, LD, s.C2, LD, (T)1);     // (A2 XC) A2^T + C2
+  mmt<T, NX, NX, NX, true, false>(s.Pn, LD, s.A1, LD, s.T2, LD, s.P1, LD, (T)1);     // A1^T (P2 XA) + P1
   __syncthreads();
   mirror_lower<T>(n, s.Pn, LD);
   mirror_lower<T>(n, s.Cn, LD);
@@ -344,13 +433,13 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_level(BatchArgs a, ScanLayou
 // Shared memory of the finalize kernel (row stride n + 1).
 template <typename T, int NX, int NU>
 struct FinSmem {
-  static constexpr int LD = NX + 1, LD2 = 2 * NX + 1, LDG = 2 * NU + NX + 1;
+  static constexpr int LD = NX + 2, LD2 = 2 * NX + 2, LDG = 2 * NU + NX + 2;  // even strides
   T P[NX * LD], W[NX * LD], Q[NX * LD], A[NX * LD], WA[NX * LD], ABK[NX * LD], Ft[NX * LD];
   T T1[NX * LD], PhiA[NX * LD], PhiB[NX * LD];
   T S2[NX * LD2];                  // [I + delta P | P]
   T B[NX * NU], M[NX * NU], WB[NX * NU], K[NU * NX], H[NU * NX];
   T GH[NU * LDG];                  // [G | H | I]
-  T fcol[NX];
+  T rowbuf[2 * (2 * NX + 2 * NU + 2)];
   double S64[NX * NX];             // FP64 LDL^T of I + delta P (FP32 certificate fallback)
   int bit, sing, pass;
 };
@@ -426,7 +515,7 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_finalize(BatchArgs a, ScanLa
     }
     __syncthreads();
     if constexpr (!FULL) {
-      scan::gj<T>(n, 2 * n, s.S2, LD2, s.fcol, nullptr, nullptr);
+      scan::gjr<T, NX, 2 * NX, scan::kTH>(s.S2, LD2, s.rowbuf, nullptr, nullptr);
     } else if constexpr (FP32) {
       // Gershgorin proof in FP32 with directed rounding; FP64 LDL^T otherwise
       if (tid < n) {
@@ -461,9 +550,9 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_finalize(BatchArgs a, ScanLa
         }
         __syncthreads();
       }
-      scan::gj<T>(n, 2 * n, s.S2, LD2, s.fcol, nullptr, nullptr);
+      scan::gjr<T, NX, 2 * NX, scan::kTH>(s.S2, LD2, s.rowbuf, nullptr, nullptr);
     } else {
-      scan::gj<T>(n, 2 * n, s.S2, LD2, s.fcol, &s.bit, &s.sing);
+      scan::gjr<T, NX, 2 * NX, scan::kTH>(s.S2, LD2, s.rowbuf, &s.bit, &s.sing);
     }
     // W = right block, exactly symmetric (lower triangle mirrored)
     for (int e = tid; e < nn; e += blockDim.x) {
@@ -513,12 +602,12 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_finalize(BatchArgs a, ScanLa
       gcf[(size_t)(i + 1) * n + tid] = f64_to_f32_rz(__ldg(I.c + (size_t)(i + 1) * n + tid));
     __syncthreads();
     // WA = W A, WB = W B
-    scan::mm<T, false, false>(n, n, n, s.WA, LD, s.W, LD, s.A, LD, nullptr, 0, (T)1);
-    scan::mm<T, false, false>(n, m, n, s.WB, m, s.W, LD, s.B, m, nullptr, 0, (T)1);
+    scan::mmt<T, NX, NX, NX, false, false>(s.WA, LD, s.W, LD, s.A, LD, nullptr, 0, (T)1);
+    scan::mmt<T, NX, NU, NX, false, false>(s.WB, m, s.W, LD, s.B, m, nullptr, 0, (T)1);
     __syncthreads();
     // G = R + B^T WB, H = M^T + B^T WA
-    scan::mm<T, true, false>(m, m, n, s.GH, LDG, s.B, m, s.WB, m, s.GH, LDG, (T)1);
-    scan::mm<T, true, false>(m, n, n, s.H, n, s.B, m, s.WA, LD, nullptr, 0, (T)1);
+    scan::mmt<T, NU, NU, NX, true, false>(s.GH, LDG, s.B, m, s.WB, m, s.GH, LDG, (T)1);
+    scan::mmt<T, NU, NX, NX, true, false>(s.H, n, s.B, m, s.WA, LD, nullptr, 0, (T)1);
     __syncthreads();
     for (int e = tid; e < m * n; e += blockDim.x) {
       const int r = e / n, col = e - r * n;
@@ -536,8 +625,10 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_finalize(BatchArgs a, ScanLa
       s.bit = 1;
       s.sing = 0;
     }
-    scan::gj<T>(m, 2 * m + n, s.GH, LDG, s.fcol, (FP32 || !FULL) ? nullptr : &s.bit,
-                (FP32 || !FULL) ? nullptr : &s.sing);
+    __syncthreads();
+    scan::gjr<T, NU, 2 * NU + NX, scan::kTH>(s.GH, LDG, s.rowbuf,
+                                             (FP32 || !FULL) ? nullptr : &s.bit,
+                                             (FP32 || !FULL) ? nullptr : &s.sing);
     const int bit1 = s.bit;
     if (!FP32 && s.sing) singular = 1;
     // K = -G^{-1} H, G^{-1}
@@ -554,10 +645,10 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_finalize(BatchArgs a, ScanLa
       }
     __syncthreads();
     // P_i = Q + A^T WA + H^T K (exactly symmetric), A + B K
-    scan::mm<T, true, false>(n, n, n, s.T1, LD, s.A, LD, s.WA, LD, s.Q, LD, (T)1);
-    scan::mm<T, false, false>(n, n, m, s.ABK, LD, s.B, m, s.K, n, s.A, LD, (T)1);
+    scan::mmt<T, NX, NX, NX, true, false>(s.T1, LD, s.A, LD, s.WA, LD, s.Q, LD, (T)1);
+    scan::mmt<T, NX, NX, NU, false, false>(s.ABK, LD, s.B, m, s.K, n, s.A, LD, (T)1);
     __syncthreads();
-    scan::mm<T, true, false>(n, n, m, s.Ft, LD, s.H, n, s.K, n, s.T1, LD, (T)1);
+    scan::mmt<T, NX, NX, NU, true, false>(s.Ft, LD, s.H, n, s.K, n, s.T1, LD, (T)1);
     __syncthreads();
     for (int e = tid; e < nn; e += blockDim.x) {
       const int r = e / n, col = e - r * n;
@@ -567,9 +658,9 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_finalize(BatchArgs a, ScanLa
     __syncthreads();
     if constexpr (FULL) {
       // Ft = (I - delta W)(A + B K) = F_i^T;  Phi <- F_i Phi = Ft^T Phi
-      scan::mm<T, false, false>(n, n, n, s.Ft, LD, s.W, LD, s.ABK, LD, s.ABK, LD, -delta);
+      scan::mmt<T, NX, NX, NX, false, false>(s.Ft, LD, s.W, LD, s.ABK, LD, s.ABK, LD, -delta);
       __syncthreads();
-      scan::mm<T, true, false>(n, n, n, Phi2, LD, s.Ft, LD, Phi, LD, nullptr, 0, (T)1);
+      scan::mmt<T, NX, NX, NX, true, false>(Phi2, LD, s.Ft, LD, Phi, LD, nullptr, 0, (T)1);
       T *tmp = Phi;
       Phi = Phi2;
       Phi2 = tmp;
