@@ -39,11 +39,61 @@ __device__ __forceinline__ T data_at(const double *g64, const float *g32, size_t
 
 template <typename T, int NX, int NU>
 struct VecSmem {
-  T W[NX * NX], A[NX * NX], B[NX * NU], K[NU * NX], G[NU * NU];
-  T Q[NX * NX], M[NX * NU], R[NU * NU];
-  T p[NX], pn[NX], g[NX], h[NU], v[NX], x[NX], u[NU];
-  T dy[NX], dyn[NX], dxn[NX];
+  alignas(16) T W[NX * NX];
+  alignas(16) T A[NX * NX];
+  alignas(16) T B[NX * NU];
+  alignas(16) T K[NU * NX];
+  alignas(16) T G[NU * NU];
+  alignas(16) T Q[NX * NX];
+  alignas(16) T M[NX * NU];
+  alignas(16) T R[NU * NU];
+  alignas(16) T p[NX];
+  alignas(16) T pn[NX];
+  alignas(16) T g[NX];
+  alignas(16) T h[NU];
+  alignas(16) T v[NX];
+  alignas(16) T x[NX];
+  alignas(16) T u[NU];
+  alignas(16) T dy[NX];
+  alignas(16) T dyn[NX];
+  alignas(16) T dxn[NX];
 };
+
+// The data array the vector passes read: the FP32 copy (mixed) or FP64 array.
+template <typename T>
+__device__ __forceinline__ const T *data_ptr(const double *g64, const float *g32) {
+  if constexpr (sizeof(T) == 4) {
+    return g32;
+  } else {
+    return g64;
+  }
+}
+
+// sum_l a[l] b[l] over contiguous rows (two accumulators)
+template <typename T, int L>
+__device__ __forceinline__ T dotc(const T *a, const T *b) {
+  T s0 = 0, s1 = 0;
+#pragma unroll
+  for (int l = 0; l + 1 < L; l += 2) {
+    s0 = fma(a[l], b[l], s0);
+    s1 = fma(a[l + 1], b[l + 1], s1);
+  }
+  if (L & 1) s0 = fma(a[L - 1], b[L - 1], s0);
+  return s0 + s1;
+}
+
+// sum_l a[l * stride] b[l] (a column of a row-major matrix; two accumulators)
+template <typename T, int L>
+__device__ __forceinline__ T dots(const T *a, int stride, const T *b) {
+  T s0 = 0, s1 = 0;
+#pragma unroll
+  for (int l = 0; l + 1 < L; l += 2) {
+    s0 = fma(a[l * stride], b[l], s0);
+    s1 = fma(a[(l + 1) * stride], b[l + 1], s1);
+  }
+  if (L & 1) s0 = fma(a[(L - 1) * stride], b[L - 1], s0);
+  return s0 + s1;
+}
 
 }  // namespace scan
 
@@ -68,10 +118,12 @@ __device__ __forceinline__ ScanRhs scan_rhs(const Inst &I, bool from_res) {
 }
 
 // Backward p recursion over chunk c.  MODE 0: from p_e = 0, writes phi_c.
-// MODE 1: from p_e = pb[c+1], writes p_i (i in [s, e)) and k_i.
+// MODE 1: from p_e = pb[c+1], writes p_i (i in [s, e)) and k_i.  The next
+// stage's matrices are prefetched into registers while a stage computes.
 template <typename T, int NX, int NU, int MODE, bool FROM_RES>
 __global__ void __launch_bounds__(32) k_scan_pvec(BatchArgs a, ScanLayout SL, size_t sbase) {
   constexpr int n = NX, m = NU, nn = n * n, nm = n * m, mmm = m * m;
+  constexpr int CP = (nn + 31) / 32, CB = (nm + 31) / 32, CR = (mmm + 31) / 32;
   using SM = scan::VecSmem<T, NX, NU>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM &s = *reinterpret_cast<SM *>(smem_raw);
@@ -84,54 +136,54 @@ __global__ void __launch_bounds__(32) k_scan_pvec(BatchArgs a, ScanLayout SL, si
   const T *gW = reinterpret_cast<const T *>(I.ws + I.L.W);
   const T *gK = reinterpret_cast<const T *>(I.ws + I.L.K);
   const T *gGi = reinterpret_cast<const T *>(I.ws + I.L.Gi);
-  const float *gAf = reinterpret_cast<const float *>(I.ws + I.L.Af);
-  const float *gBf = reinterpret_cast<const float *>(I.ws + I.L.Bf);
+  const T *dA = scan::data_ptr<T>(I.A, reinterpret_cast<const float *>(I.ws + I.L.Af));
+  const T *dB = scan::data_ptr<T>(I.B, reinterpret_cast<const float *>(I.ws + I.L.Bf));
   T *gpv = reinterpret_cast<T *>(I.ws + I.L.pv);
   T *gkv = reinterpret_cast<T *>(I.ws + I.L.kv);
   T *pb = reinterpret_cast<T *>(I.ws + sbase + SL.pb);
   T *phi = reinterpret_cast<T *>(I.ws + sbase + SL.phi);
+  LaneSeg<T, CP> fW, fA;
+  LaneSeg<T, CB> fB, fK;
+  LaneSeg<T, CR> fG;
+  double vc = 0.0, vr = 0.0, vq = 0.0;
+  auto prefetch = [&](int i) {
+    fW.load(gW + (size_t)(i + 1) * nn, nn, lane);
+    fA.load(dA + (size_t)i * nn, nn, lane);
+    fB.load(dB + (size_t)i * nm, nm, lane);
+    fK.load(gK + (size_t)i * nm, nm, lane);
+    if (MODE == 1) fG.load(gGi + (size_t)i * mmm, mmm, lane);
+    if (lane < n) {
+      vc = __ldg(rhs.c + (size_t)(i + 1) * n + lane);
+      vq = __ldg(rhs.q + (size_t)i * n + lane);
+    }
+    if (lane < m) vr = __ldg(rhs.r + (size_t)i * m + lane);
+  };
   if (lane < n) s.p[lane] = (MODE == 0) ? (T)0 : pb[(size_t)(c + 1) * n + lane];
+  prefetch(e0 - 1);
   for (int i = e0 - 1; i >= s0; --i) {
     __syncwarp();
-    for (int e = lane; e < nn; e += 32) {
-      s.W[e] = gW[(size_t)(i + 1) * nn + e];
-      s.A[e] = scan::data_at<T>(I.A, gAf, (size_t)i * nn + e);
-    }
-    for (int e = lane; e < nm; e += 32) {
-      s.B[e] = scan::data_at<T>(I.B, gBf, (size_t)i * nm + e);
-      s.K[e] = gK[(size_t)i * nm + e];
-    }
-    for (int e = lane; e < mmm; e += 32) s.G[e] = gGi[(size_t)i * mmm + e];
-    if (lane < n) s.v[lane] = to_work<T>(__ldcg(rhs.c + (size_t)(i + 1) * n + lane)) - delta * s.p[lane];
+    fW.store(s.W, nn, lane);
+    fA.store(s.A, nn, lane);
+    fB.store(s.B, nm, lane);
+    fK.store(s.K, nm, lane);
+    if (MODE == 1) fG.store(s.G, mmm, lane);
+    const T cq = to_work<T>(vq), cr = to_work<T>(vr);
+    if (lane < n) s.v[lane] = to_work<T>(vc) - delta * s.p[lane];
+    if (i > s0) prefetch(i - 1);
     __syncwarp();
     // g = p + W (c' - delta p)
-    if (lane < n) {
-      T t = s.p[lane];
-      for (int l = 0; l < n; ++l) t = fma(s.W[lane * n + l], s.v[l], t);
-      s.g[lane] = t;
-    }
+    if (lane < n) s.g[lane] = s.p[lane] + scan::dotc<T, NX>(s.W + lane * n, s.v);
     __syncwarp();
     // h = r' + B^T g
-    if (lane < m) {
-      T t = to_work<T>(__ldcg(rhs.r + (size_t)i * m + lane));
-      for (int l = 0; l < n; ++l) t = fma(s.B[l * m + lane], s.g[l], t);
-      s.h[lane] = t;
-    }
+    if (lane < m) s.h[lane] = cr + scan::dots<T, NX>(s.B + lane, m, s.g);
     __syncwarp();
     // p_i = q' + A^T g + K^T h;  k_i = -G^{-1} h
     T pnew = 0;
     if (lane < n) {
-      T t = to_work<T>(__ldcg(rhs.q + (size_t)i * n + lane));
-      for (int l = 0; l < n; ++l) t = fma(s.A[l * n + lane], s.g[l], t);
-      for (int l = 0; l < m; ++l) t = fma(s.K[l * n + lane], s.h[l], t);
-      pnew = t;
-      if (MODE == 1) gpv[(size_t)i * n + lane] = t;
+      pnew = cq + scan::dots<T, NX>(s.A + lane, n, s.g) + scan::dots<T, NU>(s.K + lane, n, s.h);
+      if (MODE == 1) gpv[(size_t)i * n + lane] = pnew;
     }
-    if (MODE == 1 && lane < m) {
-      T t = 0;
-      for (int l = 0; l < m; ++l) t = fma(s.G[lane * m + l], s.h[l], t);
-      gkv[(size_t)i * m + lane] = -t;
-    }
+    if (MODE == 1 && lane < m) gkv[(size_t)i * m + lane] = -scan::dotc<T, NU>(s.G + lane * m, s.h);
     __syncwarp();
     if (lane < n) s.p[lane] = pnew;
   }
@@ -182,11 +234,14 @@ __global__ void __launch_bounds__(32) k_scan_pbound(BatchArgs a, ScanLayout SL, 
 
 // Forward pass over chunk c.  MODE 0: from x_s = 0, writes psi_c = x_e.
 // MODE 1: from x_s = xb[c], writes x_{i+1}, u_i, y_{i+1} (FP64); FROM_RES adds
-// them to z and updates the residual rows of the chunk's stages.
+// them to z and updates the residual rows of the chunk's stages.  The next
+// stage's operands are prefetched into registers.
 template <typename T, int NX, int NU, int MODE, bool FROM_RES>
 __global__ void __launch_bounds__(32) k_scan_xvec(BatchArgs a, ScanLayout SL, size_t sbase,
                                                   int sfin1) {
   constexpr int n = NX, m = NU, nn = n * n, nm = n * m, mmm = m * m;
+  constexpr int CP = (nn + 31) / 32, CB = (nm + 31) / 32, CR = (mmm + 31) / 32;
+  constexpr bool RES = FROM_RES && MODE == 1;
   using SM = scan::VecSmem<T, NX, NU>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM &s = *reinterpret_cast<SM *>(smem_raw);
@@ -195,17 +250,16 @@ __global__ void __launch_bounds__(32) k_scan_xvec(BatchArgs a, ScanLayout SL, si
   if (FROM_RES && (I.st->converged || I.st->pivot_status == RLQR_ERR_SINGULAR)) return;
   const int N = I.N, s0 = c * SL.L, e0 = min(s0 + SL.L, N);
   const T delta = (T)I.delta;
-  const double delta64 = I.delta;
   const ScanRhs rhs = scan_rhs(I, FROM_RES);
   const T *gW = reinterpret_cast<const T *>(I.ws + I.L.W);
   const T *gK = reinterpret_cast<const T *>(I.ws + I.L.K);
   const T *gkv = reinterpret_cast<const T *>(I.ws + I.L.kv);
   const T *gpv = reinterpret_cast<const T *>(I.ws + I.L.pv);
-  const float *gAf = reinterpret_cast<const float *>(I.ws + I.L.Af);
-  const float *gBf = reinterpret_cast<const float *>(I.ws + I.L.Bf);
-  const float *gQf = reinterpret_cast<const float *>(I.ws + I.L.Qf);
-  const float *gMf = reinterpret_cast<const float *>(I.ws + I.L.Mf);
-  const float *gRf = reinterpret_cast<const float *>(I.ws + I.L.Rf);
+  const T *dA = scan::data_ptr<T>(I.A, reinterpret_cast<const float *>(I.ws + I.L.Af));
+  const T *dB = scan::data_ptr<T>(I.B, reinterpret_cast<const float *>(I.ws + I.L.Bf));
+  const T *dQ = scan::data_ptr<T>(I.Q, reinterpret_cast<const float *>(I.ws + I.L.Qf));
+  const T *dM = scan::data_ptr<T>(I.M, reinterpret_cast<const float *>(I.ws + I.L.Mf));
+  const T *dR = scan::data_ptr<T>(I.R, reinterpret_cast<const float *>(I.ws + I.L.Rf));
   const T *xb = reinterpret_cast<const T *>(I.ws + sbase + SL.xb);
   const T *pb = reinterpret_cast<const T *>(I.ws + sbase + SL.pb);
   T *psi = reinterpret_cast<T *>(I.ws + sbase + SL.psi);
@@ -213,61 +267,78 @@ __global__ void __launch_bounds__(32) k_scan_xvec(BatchArgs a, ScanLayout SL, si
   double *rq = reinterpret_cast<double *>(I.ws + I.L.res);
   double *rr = rq + (size_t)(N + 1) * n;
   double *rc = rr + (size_t)N * m;
+  LaneSeg<T, CP> fW, fA, fQ;
+  LaneSeg<T, CB> fB, fK, fM;
+  LaneSeg<T, CR> fR;
+  double vc = 0.0, zx = 0.0, zy = 0.0, zu = 0.0, rxq = 0.0, rxc = 0.0, rur = 0.0;
+  T vk = 0, vp = 0;
+  auto prefetch = [&](int i) {
+    fW.load(gW + (size_t)(i + 1) * nn, nn, lane);
+    fA.load(dA + (size_t)i * nn, nn, lane);
+    fB.load(dB + (size_t)i * nm, nm, lane);
+    fK.load(gK + (size_t)i * nm, nm, lane);
+    if (lane < n) {
+      vc = __ldg(rhs.c + (size_t)(i + 1) * n + lane);
+      vp = __ldg(gpv + (size_t)(i + 1) * n + lane);
+    }
+    if (lane < m) vk = __ldg(gkv + (size_t)i * m + lane);
+    if (RES) {
+      fQ.load(dQ + (size_t)i * nn, nn, lane);
+      fM.load(dM + (size_t)i * nm, nm, lane);
+      fR.load(dR + (size_t)i * mmm, mmm, lane);
+      if (lane < n) {
+        const size_t o = (size_t)(i + 1) * n + lane;
+        zx = __ldcg(I.x + o);
+        zy = __ldcg(I.y + o);
+        rxq = __ldcg(rq + (size_t)i * n + lane);
+        rxc = __ldcg(rc + o);
+      }
+      if (lane < m) {
+        zu = __ldcg(I.u + (size_t)i * m + lane);
+        rur = __ldcg(rr + (size_t)i * m + lane);
+      }
+    }
+  };
   if (lane < n) s.x[lane] = (MODE == 0) ? (T)0 : xb[(size_t)c * n + lane];
   __syncwarp();
-  if (FROM_RES && MODE == 1) {
+  if (RES) {
     // dy at the chunk's first stage: P_s dx_s + dp_s (P_s of the finalize)
     if (lane < n) {
-      T t = pb[(size_t)c * n + lane];
       const T *Ps = reinterpret_cast<const T *>(I.ws + sbase + SL.PstB) + (size_t)c * nn;
-      for (int l = 0; l < n; ++l) t = fma(Ps[lane * n + l], s.x[l], t);
-      s.dy[lane] = t;
+      s.dy[lane] = pb[(size_t)c * n + lane] + scan::dotc<T, NX>(Ps + lane * n, s.x);
     }
   }
+  prefetch(s0);
   for (int i = s0; i < e0; ++i) {
     __syncwarp();
-    for (int e = lane; e < nn; e += 32) {
-      s.W[e] = gW[(size_t)(i + 1) * nn + e];
-      s.A[e] = scan::data_at<T>(I.A, gAf, (size_t)i * nn + e);
-      if (FROM_RES && MODE == 1) {
-        const int r = e / n, col = e - r * n;
-        s.Q[e] = scan::data_at<T>(I.Q, gQf, (size_t)i * nn + (r <= col ? e : col * n + r));
-      }
+    fW.store(s.W, nn, lane);
+    fA.store(s.A, nn, lane);
+    fB.store(s.B, nm, lane);
+    fK.store(s.K, nm, lane);
+    if (RES) {
+      fQ.store_sym(s.Q, n, lane);
+      fM.store(s.M, nm, lane);
+      fR.store_sym(s.R, m, lane);
     }
-    for (int e = lane; e < nm; e += 32) {
-      s.B[e] = scan::data_at<T>(I.B, gBf, (size_t)i * nm + e);
-      s.K[e] = gK[(size_t)i * nm + e];
-      if (FROM_RES && MODE == 1) s.M[e] = scan::data_at<T>(I.M, gMf, (size_t)i * nm + e);
-    }
-    if (FROM_RES && MODE == 1)
-      for (int e = lane; e < mmm; e += 32) {
-        const int r = e / m, col = e - r * m;
-        s.R[e] = scan::data_at<T>(I.R, gRf, (size_t)i * mmm + (r <= col ? e : col * m + r));
-      }
-    if (lane < n) s.pn[lane] = gpv[(size_t)(i + 1) * n + lane];
+    const double zx0 = zx, zy0 = zy, zu0 = zu, rxq0 = rxq, rxc0 = rxc, rur0 = rur;
+    const T cvc = to_work<T>(vc), cvp = vp, cvk = vk;
+    if (lane < n) s.pn[lane] = cvp;
+    if (i + 1 < e0) prefetch(i + 1);
     __syncwarp();
     // u_i = K x_i + k_i
-    if (lane < m) {
-      T t = gkv[(size_t)i * m + lane];
-      for (int l = 0; l < n; ++l) t = fma(s.K[lane * n + l], s.x[l], t);
-      s.u[lane] = t;
-    }
+    if (lane < m) s.u[lane] = cvk + scan::dotc<T, NX>(s.K + lane * n, s.x);
     __syncwarp();
     // v = A x + B u + c'_{i+1} - delta p_{i+1}
-    if (lane < n) {
-      T t = to_work<T>(__ldcg(rhs.c + (size_t)(i + 1) * n + lane)) - delta * s.pn[lane];
-      for (int l = 0; l < n; ++l) t = fma(s.A[lane * n + l], s.x[l], t);
-      for (int l = 0; l < m; ++l) t = fma(s.B[lane * m + l], s.u[l], t);
-      s.v[lane] = t;
-    }
+    if (lane < n)
+      s.v[lane] = (cvc - delta * cvp) + scan::dotc<T, NX>(s.A + lane * n, s.x) +
+                  scan::dotc<T, NU>(s.B + lane * m, s.u);
     __syncwarp();
     // x_{i+1} = v - delta W v, y_{i+1} = W v + p_{i+1}
     T xn = 0, yn = 0;
     if (lane < n) {
-      T t = 0;
-      for (int l = 0; l < n; ++l) t = fma(s.W[lane * n + l], s.v[l], t);
+      const T t = scan::dotc<T, NX>(s.W + lane * n, s.v);
       xn = s.v[lane] - delta * t;
-      yn = t + s.pn[lane];
+      yn = t + cvp;
       s.dxn[lane] = xn;
       s.dyn[lane] = yn;
     }
@@ -282,32 +353,24 @@ __global__ void __launch_bounds__(32) k_scan_xvec(BatchArgs a, ScanLayout SL, si
       } else {
         if (lane < n) {
           const size_t o = (size_t)(i + 1) * n + lane;
-          I.x[o] = __ldcg(I.x + o) + widen(xn);
-          I.y[o] = __ldcg(I.y + o) + widen(yn);
+          I.x[o] = zx0 + widen(xn);
+          I.y[o] = zy0 + widen(yn);
           // x rows of stage i: Q dx + M du + A^T dy_{i+1} - dy_i
-          T t = -s.dy[lane];
-          for (int l = 0; l < n; ++l)
-            t = fma(s.Q[lane * n + l], s.x[l], fma(s.A[l * n + lane], s.dyn[l], t));
-          for (int l = 0; l < m; ++l) t = fma(s.M[lane * m + l], s.u[l], t);
-          double *dst = rq + (size_t)i * n + lane;
-          *dst = __ldcg(dst) + widen(t);
+          const T t = scan::dotc<T, NX>(s.Q + lane * n, s.x) + scan::dots<T, NX>(s.A + lane, n, s.dyn) +
+                      scan::dotc<T, NU>(s.M + lane * m, s.u) - s.dy[lane];
+          rq[(size_t)i * n + lane] = rxq0 + widen(t);
           // c rows of stage i+1: A dx + B du - dx_{i+1} - delta dy_{i+1}
-          T tc = -(xn + delta * yn);
-          for (int l = 0; l < n; ++l) tc = fma(s.A[lane * n + l], s.x[l], tc);
-          for (int l = 0; l < m; ++l) tc = fma(s.B[lane * m + l], s.u[l], tc);
-          double *dc = rc + (size_t)(i + 1) * n + lane;
-          *dc = __ldcg(dc) + widen(tc);
+          const T tc = scan::dotc<T, NX>(s.A + lane * n, s.x) + scan::dotc<T, NU>(s.B + lane * m, s.u) -
+                       (xn + delta * yn);
+          rc[o] = rxc0 + widen(tc);
         }
         if (lane < m) {
           const size_t o = (size_t)i * m + lane;
-          I.u[o] = __ldcg(I.u + o) + widen(s.u[lane]);
+          I.u[o] = zu0 + widen(s.u[lane]);
           // u rows of stage i: M^T dx + R du + B^T dy_{i+1}
-          T t = 0;
-          for (int l = 0; l < n; ++l)
-            t = fma(s.M[l * m + lane], s.x[l], fma(s.B[l * m + lane], s.dyn[l], t));
-          for (int l = 0; l < m; ++l) t = fma(s.R[lane * m + l], s.u[l], t);
-          double *dst = rr + o;
-          *dst = __ldcg(dst) + widen(t);
+          const T t = scan::dots<T, NX>(s.M + lane, m, s.x) + scan::dots<T, NX>(s.B + lane, m, s.dyn) +
+                      scan::dotc<T, NU>(s.R + lane * m, s.u);
+          rr[o] = rur0 + widen(t);
         }
       }
     }
@@ -319,7 +382,7 @@ __global__ void __launch_bounds__(32) k_scan_xvec(BatchArgs a, ScanLayout SL, si
   }
   __syncwarp();
   if (MODE == 0 && lane < n) psi[(size_t)c * n + lane] = s.x[lane];
-  if (MODE == 1 && FROM_RES && e0 == N && lane < n) {
+  if (RES && e0 == N && lane < n) {
     // terminal x rows: Q_N dx_N - dy_N
     T t = -s.dy[lane];
     for (int l = 0; l < n; ++l) {
@@ -330,7 +393,6 @@ __global__ void __launch_bounds__(32) k_scan_xvec(BatchArgs a, ScanLayout SL, si
     double *dst = rq + (size_t)N * n + lane;
     *dst = __ldcg(dst) + widen(t);
   }
-  (void)delta64;
 }
 
 // x_0, y_0 (eq. recover-x0: v0 = c'_0 - delta p_0, x_0 = v0 - delta W_0 v0,
