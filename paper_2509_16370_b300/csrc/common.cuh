@@ -101,6 +101,8 @@ struct BatchArgs {
   const double *ddelta;
   const int64_t *oQ, *oM, *oR, *oq, *or_, *oA, *oB, *oc, *ox, *ou, *oy, *of;
   const int64_t *ows;  // per-instance workspace byte offsets
+  const int32_t *perm; // launch slot -> instance (grouped launches of a ragged batch), or null
+  int goff;            // first slot of this launch's group in perm
   // shared
   char *ws;
   int tsize;
@@ -110,6 +112,11 @@ struct BatchArgs {
   double tol;
   int max_refine;
 };
+
+// Instance of a launch slot: the identity, or the group's entry of perm.
+__device__ __forceinline__ int inst_of(const BatchArgs &a, int slot) {
+  return a.perm ? a.perm[a.goff + slot] : slot;
+}
 
 struct Inst {
   int N, n, m;

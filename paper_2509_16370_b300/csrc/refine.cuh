@@ -68,8 +68,9 @@ struct SolveSmem {
 template <typename T, class D, int THREADS, bool FROM_RES>
 __global__ void __launch_bounds__(THREADS) k_solve(BatchArgs a) {
   constexpr int NM = D::NM, MM = D::MM;
-  const int b = blockIdx.x;
-  if (b >= a.count) return;
+  const int slot = blockIdx.x;
+  if (slot >= a.count) return;
+  const int b = inst_of(a, slot);
   const Inst I = get_inst(a, b);
   InstState *stp = I.st;
   if (FROM_RES) {

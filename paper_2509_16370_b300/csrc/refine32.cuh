@@ -95,8 +95,9 @@ __global__ void __launch_bounds__(32) k_refine32(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM &s = *reinterpret_cast<SM *>(smem_raw);
   const int lane = threadIdx.x;
-  const int b = blockIdx.x;
-  if (b >= a.count) return;
+  const int slot = blockIdx.x;
+  if (slot >= a.count) return;
+  const int b = inst_of(a, slot);
   const Inst I = get_inst(a, b);
   InstState *stp = I.st;
   if (stp->converged || stp->pivot_status == RLQR_ERR_SINGULAR) return;

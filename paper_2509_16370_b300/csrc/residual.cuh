@@ -36,8 +36,9 @@ template <bool FF>
 __global__ void k_residual(BatchArgs a, int store, double *res_out, double *norms_out,
                            int recompute_norms, int standalone, int rs_max, int cert_g,
                            int do_residual) {
-  const int b = blockIdx.x;
-  if (b >= a.count) return;
+  const int slot = blockIdx.x;
+  if (slot >= a.count) return;
+  const int b = inst_of(a, slot);
   const Inst I = get_inst(a, b);
   const int N = I.N, n = I.n, m = I.m;
   const double delta = I.delta;

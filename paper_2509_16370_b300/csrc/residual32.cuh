@@ -126,8 +126,9 @@ __global__ void __launch_bounds__(32 * kResWarps) k_res32(BatchArgs a, int store
   constexpr int N4 = SW::N4, M4 = SW::M4;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_red[32];
-  const int b = blockIdx.x;
-  if (b >= a.count) return;
+  const int slot = blockIdx.x;
+  if (slot >= a.count) return;
+  const int b = inst_of(a, slot);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   SW &s = reinterpret_cast<SW *>(smem_raw)[warp];
   const Inst I = get_inst(a, b);

@@ -49,6 +49,59 @@ static cudaError_t launch_first_residual_mixed(const BatchArgs &a, int n, int m,
   return launch_residual(a, rs_max, 1, nullptr, nullptr, 1, 0, s, cert_g, 1, true);
 }
 
+// ---- ragged batches: size classes and the launch order
+// Class of an instance: its exact (n, m) when that size has specialized
+// kernels (warp-per-instance or compile-time CTA), else its bucket.
+constexpr int kNumExact = 7, kNumClasses = kNumExact + 4;
+constexpr int kNBuckets = 64;  // horizon buckets for the longest-first order
+
+__host__ __device__ inline int size_class(int n, int m) {
+  if (n == 4 && m == 2) return 0;
+  if (n == 6 && m == 1) return 1;
+  if (n == 6 && m == 2) return 2;
+  if (n == 12 && m == 4) return 3;
+  if (n == 24 && m == 8) return 4;
+  if (n == 32 && m == 8) return 5;
+  if (n == 48 && m == 16) return 6;
+  const int bk = n <= 8 && m <= 4 ? 0 : (n <= 16 && m <= 8 ? 1 : (n <= 32 && m <= 16 ? 2 : 3));
+  return kNumExact + bk;
+}
+
+struct ClassOffsets {
+  int off[kNumClasses];
+};
+
+// perm: instances grouped by class (class c starts at off[c]), longest
+// horizon first within a class (counting sort over horizon buckets of
+// width q).  One block.
+__global__ void k_group(int count, const int32_t *dN, const int32_t *dn, const int32_t *dm,
+                        int q, ClassOffsets co, int32_t *perm) {
+  __shared__ int cnt[kNumClasses * kNBuckets];
+  for (int i = threadIdx.x; i < kNumClasses * kNBuckets; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < count; b += blockDim.x) {
+    const int cls = size_class(dn[b], dm[b]);
+    const int nb = kNBuckets - 1 - min(kNBuckets - 1, dN[b] / q);
+    atomicAdd(&cnt[cls * kNBuckets + nb], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < kNumClasses) {
+    const int c = threadIdx.x;
+    int acc = co.off[c];
+    for (int j = 0; j < kNBuckets; ++j) {
+      const int v = cnt[c * kNBuckets + j];
+      cnt[c * kNBuckets + j] = acc;
+      acc += v;
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < count; b += blockDim.x) {
+    const int cls = size_class(dn[b], dm[b]);
+    const int nb = kNBuckets - 1 - min(kNBuckets - 1, dN[b] / q);
+    perm[atomicAdd(&cnt[cls * kNBuckets + nb], 1)] = b;
+  }
+}
+
 // Per-instance workspace offsets of a batch: exclusive prefix sum of
 // ws_layout(...).total, after the header that holds the offsets themselves.
 __global__ void k_plan(int count, const int32_t *dN, const int32_t *dn, const int32_t *dm,
@@ -62,7 +115,8 @@ __global__ void k_plan(int count, const int32_t *dN, const int32_t *dn, const in
   part[t] = s;
   __syncthreads();
   if (t == 0) {
-    int64_t acc = (int64_t)align_up((size_t)count * sizeof(int64_t));
+    int64_t acc = (int64_t)(align_up((size_t)count * sizeof(int64_t)) +
+                            align_up((size_t)count * sizeof(int32_t)));
     for (int i = 0; i < T; ++i) {
       int64_t v = part[i];
       part[i] = acc;
@@ -288,7 +342,8 @@ size_t rlqr_batched_workspace_bytes(const rlqr_batch *batch, const rlqr_opts *op
       !valid_opts(opts))
     return 0;
   int tsize = opts->prec == RLQR_MIXED ? 4 : 8;
-  size_t tot = align_up((size_t)batch->count * sizeof(int64_t));
+  size_t tot = align_up((size_t)batch->count * sizeof(int64_t)) +
+               align_up((size_t)batch->count * sizeof(int32_t));
   for (int b = 0; b < batch->count; ++b) {
     if (!valid_dims(batch->h_N[b], batch->h_nx[b], batch->h_nu[b])) return 0;
     tot += ws_layout(batch->h_N[b], batch->h_nx[b], batch->h_nu[b], tsize).total;
@@ -311,8 +366,6 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
   if (need == 0) return RLQR_ERR_ARG;
   if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
     return RLQR_ERR_WORKSPACE;
-  // one kernel instantiation covers the whole batch: exact dimensions when
-  // all instances share them, else the bucket of the largest
   int nmax = 0, mmax = 0, rs_max = 0;
   bool uniform = true;
   for (int b = 0; b < B.count; ++b) {
@@ -348,19 +401,62 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return RLQR_ERR_CUDA;
-  e = mixed ? launch_seq<float, true>(nmax, mmax, uniform, a, s)
-            : launch_seq<double, true>(nmax, mmax, uniform, a, s);
-  if (e != cudaSuccess) return RLQR_ERR_CUDA;
-  if (mixed || rel_resid) {
-    e = mixed ? launch_first_residual_mixed(a, nmax, mmax, uniform, rs_max, 1, s)
-              : launch_residual(a, rs_max, 0, nullptr, nullptr, 1, 0, s);
-    if (e != cudaSuccess) return RLQR_ERR_CUDA;
+  // one launch sequence per size class (the whole batch when uniform)
+  struct Group {
+    int n, m, rs, count, off;
+    bool exact;
+  };
+  Group groups[kNumClasses];
+  int ng = 0;
+  if (uniform) {
+    groups[ng++] = Group{nmax, mmax, rs_max, B.count, 0, true};
+  } else {
+    int cnt[kNumClasses] = {}, gn[kNumClasses] = {}, gm[kNumClasses] = {}, grs[kNumClasses] = {};
+    int nmaxN = 1;
+    for (int b = 0; b < B.count; ++b) {
+      const int c = size_class(B.h_nx[b], B.h_nu[b]);
+      ++cnt[c];
+      gn[c] = std::max(gn[c], B.h_nx[b]);
+      gm[c] = std::max(gm[c], B.h_nu[b]);
+      grs[c] = std::max(grs[c], 2 * B.h_nx[b] + B.h_nu[b]);
+      nmaxN = std::max(nmaxN, B.h_N[b]);
+    }
+    ClassOffsets co{};
+    int acc = 0;
+    for (int c = 0; c < kNumClasses; ++c) {
+      co.off[c] = acc;
+      if (cnt[c]) groups[ng++] = Group{gn[c], gm[c], grs[c], cnt[c], acc, c < kNumExact};
+      acc += cnt[c];
+    }
+    int32_t *perm = reinterpret_cast<int32_t *>(static_cast<char *>(ws) +
+                                                align_up((size_t)B.count * sizeof(int64_t)));
+    {
+      LaunchScope ls("k_group", s);
+      k_group<<<1, 1024, 0, s>>>(B.count, B.N, B.nx, B.nu, (nmaxN + kNBuckets - 1) / kNBuckets,
+                                 co, perm);
+      if (cudaGetLastError() != cudaSuccess) return RLQR_ERR_CUDA;
+    }
+    a.perm = perm;
   }
-  if (mixed)
-    for (int it = 0; it < opts->max_refine; ++it) {
-      e = launch_solve<float, true>(nmax, mmax, uniform, a, s);
+  for (int g = 0; g < ng; ++g) {
+    const Group &G = groups[g];
+    BatchArgs ag = a;
+    ag.count = G.count;
+    ag.goff = G.off;
+    e = mixed ? launch_seq<float, true>(G.n, G.m, G.exact, ag, s)
+              : launch_seq<double, true>(G.n, G.m, G.exact, ag, s);
+    if (e != cudaSuccess) return RLQR_ERR_CUDA;
+    if (mixed || rel_resid) {
+      e = mixed ? launch_first_residual_mixed(ag, G.n, G.m, G.exact, G.rs, 1, s)
+                : launch_residual(ag, G.rs, 0, nullptr, nullptr, 1, 0, s);
       if (e != cudaSuccess) return RLQR_ERR_CUDA;
     }
+    if (mixed)
+      for (int it = 0; it < opts->max_refine; ++it) {
+        e = launch_solve<float, true>(G.n, G.m, G.exact, ag, s);
+        if (e != cudaSuccess) return RLQR_ERR_CUDA;
+      }
+  }
   return RLQR_OK;
 }
 

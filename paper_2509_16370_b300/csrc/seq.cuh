@@ -174,8 +174,9 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
   constexpr int NM = D::NM, MM = D::MM;
   constexpr int WS = 2 * NM;           // columns of [I + delta P | P]
   constexpr int WC = 2 * MM + NM + 1;  // columns of [G | H | h | I]
-  const int b = blockIdx.x;
-  if (b >= a.count) return;
+  const int slot = blockIdx.x;
+  if (slot >= a.count) return;
+  const int b = inst_of(a, slot);
   const Inst I = get_inst(a, b);
   const D dims(I.n, I.m);
   const int N = I.N, n = dims.n, m = dims.m;

@@ -127,8 +127,9 @@ __global__ void __launch_bounds__(32 * WPC) k_seq_warp(BatchArgs a) {
   using SM = WarpSmem<T, NX, NU>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int b = blockIdx.x * WPC + wid;
-  if (b >= a.count) return;  // whole warp exits together
+  const int slot = blockIdx.x * WPC + wid;
+  if (slot >= a.count) return;  // whole warp exits together
+  const int b = inst_of(a, slot);
   SM &s = reinterpret_cast<SM *>(smem_raw)[wid];
   const Inst I = get_inst(a, b);
   const int N = I.N;
@@ -551,8 +552,9 @@ __global__ void __launch_bounds__(32 * WPC) k_solve_warp(BatchArgs a) {
   using SM = WarpSmem<T, NX, NU>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int b = blockIdx.x * WPC + wid;
-  if (b >= a.count) return;
+  const int slot = blockIdx.x * WPC + wid;
+  if (slot >= a.count) return;
+  const int b = inst_of(a, slot);
   SM &s = reinterpret_cast<SM *>(smem_raw)[wid];
   // FP64 staging of the iterate and residual rows of a stage (after the
   // T-typed arrays of the warp's block)

@@ -165,8 +165,9 @@ __global__ void __launch_bounds__(32) k_sweep32(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM &s = *reinterpret_cast<SM *>(smem_raw);
   const int lane = threadIdx.x;
-  const int b = blockIdx.x;
-  if (b >= a.count) return;
+  const int slot = blockIdx.x;
+  if (slot >= a.count) return;
+  const int b = inst_of(a, slot);
   const Inst I = get_inst(a, b);
   const int N = I.N;
   const float delta = (float)I.delta;

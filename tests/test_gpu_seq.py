@@ -218,3 +218,22 @@ def test_ragged_batch(prec):
         np.testing.assert_array_equal(f, ref.flags)
         assert oracle.residual(p, x, u, y).rel <= REL_TOL
         assert oracle.forward_error((ref.x, ref.u, ref.y), x, u, y) <= FWD_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ragged_workload4_sample(prec):
+    """A sample shaped like the ragged workload (n in {6, 12, 24, 48},
+    m = n/3, M != 0, barrier-scaled diagonals of Q and R, delta log-uniform)
+    with horizons capped at 160: one call, instances grouped by size class
+    and ordered longest first on the device; every instance checked against
+    the oracle."""
+    dims = inputs.workload4_dims(4096)[:40]
+    probs = [inputs.workload4_instance(b, min(N, 160), n, m) for b, (N, n, m) in enumerate(dims)]
+    db = rlqr.DeviceBatch.from_problems(probs)
+    out = solve_batch(db, prec, max_refine=6)
+    assert set(out["status"].tolist()) <= {rlqr.RLQR_OK, rlqr.RLQR_NOT_PD}
+    for b, p in enumerate(probs):
+        x, u, y, f = db.instance_view(b)
+        ref = oracle.riccati(p)
+        np.testing.assert_array_equal(f, ref.flags)
+        assert oracle.residual(p, x, u, y).rel <= REL_TOL
