@@ -15,6 +15,7 @@ is timed beside it, and the FP64 CPU oracle is the CPU baseline.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --profile-instances K   # profiling case, no bench line
     python bench.py --long-horizon          # the single long-horizon instance
+    python bench.py --ragged K              # the first K instances of the ragged batch
 
 --long-horizon measures the other workload of the path: one instance with
 n_x = 32, n_u = 8, N = 65536 (delta = 1e-7, rho(A) = 0.99, Q and R with
@@ -296,6 +297,71 @@ def run_long_horizon(args):
     print(json.dumps(line), flush=True)
 
 
+def _ragged_instance(arg):
+    from paper_2509_16370_b300 import inputs
+    b, (N, n, m) = arg
+    return inputs.workload4_instance(b, N, n, m)
+
+
+def run_ragged(args):
+    """One JSON line for the first K instances of the ragged batch (N in
+    32..2048, n in {6, 12, 24, 48}, m = n/3): rlqr_solve_batched mixed vs
+    plain FP64.  Instances are generated by a process pool (spawn)."""
+    import multiprocessing as mp
+    import torch
+    from paper_2509_16370_b300 import inputs, rlqr
+    dims = inputs.workload4_dims(4096)[:args.ragged]
+    with mp.get_context("spawn").Pool(min(32, os.cpu_count() or 1)) as pool:
+        probs = pool.map(_ragged_instance, list(enumerate(dims)), chunksize=4)
+    db = rlqr.DeviceBatch.from_problems(probs)
+    stages = sum(N for N, _, _ in dims)
+    data_gb = sum(8 * ((N + 1) * n * n + N * (2 * n * m + m * m + n * n) + (N + 1) * n * 2 + N * m)
+                  for N, n, m in dims) / 1e9
+    B = len(probs)
+
+    def timed(prec, steps, warmup, instrument=False):
+        opts = rlqr.make_opts(prec, tol=TOL, max_refine=6)
+        ws = rlqr.alloc_workspace(rlqr.rlqr_batched_workspace_bytes(db, opts))
+        st = torch.zeros(B, dtype=torch.int32, device="cuda")
+        rel = torch.zeros(B, dtype=torch.float64, device="cuda")
+        it = torch.zeros(B, dtype=torch.int32, device="cuda")
+        for _ in range(warmup):
+            rlqr.rlqr_solve_batched(db, opts, ws, st, rel, it)
+        torch.cuda.synchronize()
+        if instrument:
+            rlqr.rlqr_instrument(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            rlqr.rlqr_solve_batched(db, opts, ws, st, rel, it)
+        e1.record()
+        torch.cuda.synchronize()
+        report = rlqr.rlqr_instrument_report() if instrument else {}
+        rlqr.rlqr_instrument(False)
+        relv, stv = rel.cpu().numpy(), st.cpu().numpy()
+        return e0.elapsed_time(e1) / steps, report, dict(
+            max_rel=float(relv.max()), all_le_tol=bool(np.all(relv <= TOL)),
+            max_iters=int(it.max().item()), statuses=sorted(set(stv.tolist())))
+
+    with ClockSampler(0) as clk:
+        ms, report, acc = timed(rlqr.RLQR_MIXED, args.steps, args.warmup, True)
+    ms64, _, acc64 = timed(rlqr.RLQR_FP64, max(1, args.steps // 4), 1)
+    line = {"metric": METRIC, "value": stages / (ms / 1e3), "unit": "stage-solves/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64 (FP32 sweep; FP64 certificate, residual, correction)",
+            "data": "synthetic",
+            "config": {"workload": f"first {B} instances of the ragged batch of 4096 "
+                                   "(N in 32..2048, n in {6,12,24,48}, m = n/3, barrier-scaled "
+                                   "diagonals)", "instances": B, "stages": stages,
+                       "data_gb": round(data_gb, 2)},
+            "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in report.items()},
+            "accuracy": acc,
+            "fp64_plain": {"value": stages / (ms64 / 1e3), "ms_per_step": ms64, **acc64},
+            "speedup_vs_fp64_plain": ms64 / ms, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     rank, world, local = _dist()
@@ -430,6 +496,8 @@ def main():
                     help="profiling case: the mixed solve on the first K instances only")
     ap.add_argument("--long-horizon", action="store_true",
                     help="the single long-horizon instance (associative scan)")
+    ap.add_argument("--ragged", type=int, default=0,
+                    help="the first K instances of the ragged batch")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -439,6 +507,8 @@ def main():
         run_profile_case(args)
     elif args.long_horizon:
         run_long_horizon(args)
+    elif args.ragged > 0:
+        run_ragged(args)
     else:
         run_ours(args)
 

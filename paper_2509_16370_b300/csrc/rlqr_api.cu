@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "launch.cuh"
 #include "residual.cuh"
+#include "residual_grid.cuh"
 #include "scan.cuh"
 
 namespace rlqr {
@@ -102,33 +103,53 @@ __global__ void k_group(int count, const int32_t *dN, const int32_t *dn, const i
   }
 }
 
-// Per-instance workspace offsets of a batch: exclusive prefix sum of
-// ws_layout(...).total, after the header that holds the offsets themselves.
+// Header of a batch's workspace: per-instance byte offsets (int64), the
+// launch permutation of a ragged batch (int32), the exclusive prefix sum of
+// N_b + 1 (int64, count + 1 entries: the residual's work items).
+__host__ __device__ inline size_t batch_header_bytes(int count) {
+  return align_up((size_t)count * sizeof(int64_t)) + align_up((size_t)count * sizeof(int32_t)) +
+         align_up((size_t)(count + 1) * sizeof(int64_t));
+}
+
+// Per-instance workspace offsets of a batch (exclusive prefix sum of
+// ws_layout(...).total after the header) and the work-item prefix sum.
 __global__ void k_plan(int count, const int32_t *dN, const int32_t *dn, const int32_t *dm,
                        int tsize, int64_t *ows) {
-  __shared__ int64_t part[1024];
+  __shared__ int64_t part[1024], part2[1024];
   const int t = threadIdx.x, T = blockDim.x;
   const int per = (count + T - 1) / T;
   const int lo = min(count, t * per), hi = min(count, lo + per);
-  int64_t s = 0;
-  for (int b = lo; b < hi; ++b) s += (int64_t)ws_layout(dN[b], dn[b], dm[b], tsize).total;
+  int64_t s = 0, s2 = 0;
+  for (int b = lo; b < hi; ++b) {
+    s += (int64_t)ws_layout(dN[b], dn[b], dm[b], tsize).total;
+    s2 += (int64_t)dN[b] + 1;
+  }
   part[t] = s;
+  part2[t] = s2;
   __syncthreads();
   if (t == 0) {
-    int64_t acc = (int64_t)(align_up((size_t)count * sizeof(int64_t)) +
-                            align_up((size_t)count * sizeof(int32_t)));
+    int64_t acc = (int64_t)batch_header_bytes(count), acc2 = 0;
     for (int i = 0; i < T; ++i) {
-      int64_t v = part[i];
+      const int64_t v = part[i], v2 = part2[i];
       part[i] = acc;
+      part2[i] = acc2;
       acc += v;
+      acc2 += v2;
     }
   }
   __syncthreads();
-  int64_t acc = part[t];
+  int64_t *spre = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(ows) +
+                                              align_up((size_t)count * sizeof(int64_t)) +
+                                              align_up((size_t)count * sizeof(int32_t)));
+  int64_t acc = part[t], acc2 = part2[t];
   for (int b = lo; b < hi; ++b) {
     ows[b] = acc;
+    spre[b] = acc2;
     acc += (int64_t)ws_layout(dN[b], dn[b], dm[b], tsize).total;
+    acc2 += (int64_t)dN[b] + 1;
   }
+  if (hi == count && lo < hi) spre[count] = acc2;
+  if (count == 0 && t == 0) spre[0] = 0;
 }
 
 static bool valid_opts(const rlqr_opts *o) {
@@ -342,8 +363,7 @@ size_t rlqr_batched_workspace_bytes(const rlqr_batch *batch, const rlqr_opts *op
       !valid_opts(opts))
     return 0;
   int tsize = opts->prec == RLQR_MIXED ? 4 : 8;
-  size_t tot = align_up((size_t)batch->count * sizeof(int64_t)) +
-               align_up((size_t)batch->count * sizeof(int32_t));
+  size_t tot = batch_header_bytes(batch->count);
   for (int b = 0; b < batch->count; ++b) {
     if (!valid_dims(batch->h_N[b], batch->h_nx[b], batch->h_nu[b])) return 0;
     tot += ws_layout(batch->h_N[b], batch->h_nx[b], batch->h_nu[b], tsize).total;
@@ -438,25 +458,49 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
     }
     a.perm = perm;
   }
+  auto group_args = [&](int g) {
+    BatchArgs ag = a;
+    ag.count = groups[g].count;
+    ag.goff = groups[g].off;
+    return ag;
+  };
   for (int g = 0; g < ng; ++g) {
     const Group &G = groups[g];
-    BatchArgs ag = a;
-    ag.count = G.count;
-    ag.goff = G.off;
+    const BatchArgs ag = group_args(g);
     e = mixed ? launch_seq<float, true>(G.n, G.m, G.exact, ag, s)
               : launch_seq<double, true>(G.n, G.m, G.exact, ag, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
-    if (mixed || rel_resid) {
-      e = mixed ? launch_first_residual_mixed(ag, G.n, G.m, G.exact, G.rs, 1, s)
+    if (uniform && (mixed || rel_resid)) {
+      e = mixed ? launch_first_residual_mixed(ag, G.n, G.m, true, G.rs, 1, s)
                 : launch_residual(ag, G.rs, 0, nullptr, nullptr, 1, 0, s);
       if (e != cudaSuccess) return RLQR_ERR_CUDA;
     }
-    if (mixed)
+  }
+  if (!uniform && (mixed || rel_resid)) {
+    // ragged: one stage-parallel residual over every instance
+    const int64_t *spre = reinterpret_cast<const int64_t *>(
+        static_cast<char *>(ws) + align_up((size_t)B.count * sizeof(int64_t)) +
+        align_up((size_t)B.count * sizeof(int32_t)));
+    int64_t items = 0;
+    for (int b = 0; b < B.count; ++b) items += (int64_t)B.h_N[b] + 1;
+    BatchArgs ab = a;
+    ab.perm = nullptr;
+    LaunchScope ls(mixed ? "k_residual_ff" : "k_residual_fp64", s);
+    k_resb_reset<<<(B.count + 255) / 256, 256, 0, s>>>(ab);
+    if (mixed) k_certb<<<(int)std::min<int64_t>((items + 255) / 256, 148 * 16), 256, 0, s>>>(ab, spre, items);
+    k_resb<<<148 * 16, 256, 0, s>>>(ab, spre, items, mixed ? 1 : 0);
+    k_resb_final<<<(B.count + 255) / 256, 256, 0, s>>>(ab);
+    if (cudaGetLastError() != cudaSuccess) return RLQR_ERR_CUDA;
+  }
+  if (mixed)
+    for (int g = 0; g < ng; ++g) {
+      const Group &G = groups[g];
+      const BatchArgs ag = group_args(g);
       for (int it = 0; it < opts->max_refine; ++it) {
         e = launch_solve<float, true>(G.n, G.m, G.exact, ag, s);
         if (e != cudaSuccess) return RLQR_ERR_CUDA;
       }
-  }
+    }
   return RLQR_OK;
 }
 
