@@ -49,8 +49,17 @@ struct WsLayout {
   size_t Qf;     // N n n (as given; readers take the upper triangle)
   size_t Mf;     // N n m
   size_t Rf;     // N m m (as given; readers take the upper triangle)
+  // mixed path, compile-time CTA sweep: state pivots whose FP32 Gershgorin
+  // proof failed are certified afterwards in FP64 from the stored FP32 P_i
+  size_t Pc;     // (N+1) n n FP32 P_i of the pending stages
+  size_t pend;   // (N+1) bytes: 1 = bit0 of flags[i] still to decide
   size_t total;
 };
+
+// (n, m) of the compile-time CTA sweep (seqx.cuh)
+__host__ __device__ constexpr bool seqx_size(int n, int m) {
+  return (n == 24 && m == 8) || (n == 32 && m == 8) || (n == 48 && m == 16);
+}
 
 __host__ __device__ inline WsLayout ws_layout(int N, int n, int m, int tsize) {
   WsLayout L;
@@ -82,6 +91,11 @@ __host__ __device__ inline WsLayout ws_layout(int N, int n, int m, int tsize) {
   o = align_up(o + (size_t)N * n * m * ts);
   L.Rf = o;
   o = align_up(o + (size_t)N * m * m * ts);
+  const bool cta_sizes = ts != 0 && seqx_size(n, m);
+  L.Pc = o;
+  o = align_up(o + (cta_sizes ? (size_t)(N + 1) * n * n * 4 : 0));
+  L.pend = o;
+  o = align_up(o + (cta_sizes ? (size_t)(N + 1) : 0));
   L.total = o;
   return L;
 }

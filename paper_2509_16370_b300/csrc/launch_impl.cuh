@@ -9,6 +9,7 @@
 #include "sweep32.cuh"
 #include "refine32.cuh"
 #include "residual32.cuh"
+#include "seqx.cuh"
 
 namespace rlqr {
 
@@ -106,6 +107,20 @@ static cudaError_t launch_solve_warp(const BatchArgs &a, cudaStream_t s) {
   X(6, 2)                  \
   X(12, 4)
 
+// FP64 certificate of the state pivots the FP32 CTA sweep left undecided:
+// 4 warps per block, about 8 warps per SM over the grid.
+template <int NX>
+cudaError_t launch_seqx_cert(const BatchArgs &a, cudaStream_t s) {
+  auto kern = k_seqx_cert<NX>;
+  const size_t bytes = (size_t)4 * NX * NX * sizeof(double);
+  cudaError_t e = set_smem(kern, bytes);
+  if (e != cudaSuccess) return e;
+  const int gy = std::max(1, std::min(65535, (148 * 2 + a.count - 1) / a.count));
+  LaunchScope ls("k_cert_state_fp64", s);
+  kern<<<dim3(a.count, gy), 128, bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T, bool SOLVE>
 cudaError_t launch_seq(int n, int m, bool uniform, const BatchArgs &a, cudaStream_t s) {
   if (uniform) {
@@ -113,6 +128,26 @@ cudaError_t launch_seq(int n, int m, bool uniform, const BatchArgs &a, cudaStrea
     if (n == NX && m == NU) return launch_seq_warp<T, NX, NU, SOLVE>(a, s);
     RLQR_WARP_SIZES(RLQR_SEQ_WARP)
 #undef RLQR_SEQ_WARP
+  }
+  if (uniform) {
+    // the larger compile-time sizes: register-tiled CTA sweep
+#define RLQR_SEQ_X(NX, NU)                                             \
+    if (n == NX && m == NU) {                                          \
+      auto kern = k_seqx<T, NX, NU, SOLVE>;                            \
+      const size_t bytes = sizeof(SxSmem<T, NX, NU>);                  \
+      cudaError_t e = set_smem(kern, bytes);                           \
+      if (e != cudaSuccess) return e;                                  \
+      LaunchScope ls(sizeof(T) == 4 ? (SOLVE ? "k_seq_fp32_solve" : "k_seq_fp32_factor") \
+                                    : (SOLVE ? "k_seq_fp64_solve" : "k_seq_fp64_factor"), s); \
+      kern<<<a.count, scan::kTH, bytes, s>>>(a);                       \
+      e = cudaGetLastError();                                          \
+      if (e != cudaSuccess || sizeof(T) != 4) return e;                \
+      return launch_seqx_cert<NX>(a, s);                               \
+    }
+    RLQR_SEQ_X(24, 8)
+    RLQR_SEQ_X(32, 8)
+    RLQR_SEQ_X(48, 16)
+#undef RLQR_SEQ_X
   }
   if (uniform && SOLVE) {
 #define RLQR_SEQ_FIXED(NX, NU, TH) \

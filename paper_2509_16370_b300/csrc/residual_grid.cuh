@@ -4,8 +4,8 @@
 // maxima of each instance by atomicMax on order-preserving bit patterns and
 // a per-instance finalize of the normwise backward error.  Work item g of the
 // flattened index belongs to instance b with spre[b] <= g < spre[b+1]
-// (spre: exclusive prefix sum of N_b + 1, from k_plan); item N_b of an
-// instance holds its rows x_N and c_0.  Included by rlqr_api.cu only.
+// (spre: exclusive prefix sum of N_b + 1, from k_plan; null for a single
+// instance); item N_b of an instance holds its rows x_N and c_0.  Included by rlqr_api.cu only.
 #pragma once
 
 #include "common.cuh"
@@ -14,6 +14,7 @@
 namespace rlqr {
 
 __device__ __forceinline__ int instance_of_item(const int64_t *spre, int count, int64_t g) {
+  if (!spre) return 0;  // one instance: items 0..N
   int lo = 0, hi = count;  // spre[lo] <= g < spre[hi]
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -40,7 +41,7 @@ __global__ void k_certb(BatchArgs a, const int64_t *spre, int64_t total) {
        g += (int64_t)gridDim.x * blockDim.x) {
     const int b = instance_of_item(spre, a.count, g);
     const Inst I = get_inst(a, b);
-    const int s = (int)(g - spre[b]);
+    const int s = (int)(g - (spre ? spre[b] : 0));
     if (s >= I.N) continue;
     const int m = I.m;
     const float *G = reinterpret_cast<const float *>(I.ws + I.L.G) + (size_t)s * m * m;
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(256) k_resb(BatchArgs a, const int64_t *spre, 
   for (int64_t g = w0; g < total; g += nw) {
     const int b = instance_of_item(spre, a.count, g);
     const Inst I = get_inst(a, b);
-    const int N = I.N, n = I.n, m = I.m, s = (int)(g - spre[b]);
+    const int N = I.N, n = I.n, m = I.m, s = (int)(g - (spre ? spre[b] : 0));
     const int nn = n * n, nm = n * m, mmm = m * m;
     const double delta = I.delta;
     double *rq = reinterpret_cast<double *>(I.ws + I.L.res);

@@ -40,14 +40,40 @@ static cudaError_t launch_residual(const BatchArgs &a, int rs_max, int store, do
   return cudaGetLastError();
 }
 
-// First residual of a mixed-precision solve (stored for the refinement, norms
-// recomputed, control pivots certified when cert_g): the compile-time-size
-// float-float kernel where it exists, the generic one otherwise.
-static cudaError_t launch_first_residual_mixed(const BatchArgs &a, int n, int m, bool uniform,
-                                               int rs_max, int cert_g, cudaStream_t s) {
-  cudaError_t e = launch_residual32<float>(n, m, uniform, a, cert_g, s);
-  if (e != cudaErrorNotSupported) return e;
-  return launch_residual(a, rs_max, 1, nullptr, nullptr, 1, 0, s, cert_g, 1, true);
+// Stage-parallel first residual over every instance of `a` (residual_grid.cuh):
+// spre is the work-item prefix sum of a batch (null for one instance), items
+// the number of work items (sum of N_b + 1).  Mixed: the residual is stored
+// for the refinement and, when cert_g, the control pivots are certified.
+static cudaError_t launch_grid_residual(const BatchArgs &a, const int64_t *spre, int64_t items,
+                                        bool mixed, int cert_g, cudaStream_t s) {
+  BatchArgs ab = a;
+  ab.perm = nullptr;
+  ab.goff = 0;
+  LaunchScope ls(mixed ? "k_residual_grid_ff" : "k_residual_grid_fp64", s);
+  const int cb = (int)std::min<int64_t>((ab.count + 255) / 256, 148 * 16);
+  k_resb_reset<<<cb, 256, 0, s>>>(ab);
+  if (mixed && cert_g)
+    k_certb<<<(int)std::min<int64_t>((items + 255) / 256, 148 * 16), 256, 0, s>>>(ab, spre, items);
+  k_resb<<<(int)std::min<int64_t>((items + 7) / 8, 148 * 16), 256, 0, s>>>(ab, spre, items,
+                                                                           mixed ? 1 : 0);
+  k_resb_final<<<cb, 256, 0, s>>>(ab);
+  return cudaGetLastError();
+}
+
+// Sizes with a compile-time warp residual (k_res32) take it; the rest take
+// the stage-parallel grid residual.
+static bool warp_residual_size(int n, int m) {
+  return (n == 4 && m == 2) || (n == 6 && m == 1) || (n == 6 && m == 2) || (n == 12 && m == 4);
+}
+
+// First residual of a uniform launch group (or one instance): stored for the
+// refinement and certifying the control pivots when cert_g (mixed), or the
+// FP64 backward error only.
+static cudaError_t launch_first_residual(const BatchArgs &a, int n, int m, bool mixed, int cert_g,
+                                         const int64_t *spre, int64_t items, cudaStream_t s) {
+  if (!warp_residual_size(n, m)) return launch_grid_residual(a, spre, items, mixed, cert_g, s);
+  if (mixed) return launch_residual32<float>(n, m, true, a, cert_g, s);
+  return launch_residual(a, 2 * n + m, 0, nullptr, nullptr, 1, 0, s);
 }
 
 // ---- ragged batches: size classes and the launch order
@@ -333,9 +359,7 @@ rlqr_status rlqr_solve(const rlqr_problem *prob, const rlqr_opts *opts, void *ws
                         : launch_solve<double, false>(n, m, true, a, s);
   if (e != cudaSuccess) return RLQR_ERR_CUDA;
   if (mixed || rel_resid) {
-    e = mixed ? launch_first_residual_mixed(a, prob->nx, prob->nu, true, 2 * prob->nx + prob->nu,
-                                            0, s)
-              : launch_residual(a, 2 * prob->nx + prob->nu, 0, nullptr, nullptr, 1, 0, s);
+    e = launch_first_residual(a, n, m, mixed, 0, nullptr, (int64_t)prob->N + 1, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
   if (mixed)
@@ -470,27 +494,18 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
     e = mixed ? launch_seq<float, true>(G.n, G.m, G.exact, ag, s)
               : launch_seq<double, true>(G.n, G.m, G.exact, ag, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
-    if (uniform && (mixed || rel_resid)) {
-      e = mixed ? launch_first_residual_mixed(ag, G.n, G.m, true, G.rs, 1, s)
-                : launch_residual(ag, G.rs, 0, nullptr, nullptr, 1, 0, s);
-      if (e != cudaSuccess) return RLQR_ERR_CUDA;
-    }
   }
-  if (!uniform && (mixed || rel_resid)) {
-    // ragged: one stage-parallel residual over every instance
+  if (mixed || rel_resid) {
+    // uniform: the group's first residual; ragged: one stage-parallel
+    // residual over every instance
     const int64_t *spre = reinterpret_cast<const int64_t *>(
         static_cast<char *>(ws) + align_up((size_t)B.count * sizeof(int64_t)) +
         align_up((size_t)B.count * sizeof(int32_t)));
     int64_t items = 0;
     for (int b = 0; b < B.count; ++b) items += (int64_t)B.h_N[b] + 1;
-    BatchArgs ab = a;
-    ab.perm = nullptr;
-    LaunchScope ls(mixed ? "k_residual_ff" : "k_residual_fp64", s);
-    k_resb_reset<<<(B.count + 255) / 256, 256, 0, s>>>(ab);
-    if (mixed) k_certb<<<(int)std::min<int64_t>((items + 255) / 256, 148 * 16), 256, 0, s>>>(ab, spre, items);
-    k_resb<<<148 * 16, 256, 0, s>>>(ab, spre, items, mixed ? 1 : 0);
-    k_resb_final<<<(B.count + 255) / 256, 256, 0, s>>>(ab);
-    if (cudaGetLastError() != cudaSuccess) return RLQR_ERR_CUDA;
+    e = uniform ? launch_first_residual(a, nmax, mmax, mixed, 1, spre, items, s)
+                : launch_grid_residual(a, spre, items, mixed, 1, s);
+    if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
   if (mixed)
     for (int g = 0; g < ng; ++g) {
@@ -554,8 +569,7 @@ rlqr_status rlqr_solve_noalloc(const rlqr_problem *prob, const rlqr_opts *opts, 
                         : launch_seq<double, true>(n, m, true, a, s);
   if (e != cudaSuccess) return RLQR_ERR_CUDA;
   if (mixed || rel_resid) {
-    e = mixed ? launch_first_residual_mixed(a, n, m, true, 2 * n + m, 1, s)
-              : launch_residual(a, 2 * n + m, 0, nullptr, nullptr, 1, 0, s);
+    e = launch_first_residual(a, n, m, mixed, 1, nullptr, (int64_t)prob->N + 1, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
   if (mixed)
