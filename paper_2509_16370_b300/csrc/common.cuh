@@ -460,6 +460,98 @@ __device__ __forceinline__ float abs_f32_trunc(double v) {
 
 __device__ __forceinline__ bool finite_nonzero(double d) { return isfinite(d) && d != 0.0; }
 
+// Proof in FP32, by one warp, that I + delta P is positive definite (delta >
+// 0; P symmetric FP32, row-major NX x NX, NX <= 64).  Method: the
+// verification of positive definiteness of S. M. Rump (BIT 46, 2006) applied
+// to A = P + I/delta, which is PD exactly when I + delta P is.  A is scaled
+// as D A D with D the powers of two nearest diag(A)^(-1/2) (exact), its
+// diagonal is lowered by c and the result S is Cholesky-factored (S = R^T R,
+// R upper) in FP32 with correctly rounded square roots and divisions.  If
+// that run completes (every pivot finite and positive), the backward error
+// of Cholesky (Demmel; Higham, "Accuracy and Stability of Numerical
+// Algorithms", Thm 10.5: R^T R = S + dS, |dS| <= gamma_{n+1} |R^T| |R|)
+// gives ||dS||_2 <= gamma_{n+1} / (1 - gamma_{n+1}) tr(S), so
+// lambda_min(D A D) >= c - ||dS||_2 - (underflow terms) > 0 for
+// c = gamma' tr + 2^-120, every bound rounded outward.  Returns 1 when the
+// proof succeeds; 0 decides nothing.  Registers only: lane l holds the upper
+// triangle's columns l and l + 32; row j of R reaches the other lanes by
+// shuffles.
+template <int NX>
+__device__ __noinline__ int warp_pd_proof_f32(const float *P, double delta) {
+  static_assert(NX >= 1 && NX <= 64, "one warp, two columns per lane");
+  constexpr int R0 = NX < 32 ? NX : 32;  // rows held for column lane (<= lane)
+  constexpr int R1 = NX > 32 ? NX : 1;   // rows held for column lane + 32
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int c0 = lane, c1 = lane + 32;
+  const bool h0 = c0 < NX, h1 = c1 < NX;
+  const float invd = __double2float_rd(__ddiv_rd(1.0, delta));  // <= 1/delta
+  // diagonal of A (rounded down), power-of-two scales, trace bound
+  auto scale_of = [](float a) {
+    int ex = 0;
+    frexpf(a, &ex);
+    return __int_as_float((127 - (ex >> 1)) << 23);  // 2^-(ex/2), a normal number
+  };
+  const float a0 = h0 ? __fadd_rd(__ldcg(P + c0 * NX + c0), invd) : 1.f;
+  const float a1 = h1 ? __fadd_rd(__ldcg(P + c1 * NX + c1), invd) : 1.f;
+  int bad = !(a0 > 0.f && a0 <= 3.0e38f) || !(a1 > 0.f && a1 <= 3.0e38f);
+  const float s0 = bad ? 1.f : scale_of(a0), s1 = bad ? 1.f : scale_of(a1);
+  float tr = __fadd_ru(h0 ? a0 * s0 * s0 : 0.f, h1 ? a1 * s1 * s1 : 0.f);
+  for (int o = 16; o > 0; o >>= 1) tr = __fadd_ru(tr, __shfl_xor_sync(FULL, tr, o));
+  if (__any_sync(FULL, bad)) return 0;
+  const float num = (float)(NX + 1) * 0x1p-24f;               // (n+1) u, exact
+  const float den = __fsub_rd(1.0f, __fmul_ru(2.0f, num));    // 1 - 2 (n+1) u
+  const float gam = __fmul_ru(__fdiv_ru(num, den), 1.01f);    // >= gamma/(1-gamma)
+  const float c = __fadd_ru(__fmul_ru(gam, tr), 0x1p-120f);
+  // this lane's columns of the upper triangle of S = D A D - c I
+  float x0[R0], x1[R1];
+#pragma unroll
+  for (int i = 0; i < R0; ++i) {
+    const float si = __shfl_sync(FULL, s0, i);
+    float v = 0.f;
+    if (h0 && i < c0) v = (si * __ldcg(P + i * NX + c0)) * s0;
+    if (h0 && i == c0) v = __fsub_rd(a0 * s0 * s0, c);
+    x0[i] = v;
+    bad |= !(fabsf(v) <= 3.0e38f);
+  }
+  if constexpr (NX > 32) {
+#pragma unroll
+    for (int i = 0; i < NX; ++i) {
+      const float si = __shfl_sync(FULL, i < 32 ? s0 : s1, i & 31);
+      float v = 0.f;
+      if (h1 && i < c1) v = (si * __ldcg(P + i * NX + c1)) * s1;
+      if (h1 && i == c1) v = __fsub_rd(a1 * s1 * s1, c);
+      x1[i] = v;
+      bad |= !(fabsf(v) <= 3.0e38f);
+    }
+  }
+  if (__any_sync(FULL, bad)) return 0;
+  // right-looking Cholesky
+#pragma unroll
+  for (int j = 0; j < NX; ++j) {
+    float d;
+    if (j < 32) d = __shfl_sync(FULL, x0[j < R0 ? j : 0], j);
+    else d = __shfl_sync(FULL, x1[j < R1 ? j : 0], j & 31);
+    if (!(d > 0.f && d <= 3.0e38f)) return 0;  // uniform over the warp
+    const float rj = __fsqrt_rn(d);
+    if (j < R0 && h0 && c0 > j) x0[j] = __fdiv_rn(x0[j], rj);
+    if constexpr (NX > 32) {
+      if (h1 && c1 > j) x1[j] = __fdiv_rn(x1[j], rj);
+    }
+#pragma unroll
+    for (int i = j + 1; i < NX; ++i) {
+      float uji;  // R_ji, held by the owner of column i
+      if (i < 32) uji = __shfl_sync(FULL, x0[j < R0 ? j : 0], i);
+      else uji = __shfl_sync(FULL, x1[j < R1 ? j : 0], i & 31);
+      if (i < R0 && c0 >= i) x0[i < R0 ? i : 0] = fmaf(-uji, x0[j < R0 ? j : 0], x0[i < R0 ? i : 0]);
+      if constexpr (NX > 32) {
+        if (c1 >= i && h1) x1[i] = fmaf(-uji, x1[j], x1[i]);
+      }
+    }
+  }
+  return 1;
+}
+
 // Block-wide max of non-negative doubles (all threads return the result).
 template <int THREADS>
 __device__ __forceinline__ double block_max(double v, double *scratch /* >= THREADS/32 */) {

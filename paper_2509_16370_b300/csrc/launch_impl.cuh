@@ -107,17 +107,19 @@ static cudaError_t launch_solve_warp(const BatchArgs &a, cudaStream_t s) {
   X(6, 2)                  \
   X(12, 4)
 
-// FP64 certificate of the state pivots the FP32 CTA sweep left undecided:
-// 4 warps per block, about 8 warps per SM over the grid.
+// Certificate of the state pivots the FP32 CTA sweep left undecided: the
+// FP32 proof, then the FP64 decision for what it did not prove.  4 warps per
+// block, about 32 warps per SM over the grid.
 template <int NX>
 cudaError_t launch_seqx_cert(const BatchArgs &a, cudaStream_t s) {
-  auto kern = k_seqx_cert<NX>;
+  const int gy = std::max(1, std::min(65535, (148 * 8 + a.count - 1) / a.count));
+  auto k64 = k_seqx_cert64<NX>;
   const size_t bytes = (size_t)4 * NX * NX * sizeof(double);
-  cudaError_t e = set_smem(kern, bytes);
+  cudaError_t e = set_smem(k64, bytes);
   if (e != cudaSuccess) return e;
-  const int gy = std::max(1, std::min(65535, (148 * 2 + a.count - 1) / a.count));
-  LaunchScope ls("k_cert_state_fp64", s);
-  kern<<<dim3(a.count, gy), 128, bytes, s>>>(a);
+  LaunchScope ls("k_cert_state", s);
+  k_seqx_cert<NX><<<dim3(a.count, gy), 128, 0, s>>>(a);
+  k64<<<dim3(a.count, gy), 128, bytes, s>>>(a);
   return cudaGetLastError();
 }
 

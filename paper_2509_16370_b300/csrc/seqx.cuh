@@ -7,8 +7,8 @@
 // eliminations of scan.cuh (one barrier per elimination step).  The next
 // stage's data is prefetched into registers during a stage.  Mixed path:
 // bit0 of a stage whose FP32 Gershgorin proof fails is decided afterwards by
-// k_seqx_cert in FP64 from the stored FP32 P_i, stage-parallel after the
-// sweep; the sweep writes bit0 = 1 there provisionally.
+// k_seqx_cert / k_seqx_cert64 from the stored FP32 P_i, stage-parallel after
+// the sweep; the sweep writes bit0 = 1 there provisionally.
 #pragma once
 
 #include "common.cuh"
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(scan::kTH) k_seqx(BatchArgs a) {
     __syncthreads();
     if constexpr (FP32) {
       // Gershgorin proof in FP32 with directed rounding; when it fails the
-      // stage's P is stored and k_seqx_cert decides bit0 in FP64 later,
+      // stage's P is stored and k_seqx_cert decides bit0 later,
       // off this instance's sequential chain
       if (tid < n) {
         float off = 0.f;
@@ -389,15 +389,34 @@ __global__ void __launch_bounds__(scan::kTH) k_seqx(BatchArgs a) {
   }
 }
 
-// Deferred FP64 certificate of the state pivots I + delta P_s whose FP32
-// Gershgorin proof failed in k_seqx (mixed path): unpivoted LDL^T of the
-// symmetric matrix, one warp per pending stage, the trailing triangle's
-// updates spread over the lanes.  Grid: x = instance slot, y (with the warps
-// of a block) strides over the stages 0..N.  Sets bit0 of flags[s] and
-// raises the instance's pivot status (and status output) to RLQR_NOT_PD or
-// RLQR_ERR_SINGULAR.
+// Deferred certificate of the state pivots I + delta P_s whose FP32
+// Gershgorin proof failed in k_seqx (mixed path), one warp per pending stage
+// (pend[s] = 1): the FP32 register proof of warp_pd_proof_f32; a stage it
+// does not prove is handed to k_seqx_cert64 (pend[s] = 2).  Grid: x =
+// instance slot, y (with the warps of a block) strides over the stages 0..N.
 template <int NX>
 __global__ void __launch_bounds__(128) k_seqx_cert(BatchArgs a) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+  const int slot = blockIdx.x;
+  if (slot >= a.count) return;
+  const Inst I = get_inst(a, inst_of(a, slot));
+  uint8_t *pend = reinterpret_cast<uint8_t *>(I.ws + I.L.pend);
+  const float *Pc = reinterpret_cast<const float *>(I.ws + I.L.Pc);
+  for (int st = blockIdx.y * nwb + wid; st <= I.N; st += gridDim.y * nwb) {
+    if (!__ldcg(pend + st)) continue;
+    // proven: bit0 stays as the sweep wrote it (1)
+    if (warp_pd_proof_f32<NX>(Pc + (size_t)st * NX * NX, I.delta)) continue;
+    if (lane == 0) pend[st] = 2;
+  }
+}
+
+// The FP64 decision for the stages the FP32 proof left open (pend[s] = 2):
+// unpivoted LDL^T of I + delta P_s in shared memory, one warp per stage, the
+// trailing triangle's updates spread over the lanes.  Sets bit0 of flags[s]
+// and raises the instance's pivot status (and status output) to RLQR_NOT_PD
+// or RLQR_ERR_SINGULAR.  Same grid as k_seqx_cert.
+template <int NX>
+__global__ void __launch_bounds__(128) k_seqx_cert64(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int n = NX, nn = NX * NX;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwb = blockDim.x >> 5;
@@ -410,7 +429,7 @@ __global__ void __launch_bounds__(128) k_seqx_cert(BatchArgs a) {
   const float *Pc = reinterpret_cast<const float *>(I.ws + I.L.Pc);
   int worst = RLQR_OK;
   for (int st = blockIdx.y * nwb + wid; st <= I.N; st += gridDim.y * nwb) {
-    if (!__ldcg(pend + st)) continue;
+    if (__ldcg(pend + st) != 2) continue;
     const float *P = Pc + (size_t)st * nn;
     __syncwarp();
     for (int e = lane; e < nn; e += 32) {

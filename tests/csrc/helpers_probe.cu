@@ -1,6 +1,7 @@
 // Test-only probe of the device helpers in the package's common.cuh: the
 // integer FP64 <-> FP32 conversions, the float-float split and dot product,
-// the pivot reciprocal and the FP32 Gershgorin test.  Compiled by the GPU
+// the pivot reciprocal, the FP32 Gershgorin test and the FP32 Cholesky proof
+// of positive definiteness.  Compiled by the GPU
 // tests with nvcc; every entry point takes device pointers, runs on the
 // default stream and returns the CUDA error code after synchronizing.
 #include <cuda_runtime.h>
@@ -51,6 +52,15 @@ __global__ void k_gersh(const float *P, int rows, int n, double delta, int *pass
   pass[r] = gershgorin_row_pd(row[i], off, __double2float_ru(delta)) ? 1 : 0;
 }
 
+// one warp per matrix: the FP32 proof that I + delta P_k is PD
+template <int NX>
+__global__ void k_pdproof(const float *P, int count, double delta, int *pass) {
+  const int k = blockIdx.x;
+  if (k >= count) return;
+  const int r = warp_pd_proof_f32<NX>(P + (size_t)k * NX * NX, delta);
+  if (threadIdx.x == 0) pass[k] = r;
+}
+
 static int finish() {
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -76,5 +86,13 @@ extern "C" int probe_recip(const float *d, float *r, int n) {
 }
 extern "C" int probe_gersh(const float *P, int rows, int n, double delta, int *pass) {
   k_gersh<<<(rows + 127) / 128, 128>>>(P, rows, n, delta, pass);
+  return finish();
+}
+
+extern "C" int probe_pdproof(const float *P, int count, int n, double delta, int *pass) {
+  if (n == 12) k_pdproof<12><<<count, 32>>>(P, count, delta, pass);
+  else if (n == 24) k_pdproof<24><<<count, 32>>>(P, count, delta, pass);
+  else if (n == 48) k_pdproof<48><<<count, 32>>>(P, count, delta, pass);
+  else return -1;
   return finish();
 }

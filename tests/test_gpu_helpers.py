@@ -10,6 +10,10 @@ against an independent definition computed on the host:
 * recip_pivot: within one FP32 ulp of the exact reciprocal;
 * gershgorin_row_pd: sound (a pass implies the exact rational test
   1 + delta (P_ii - sum |P_ij|) > 0) and not needlessly conservative.
+* warp_pd_proof_f32: sound (a pass implies that the smallest eigenvalue of
+  I + delta P, computed by LAPACK in FP64 from the exact FP32 P, is
+  positive), invariant to diagonal scaling, and passing every matrix whose
+  Jacobi-scaled smallest eigenvalue is clear of zero.
 """
 import ctypes
 import os
@@ -33,7 +37,8 @@ def probe(tmp_path_factory):
            os.path.join(HERE, "csrc", "helpers_probe.cu")]
     subprocess.run(cmd, check=True, capture_output=True)
     lib = ctypes.CDLL(str(out))
-    for name in ("probe_conv", "probe_widen", "probe_ffdot", "probe_recip", "probe_gersh"):
+    for name in ("probe_conv", "probe_widen", "probe_ffdot", "probe_recip", "probe_gersh",
+                 "probe_pdproof"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -172,3 +177,52 @@ def test_gershgorin_row_test_is_sound(probe):
             mag = 1 + dl * (abs(row[i]) + off)
             if val > Fraction(1, 10 ** 5) * mag:
                 assert pas[r], (delta, r, float(val))
+
+
+def _pd_cases(rng, n, delta, count):
+    """FP32 P with I + delta P of prescribed spectra, in a scaled basis:
+    M = D0 (V diag(lam) V^T) D0 with D0 spread over up to 8 decades (the
+    barrier-scaled diagonals), P = (M - I) / delta rounded to FP32."""
+    mats = []
+    for k in range(count):
+        V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        kind = k % 4
+        lam = 10.0 ** rng.uniform(-2, 2, n)
+        if kind == 1:    # indefinite: one eigenvalue slightly below zero
+            lam[0] = -10.0 ** rng.uniform(-9, -3) * lam.max()
+        elif kind == 2:  # PD, close to singular
+            lam[0] = 10.0 ** rng.uniform(-9, -5) * lam.max()
+        C = (V * lam) @ V.T
+        d0 = 10.0 ** rng.uniform(0, 4 if kind == 3 else 1, n)
+        M = d0[:, None] * C * d0[None, :]
+        P = ((M - np.eye(n)) / delta).astype(np.float32)
+        P = np.triu(P) + np.triu(P, 1).T  # exactly symmetric
+        mats.append(P)
+    return mats
+
+
+@pytest.mark.parametrize("n", [12, 24, 48])
+def test_fp32_cholesky_pd_proof(probe, n):
+    rng = np.random.default_rng(100 + n)
+    for delta in (1e-3, 0.3, 7.0):
+        mats = _pd_cases(rng, n, delta, 64)
+        P = np.stack(mats)
+        pas = torch.empty(len(mats), dtype=torch.int32, device="cuda")
+        assert probe.probe_pdproof(_ptr(_dev(P)), len(mats), n, ctypes.c_double(delta), _ptr(pas)) == 0
+        pas = pas.cpu().numpy()
+        passed = 0
+        for k, Pk in enumerate(mats):
+            M = np.eye(n) + delta * Pk.astype(np.float64)
+            lam_min = np.linalg.eigvalsh(M).min()
+            tol = 64 * n * np.finfo(np.float64).eps * np.abs(M).max()
+            if pas[k]:
+                # sound: a proof never passes a matrix that is not PD
+                assert lam_min > -tol, (n, delta, k, lam_min)
+                passed += 1
+            # complete where the Jacobi-scaled spectrum is clear of zero
+            d = 1.0 / np.sqrt(np.abs(np.diag(M)))
+            lam_s = np.linalg.eigvalsh(d[:, None] * M * d[None, :]).min()
+            if lam_s > 2e-3:
+                assert pas[k], (n, delta, k, lam_s)
+        assert passed >= len(mats) // 4
+
