@@ -16,6 +16,7 @@ is timed beside it, and the FP64 CPU oracle is the CPU baseline.
     python bench.py --profile-instances K   # profiling case, no bench line
     python bench.py --long-horizon          # the single long-horizon instance
     python bench.py --ragged K              # the first K instances of the ragged batch
+    python bench.py --ragged K --ragged-n 48   # only the n = 48 instances among them
 
 --long-horizon measures the other workload of the path: one instance with
 n_x = 32, n_u = 8, N = 65536 (delta = 1e-7, rho(A) = 0.99, Q and R with
@@ -310,9 +311,12 @@ def run_ragged(args):
     import multiprocessing as mp
     import torch
     from paper_2509_16370_b300 import inputs, rlqr
-    dims = inputs.workload4_dims(4096)[:args.ragged]
+    items = list(enumerate(inputs.workload4_dims(4096)[:args.ragged]))
+    if args.ragged_n:  # one size class of that sample
+        items = [(b, d) for b, d in items if d[1] == args.ragged_n]
+    dims = [d for _, d in items]
     with mp.get_context("spawn").Pool(min(32, os.cpu_count() or 1)) as pool:
-        probs = pool.map(_ragged_instance, list(enumerate(dims)), chunksize=4)
+        probs = pool.map(_ragged_instance, items, chunksize=4)
     db = rlqr.DeviceBatch.from_problems(probs)
     stages = sum(N for N, _, _ in dims)
     data_gb = sum(8 * ((N + 1) * n * n + N * (2 * n * m + m * m + n * n) + (N + 1) * n * 2 + N * m)
@@ -351,7 +355,9 @@ def run_ragged(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64 (FP32 sweep; FP64 certificate, residual, correction)",
             "data": "synthetic",
-            "config": {"workload": f"first {B} instances of the ragged batch of 4096 "
+            "config": {"workload": (f"the n={args.ragged_n} instances ({B}) of " if args.ragged_n
+                                    else f"{B} instances: ") +
+                                   f"the first {args.ragged} of the ragged batch of 4096 "
                                    "(N in 32..2048, n in {6,12,24,48}, m = n/3, barrier-scaled "
                                    "diagonals)", "instances": B, "stages": stages,
                        "data_gb": round(data_gb, 2)},
@@ -498,6 +504,8 @@ def main():
                     help="the single long-horizon instance (associative scan)")
     ap.add_argument("--ragged", type=int, default=0,
                     help="the first K instances of the ragged batch")
+    ap.add_argument("--ragged-n", type=int, default=0,
+                    help="with --ragged: only the instances of that state dimension")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
