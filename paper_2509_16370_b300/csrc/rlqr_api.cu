@@ -129,6 +129,36 @@ __global__ void k_group(int count, const int32_t *dN, const int32_t *dn, const i
   }
 }
 
+// Streams of the size classes of a ragged batch: one non-blocking stream per
+// class and device, created on first use and kept; the classes' launch
+// sequences are forked from the caller's stream and joined back with events
+// (which also places them in a graph when the caller's stream is being
+// captured).  The mutex orders the fork/join enqueues of concurrent callers.
+struct ClassStreams {
+  bool ok = false;
+  cudaStream_t st[kNumClasses];
+  cudaEvent_t fork, join[kNumClasses];
+};
+constexpr int kMaxClassDevices = 64;
+static ClassStreams g_class_streams[kMaxClassDevices];
+static std::mutex g_class_mu;
+
+static ClassStreams *class_streams_locked() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxClassDevices) return nullptr;
+  ClassStreams &cs = g_class_streams[dev];
+  if (!cs.ok) {
+    for (int c = 0; c < kNumClasses; ++c) {
+      if (cudaStreamCreateWithFlags(&cs.st[c], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&cs.join[c], cudaEventDisableTiming) != cudaSuccess)
+        return nullptr;
+    }
+    if (cudaEventCreateWithFlags(&cs.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    cs.ok = true;
+  }
+  return &cs;
+}
+
 // Header of a batch's workspace: per-instance byte offsets (int64), the
 // launch permutation of a ragged batch (int32), the exclusive prefix sum of
 // N_b + 1 (int64, count + 1 entries: the residual's work items).
@@ -488,13 +518,38 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
     ag.goff = groups[g].off;
     return ag;
   };
+  // several classes: each on its own stream, concurrently
+  std::unique_lock<std::mutex> lock(g_class_mu, std::defer_lock);
+  ClassStreams *cs = nullptr;
+  if (ng > 1) {
+    lock.lock();
+    cs = class_streams_locked();
+  }
+  auto gstream = [&](int g) { return cs ? cs->st[g] : s; };
+  auto fork = [&]() -> bool {
+    if (!cs) return true;
+    if (cudaEventRecord(cs->fork, s) != cudaSuccess) return false;
+    for (int g = 0; g < ng; ++g)
+      if (cudaStreamWaitEvent(cs->st[g], cs->fork, 0) != cudaSuccess) return false;
+    return true;
+  };
+  auto join = [&]() -> bool {
+    if (!cs) return true;
+    for (int g = 0; g < ng; ++g)
+      if (cudaEventRecord(cs->join[g], cs->st[g]) != cudaSuccess ||
+          cudaStreamWaitEvent(s, cs->join[g], 0) != cudaSuccess)
+        return false;
+    return true;
+  };
+  if (!fork()) return RLQR_ERR_CUDA;
   for (int g = 0; g < ng; ++g) {
     const Group &G = groups[g];
     const BatchArgs ag = group_args(g);
-    e = mixed ? launch_seq<float, true>(G.n, G.m, G.exact, ag, s)
-              : launch_seq<double, true>(G.n, G.m, G.exact, ag, s);
+    e = mixed ? launch_seq<float, true>(G.n, G.m, G.exact, ag, gstream(g))
+              : launch_seq<double, true>(G.n, G.m, G.exact, ag, gstream(g));
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
+  if (!join()) return RLQR_ERR_CUDA;
   if (mixed || rel_resid) {
     // uniform: the group's first residual; ragged: one stage-parallel
     // residual over every instance
@@ -507,15 +562,18 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
                 : launch_grid_residual(a, spre, items, mixed, 1, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
-  if (mixed)
+  if (mixed) {
+    if (!fork()) return RLQR_ERR_CUDA;
     for (int g = 0; g < ng; ++g) {
       const Group &G = groups[g];
       const BatchArgs ag = group_args(g);
       for (int it = 0; it < opts->max_refine; ++it) {
-        e = launch_solve<float, true>(G.n, G.m, G.exact, ag, s);
+        e = launch_solve<float, true>(G.n, G.m, G.exact, ag, gstream(g));
         if (e != cudaSuccess) return RLQR_ERR_CUDA;
       }
     }
+    if (!join()) return RLQR_ERR_CUDA;
+  }
   return RLQR_OK;
 }
 

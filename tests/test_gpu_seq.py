@@ -237,3 +237,44 @@ def test_ragged_workload4_sample(prec):
         ref = oracle.riccati(p)
         np.testing.assert_array_equal(f, ref.flags)
         assert oracle.residual(p, x, u, y).rel <= REL_TOL
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ragged_batch_graph_replay(prec):
+    """A ragged batch runs its size classes on the library's own streams,
+    forked from and joined back to the caller's stream: the call can be
+    captured into a CUDA graph, and a replay reproduces the eager call's
+    solution, flags, status and backward errors bit for bit."""
+    dims = inputs.workload4_dims(4096)[:24]
+    probs = [inputs.workload4_instance(b, min(N, 96), n, m) for b, (N, n, m) in enumerate(dims)]
+    assert len({(p.n, p.m) for p in probs}) > 1
+    db = rlqr.DeviceBatch.from_problems(probs)
+    opts = rlqr.make_opts(prec, tol=1e-9, max_refine=6)
+    ws = rlqr.alloc_workspace(rlqr.rlqr_batched_workspace_bytes(db, opts))
+    B = db.count
+    st = torch.full((B,), -1, dtype=torch.int32, device="cuda")
+    rel = torch.full((B,), -1.0, dtype=torch.float64, device="cuda")
+    it = torch.full((B,), -1, dtype=torch.int32, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):  # eager call (also creates the class streams)
+        rlqr.rlqr_solve_batched(db, opts, ws, st, rel, it)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    eager = [t.clone() for t in (db.x, db.u, db.y, db.pivot_pd, st, rel, it)]
+    for t in (db.x, db.u, db.y, rel):
+        t.fill_(float("nan"))
+    db.pivot_pd.fill_(0)
+    st.fill_(-1)
+    it.fill_(-1)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rlqr.rlqr_solve_batched(db, opts, ws, st, rel, it)
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(eager, (db.x, db.u, db.y, db.pivot_pd, st, rel, it)):
+        assert torch.equal(a, b)
+    for b, p in enumerate(probs):
+        x, u, y, f = db.instance_view(b)
+        np.testing.assert_array_equal(f, oracle.riccati(p).flags)
+        assert oracle.residual(p, x, u, y).rel <= REL_TOL
