@@ -60,18 +60,18 @@ static cudaError_t launch_grid_residual(const BatchArgs &a, const int64_t *spre,
   return cudaGetLastError();
 }
 
-// Sizes with a compile-time warp residual (k_res32) take it; the rest take
-// the stage-parallel grid residual.
-static bool warp_residual_size(int n, int m) {
-  return (n == 4 && m == 2) || (n == 6 && m == 1) || (n == 6 && m == 2) || (n == 12 && m == 4);
-}
-
 // First residual of a uniform launch group (or one instance): stored for the
 // refinement and certifying the control pivots when cert_g (mixed), or the
-// FP64 backward error only.
+// FP64 backward error only.  The sizes of the FP32 warp sweep take the
+// float-float warp residual (mixed) or the generic FP64 one; the rest take
+// the stage-parallel grid residual.
+static bool warp_sweep32_size(int n, int m) {
+  return (n == 4 && m == 2) || (n == 6 && m == 2) || (n == 12 && m == 4);
+}
+
 static cudaError_t launch_first_residual(const BatchArgs &a, int n, int m, bool mixed, int cert_g,
                                          const int64_t *spre, int64_t items, cudaStream_t s) {
-  if (!warp_residual_size(n, m)) return launch_grid_residual(a, spre, items, mixed, cert_g, s);
+  if (!warp_sweep32_size(n, m)) return launch_grid_residual(a, spre, items, mixed, cert_g, s);
   if (mixed) return launch_residual32<float>(n, m, true, a, cert_g, s);
   return launch_residual(a, 2 * n + m, 0, nullptr, nullptr, 1, 0, s);
 }

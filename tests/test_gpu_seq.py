@@ -61,7 +61,8 @@ CASES = [  # (seed, N, n, m, delta, with_M) spanning every kernel bucket and rag
     (1, 1, 1, 1, 1e-3, True), (2, 2, 3, 1, 0.0, True), (3, 7, 4, 2, 1e-2, True),
     (4, 33, 8, 4, 1e-6, True), (5, 5, 9, 3, 0.5, True), (6, 17, 12, 4, 1e-8, False),
     (7, 9, 16, 8, 1e-4, True), (8, 6, 17, 5, 1e-3, True), (9, 4, 32, 16, 1e-2, True),
-    (10, 3, 33, 11, 1e-5, True), (11, 3, 48, 16, 1e-7, True), (12, 40, 6, 2, 2.0, True)]
+    (10, 3, 33, 11, 1e-5, True), (11, 3, 48, 16, 1e-7, True), (12, 40, 6, 2, 2.0, True),
+    (13, 21, 6, 1, 1e-3, True), (14, 19, 24, 8, 1e-4, True), (15, 11, 32, 8, 1e-6, True)]
 
 
 @pytest.mark.parametrize("case", CASES, ids=[f"N{c[1]}n{c[2]}m{c[3]}" for c in CASES])
@@ -278,3 +279,24 @@ def test_ragged_batch_graph_replay(prec):
         x, u, y, f = db.instance_view(b)
         np.testing.assert_array_equal(f, oracle.riccati(p).flags)
         assert oracle.residual(p, x, u, y).rel <= REL_TOL
+
+
+@pytest.mark.parametrize("dims", [(6, 1), (12, 4), (24, 8), (32, 8), (48, 16), (10, 3)],
+                         ids=lambda d: f"n{d[0]}m{d[1]}")
+@pytest.mark.parametrize("prec", PRECS)
+def test_uniform_batch_every_residual_route(dims, prec):
+    """Uniform batches at the sizes of every first-residual route (float-float
+    warp residual, generic FP64 residual, stage-parallel grid residual) and
+    of every sweep kernel; horizons differ inside the batch."""
+    n, m = dims
+    probs = [inputs.random_instance(300 + b, N, n, m, 10.0 ** (-2 - b))
+             for b, N in enumerate((23, 7, 31))]
+    db = rlqr.DeviceBatch.from_problems(probs)
+    out = solve_batch(db, prec)
+    assert set(out["status"].tolist()) <= {rlqr.RLQR_OK, rlqr.RLQR_NOT_PD}
+    for b, p in enumerate(probs):
+        x, u, y, f = db.instance_view(b)
+        ref = oracle.riccati(p)
+        np.testing.assert_array_equal(f, ref.flags)
+        assert oracle.residual(p, x, u, y).rel <= REL_TOL
+        assert out["rel"][b] <= 1e-9 or prec == rlqr.RLQR_FP64
