@@ -50,15 +50,35 @@ TOL = 1e-9
 FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12  # 2 DFMA/clk/SM (measured rate), max SM clock
 
 
-def _dist():
+def _dist(backend: str = "nccl"):
+    """(rank, world size, local rank) from the torchrun environment; joins the
+    process group when there is more than one rank."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
         return 0, 1, 0
     import torch.distributed as dist
     rank = int(os.environ["RANK"])
     local = int(os.environ.get("LOCAL_RANK", rank))
-    dist.init_process_group("nccl")
+    if not dist.is_initialized():
+        dist.init_process_group(backend)
     return rank, ws, local
+
+
+def rank_max(value: float, world: int, device="cuda") -> float:
+    """The largest of a per-rank value over all ranks (the slowest rank's time
+    bounds the job); the value itself on one rank."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput of replicas: every rank processes units_per_rank
+    in at most ms_max milliseconds."""
+    return world * units_per_rank / (ms_max / 1e3)
 
 
 class ClockSampler:
@@ -408,11 +428,7 @@ def run_ours(args):
             rlqr.rlqr_instrument(False)
         if world > 1:
             torch.distributed.barrier()
-        ms = e0.elapsed_time(e1) / steps
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = rank_max(e0.elapsed_time(e1) / steps, world)
         stv = st.cpu().numpy()
         relv = rel.cpu().numpy()
         ok = bool(np.all(relv <= TOL) and np.all((stv == 0) | (stv == 1)))
@@ -455,16 +471,12 @@ def run_ours(args):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1) / e2e_steps
-    if world > 1:
-        t = torch.tensor([ms_e2e], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = rank_max(e0.elapsed_time(e1) / e2e_steps, world)
 
     if rank != 0:
         return
-    value = world * stages / (ms_mixed / 1e3)
-    fp64_value = world * stages / (ms_fp64 / 1e3)
+    value = job_rate(stages, world, ms_mixed)
+    fp64_value = job_rate(stages, world, ms_fp64)
     launches = sum(c for c, _ in report.values())
     line = {
         "metric": METRIC, "value": value, "unit": "stage-solves/s", "n_gpus": world,
@@ -481,7 +493,7 @@ def run_ours(args):
         "fp64_plain": {"value": fp64_value, "ms_per_step": ms_fp64,
                        "max_rel_resid": chk_fp64["max_rel"], "all_le_tol": chk_fp64["ok"]},
         "speedup_vs_fp64_plain": value / fp64_value,
-        "e2e": {"value": world * stages / (ms_e2e / 1e3), "unit": "stage-solves/s",
+        "e2e": {"value": job_rate(stages, world, ms_e2e), "unit": "stage-solves/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
         "clocks": clk.summary(),
     }
