@@ -222,6 +222,80 @@ rlqr_status rlqr_solve_noalloc(const rlqr_problem *prob, const rlqr_opts *opts, 
                                int32_t *status, rlqr_stream_t stream);
 
 /* ------------------------------------------------------------------ *
+ * Horizon shards of one long instance (one GPU per shard).            *
+ * ------------------------------------------------------------------ */
+
+/* The horizon [0, N] of one instance is split into G contiguous shards
+ * [s_g, e_g] (s_0 = 0, e_g = s_{g+1}, e_{G-1} = N).  Shard g is solved as an
+ * ordinary rlqr_problem with N_g = e_g - s_g stages whose arrays hold stages
+ * s_g .. e_g of Q, q, c and s_g .. e_g - 1 of M, R, r, A, B, except three
+ * boundary entries that the caller overwrites (dynamic-programming cut):
+ *   Q[N_g] = P_{e_g}, q[N_g] = p_{e_g}   (the cost-to-go after the shard;
+ *                                          the true Q_N, q_N for the last),
+ *   c[0]   = the initial term whose first state is x_{s_g} (the true c_0
+ *            for shard 0; rlqr_shard_entry for the others).
+ * The boundary values come from summaries the shards exchange (Section
+ * "Parallel Algorithm": interval elements compose with the associative rule
+ * of eq. lqr-gpu-combo; Corollary p-recurrence and Section "Composing Affine
+ * Functions" for the vector maps):
+ *   1. rlqr_shard_element on every shard, gathered -> rlqr_shard_boundary;
+ *   2. after rlqr_factor (with Q[N_g] = P_{e_g}) and a solve with
+ *      q[N_g] = 0: rlqr_shard_pmap, gathered -> rlqr_shard_p_end;
+ *   3. after a solve with the true q[N_g] and c[0] = 0: rlqr_shard_x_offset,
+ *      gathered -> rlqr_shard_x_start -> rlqr_shard_entry -> the final solve.
+ * Every call below is FP64 and stream-ordered; the shard calls need the
+ * scan sizes (nx, nu) in {(4,2), (6,2), (12,4), (32,8)}, delta > 0,
+ * opts->prec == RLQR_FP64 and opts->algo == RLQR_ALGO_SCAN; all pointers
+ * are device pointers to row-major FP64 arrays owned by the caller.  Host
+ * return: RLQR_ERR_ARG for invalid arguments, RLQR_ERR_WORKSPACE for a
+ * missing or small workspace, RLQR_ERR_CUDA for a launch error. */
+
+/* Interval element (P, A, C) of the shard's stages 0 .. N_g - 1 (its
+ * terminal entry is not used): elem = 3 n^2 doubles, P then A then C.
+ * Uses ws (rlqr_workspace_bytes of the shard) as scratch. */
+rlqr_status rlqr_shard_element(const rlqr_problem *shard, const rlqr_opts *opts, void *ws,
+                               size_t ws_bytes, double *elem, rlqr_stream_t stream);
+
+/* From the G gathered elements (G x 3 n^2, shard order) and Q_N (n^2):
+ * P_end = P_{e_g} (the composition of the elements of shards g+1 .. G-1 and
+ * the terminal element (Q_N, 0, 0)) and, when P_start is not NULL,
+ * P_start = P_{s_g} (shard g's element in front of that). */
+rlqr_status rlqr_shard_boundary(int32_t G, int32_t g, int32_t nx, int32_t nu,
+                                const double *elems, const double *QN, double *P_end,
+                                double *P_start, rlqr_stream_t stream);
+
+/* After rlqr_factor and rlqr_solve of the shard (SCAN, FP64) in ws: the p map
+ * p_0 = Phi p_{N_g} + phi of its p-recurrence, Phi = n^2 (the product of the
+ * chunk maps F_s ... F_{e-1}), phi = n (p_0 of that solve, which is the
+ * offset when q[N_g] was 0). */
+rlqr_status rlqr_shard_pmap(const rlqr_problem *shard, const rlqr_opts *opts, const void *ws,
+                            size_t ws_bytes, double *Phi, double *phi, rlqr_stream_t stream);
+
+/* p_{e_g} from the gathered maps (Phis G x n^2, phis G x n) and q_N (n):
+ * v = q_N, then v <- Phi_h v + phi_h for h = G-1 down to g+1. */
+rlqr_status rlqr_shard_p_end(int32_t G, int32_t g, int32_t nx, const double *Phis,
+                             const double *phis, const double *qN, double *p_end,
+                             rlqr_stream_t stream);
+
+/* psi = x_last - Phi^T x_first: the offset of the shard's x map
+ * x_{N_g} = Phi^T x_0 + psi from any of its solved trajectories (shard 0
+ * passes x_first = 0 so that psi is its true last state). */
+rlqr_status rlqr_shard_x_offset(int32_t nx, const double *Phi, const double *x_first,
+                                const double *x_last, double *psi, rlqr_stream_t stream);
+
+/* x_{s_g} for g >= 1 from the gathered maps (Phis G x n^2, psis G x n):
+ * v = psi_0, then v <- Phi_h^T v + psi_h for h = 1 .. g-1. */
+rlqr_status rlqr_shard_x_start(int32_t g, int32_t nx, const double *Phis, const double *psis,
+                               double *x_start, rlqr_stream_t stream);
+
+/* c0 = (I + delta P_start)(x_start - x_first): the initial term that gives
+ * the shard the first state x_start, where x_first is its first state with
+ * c[0] = 0 (eq. recover-x0: x_0 = (I + delta P_0)^{-1} (c_0 - delta p_0)). */
+rlqr_status rlqr_shard_entry(int32_t nx, double delta, const double *P_start,
+                             const double *x_start, const double *x_first, double *c0,
+                             rlqr_stream_t stream);
+
+/* ------------------------------------------------------------------ *
  * Instrumentation (no counterpart in the paper): per-kernel timing.    *
  * ------------------------------------------------------------------ */
 

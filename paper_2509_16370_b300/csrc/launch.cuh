@@ -82,4 +82,23 @@ cudaError_t launch_scan_residual(int n, int m, const BatchArgs &a, int cert_g, i
 template <typename T>
 cudaError_t launch_scan_norms(const BatchArgs &a, cudaStream_t s);
 
+// Horizon shards of one long instance, FP64 (shard.cu); cudaErrorNotSupported
+// for sizes without scan kernels.
+cudaError_t launch_shard_element(int n, int m, const BatchArgs &a, const ScanLayout &SL,
+                                 size_t sbase, double *elem, cudaStream_t s);
+cudaError_t launch_shard_boundary(int n, int m, int G, int g, const double *elems,
+                                  const double *QN, double *P_end, double *P_start,
+                                  cudaStream_t s);
+cudaError_t launch_shard_pmap(int n, int m, const BatchArgs &a, const ScanLayout &SL,
+                              size_t sbase, double *Phi, double *phi, cudaStream_t s);
+cudaError_t launch_shard_p_end(int G, int g, int n, const double *Phis, const double *phis,
+                               const double *qN, double *p_end, cudaStream_t s);
+cudaError_t launch_shard_x_start(int g, int n, const double *Phis, const double *psis,
+                                 double *x_start, cudaStream_t s);
+cudaError_t launch_shard_x_offset(int n, const double *Phi, const double *x_first,
+                                  const double *x_last, double *psi, cudaStream_t s);
+cudaError_t launch_shard_entry(int n, double delta, const double *P_start,
+                               const double *x_start, const double *x_first, double *c0,
+                               cudaStream_t s);
+
 }  // namespace rlqr

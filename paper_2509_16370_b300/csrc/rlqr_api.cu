@@ -638,6 +638,79 @@ rlqr_status rlqr_solve_noalloc(const rlqr_problem *prob, const rlqr_opts *opts, 
   return RLQR_OK;
 }
 
+// ---- horizon shards of one long instance
+static bool shard_ok(const rlqr_problem *p, const rlqr_opts *o) {
+  return valid_problem(p) && valid_opts(o) && o->prec == RLQR_FP64 &&
+         o->algo == RLQR_ALGO_SCAN && scan_sizes(p->nx, p->nu) && p->delta > 0.0;
+}
+
+rlqr_status rlqr_shard_element(const rlqr_problem *shard, const rlqr_opts *opts, void *ws,
+                               size_t ws_bytes, double *elem, rlqr_stream_t stream) {
+  if (!shard_ok(shard, opts) || !elem) return RLQR_ERR_ARG;
+  const size_t need = rlqr_workspace_bytes(shard->N, shard->nx, shard->nu, opts);
+  if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
+    return RLQR_ERR_WORKSPACE;
+  size_t sbase;
+  const ScanLayout SL = scan_args(shard, opts, &sbase);
+  const BatchArgs a = single_args(shard, opts, ws);
+  return cuda_status(launch_shard_element(shard->nx, shard->nu, a, SL, sbase, elem,
+                                          reinterpret_cast<cudaStream_t>(stream)));
+}
+
+rlqr_status rlqr_shard_boundary(int32_t G, int32_t g, int32_t nx, int32_t nu,
+                                const double *elems, const double *QN, double *P_end,
+                                double *P_start, rlqr_stream_t stream) {
+  if (G < 1 || g < 0 || g >= G || !scan_sizes(nx, nu) || !elems || !QN || !P_end)
+    return RLQR_ERR_ARG;
+  return cuda_status(launch_shard_boundary(nx, nu, G, g, elems, QN, P_end, P_start,
+                                           reinterpret_cast<cudaStream_t>(stream)));
+}
+
+rlqr_status rlqr_shard_pmap(const rlqr_problem *shard, const rlqr_opts *opts, const void *ws,
+                            size_t ws_bytes, double *Phi, double *phi, rlqr_stream_t stream) {
+  if (!shard_ok(shard, opts) || !Phi || !phi) return RLQR_ERR_ARG;
+  const size_t need = rlqr_workspace_bytes(shard->N, shard->nx, shard->nu, opts);
+  if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
+    return RLQR_ERR_WORKSPACE;
+  size_t sbase;
+  const ScanLayout SL = scan_args(shard, opts, &sbase);
+  const BatchArgs a = single_args(shard, opts, const_cast<void *>(ws));
+  return cuda_status(launch_shard_pmap(shard->nx, shard->nu, a, SL, sbase, Phi, phi,
+                                       reinterpret_cast<cudaStream_t>(stream)));
+}
+
+rlqr_status rlqr_shard_p_end(int32_t G, int32_t g, int32_t nx, const double *Phis,
+                             const double *phis, const double *qN, double *p_end,
+                             rlqr_stream_t stream) {
+  if (G < 1 || g < 0 || g >= G || nx < 1 || nx > 64 || !Phis || !phis || !qN || !p_end)
+    return RLQR_ERR_ARG;
+  return cuda_status(launch_shard_p_end(G, g, nx, Phis, phis, qN, p_end,
+                                        reinterpret_cast<cudaStream_t>(stream)));
+}
+
+rlqr_status rlqr_shard_x_offset(int32_t nx, const double *Phi, const double *x_first,
+                                const double *x_last, double *psi, rlqr_stream_t stream) {
+  if (nx < 1 || nx > 64 || !Phi || !x_first || !x_last || !psi) return RLQR_ERR_ARG;
+  return cuda_status(launch_shard_x_offset(nx, Phi, x_first, x_last, psi,
+                                           reinterpret_cast<cudaStream_t>(stream)));
+}
+
+rlqr_status rlqr_shard_x_start(int32_t g, int32_t nx, const double *Phis, const double *psis,
+                               double *x_start, rlqr_stream_t stream) {
+  if (g < 1 || nx < 1 || nx > 64 || !Phis || !psis || !x_start) return RLQR_ERR_ARG;
+  return cuda_status(launch_shard_x_start(g, nx, Phis, psis, x_start,
+                                          reinterpret_cast<cudaStream_t>(stream)));
+}
+
+rlqr_status rlqr_shard_entry(int32_t nx, double delta, const double *P_start,
+                             const double *x_start, const double *x_first, double *c0,
+                             rlqr_stream_t stream) {
+  if (nx < 1 || nx > 64 || !(delta >= 0.0) || !P_start || !x_start || !x_first || !c0)
+    return RLQR_ERR_ARG;
+  return cuda_status(launch_shard_entry(nx, delta, P_start, x_start, x_first, c0,
+                                        reinterpret_cast<cudaStream_t>(stream)));
+}
+
 rlqr_status rlqr_instrument(int enable) {
   g_instr.on = enable != 0;
   g_instr.n = 0;

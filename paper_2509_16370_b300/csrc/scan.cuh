@@ -357,9 +357,12 @@ __device__ __forceinline__ void store_elem(T *g, const T *P, const T *A, const T
 }  // namespace scan
 
 // Chunk elements into S0 (blocks 0..C-1) and the terminal element (block C).
+// ident_terminal: block C writes the identity element (0, I, 0) instead, so
+// that the suffix scan's first entry is the interval element of stages
+// 0..N-1 alone (a horizon shard's summary).
 template <typename T, int NX, int NU>
 __global__ void __launch_bounds__(scan::kTH) k_scan_reduce(BatchArgs a, ScanLayout SL,
-                                                           size_t sbase) {
+                                                           size_t sbase, int ident_terminal) {
   using SM = scan::CombSmem<T, NX, NU>;
   constexpr int n = NX, nn = n * n, LD = SM::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -377,8 +380,10 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_reduce(BatchArgs a, ScanLayo
     }
     for (int e = threadIdx.x; e < nn; e += blockDim.x) {
       const int r = e / n, col = e - r * n;
-      out[e] = scan::to_T<T>(__ldg(I.Q + (size_t)N * nn + (r <= col ? e : col * n + r)));
-      out[nn + e] = (T)0;
+      out[e] = ident_terminal
+                   ? (T)0
+                   : scan::to_T<T>(__ldg(I.Q + (size_t)N * nn + (r <= col ? e : col * n + r)));
+      out[nn + e] = (ident_terminal && r == col) ? (T)1 : (T)0;
       out[2 * nn + e] = (T)0;
     }
     return;

@@ -25,7 +25,7 @@ static cudaError_t scan_factor_sz(const BatchArgs &a, const ScanLayout &SL, size
     const size_t b = sizeof(scan::CombSmem<T, NX, NU>);
     if ((e = set_smem(k, b)) != cudaSuccess) return e;
     LaunchScope ls("k_scan_reduce", s);
-    k<<<SL.C + 1, scan::kTH, b, s>>>(a, SL, sbase);
+    k<<<SL.C + 1, scan::kTH, b, s>>>(a, SL, sbase, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   int from1 = 0;

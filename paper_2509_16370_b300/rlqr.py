@@ -81,6 +81,17 @@ def _load():
     lib.rlqr_solve_noalloc.restype = st
     lib.rlqr_solve_noalloc.argtypes = [P(rlqr_problem), P(rlqr_opts), _dp, _dp, _dp, _dp, _dp, _dp,
                                        _dp]
+    i32, dbl = ctypes.c_int32, ctypes.c_double
+    for name, args in (
+            ("rlqr_shard_element", [P(rlqr_problem), P(rlqr_opts), _dp, sz, _dp, _dp]),
+            ("rlqr_shard_boundary", [i32, i32, i32, i32, _dp, _dp, _dp, _dp, _dp]),
+            ("rlqr_shard_pmap", [P(rlqr_problem), P(rlqr_opts), _dp, sz, _dp, _dp, _dp]),
+            ("rlqr_shard_p_end", [i32, i32, i32, _dp, _dp, _dp, _dp, _dp]),
+            ("rlqr_shard_x_offset", [i32, _dp, _dp, _dp, _dp, _dp]),
+            ("rlqr_shard_x_start", [i32, i32, _dp, _dp, _dp, _dp]),
+            ("rlqr_shard_entry", [i32, dbl, _dp, _dp, _dp, _dp, _dp])):
+        getattr(lib, name).restype = st
+        getattr(lib, name).argtypes = args
     lib.rlqr_instrument.restype = st
     lib.rlqr_instrument.argtypes = [ctypes.c_int]
     lib.rlqr_instrument_report.restype = ctypes.c_int
@@ -321,3 +332,46 @@ def rlqr_solve_batched(batch: DeviceBatch, opts: rlqr_opts, ws: torch.Tensor, st
     _check(lib.rlqr_solve_batched(ctypes.byref(s), ctypes.byref(opts), _ptr(ws), ws.numel(),
                                   _ptr(status), _ptr(rel_resid), _ptr(iters), _stream(stream)),
            "rlqr_solve_batched")
+
+
+# ------------------------------------------------------------ horizon shards
+# Building blocks of the sharded long-horizon solve (see shard.py); every
+# tensor is a contiguous FP64 CUDA tensor.
+
+def rlqr_shard_element(shard: "DeviceProblem", opts: rlqr_opts, ws: torch.Tensor, elem, stream=None):
+    ps = shard.c_struct()
+    _check(lib.rlqr_shard_element(ctypes.byref(ps), ctypes.byref(opts), _ptr(ws), ws.numel(),
+                                  _ptr(elem), _stream(stream)), "rlqr_shard_element")
+
+
+def rlqr_shard_boundary(G: int, g: int, nx: int, nu: int, elems, QN, P_end, P_start=None,
+                        stream=None):
+    _check(lib.rlqr_shard_boundary(G, g, nx, nu, _ptr(elems), _ptr(QN), _ptr(P_end),
+                                   _ptr(P_start), _stream(stream)), "rlqr_shard_boundary")
+
+
+def rlqr_shard_pmap(shard: "DeviceProblem", opts: rlqr_opts, ws: torch.Tensor, Phi, phi,
+                    stream=None):
+    ps = shard.c_struct()
+    _check(lib.rlqr_shard_pmap(ctypes.byref(ps), ctypes.byref(opts), _ptr(ws), ws.numel(),
+                               _ptr(Phi), _ptr(phi), _stream(stream)), "rlqr_shard_pmap")
+
+
+def rlqr_shard_p_end(G: int, g: int, nx: int, Phis, phis, qN, p_end, stream=None):
+    _check(lib.rlqr_shard_p_end(G, g, nx, _ptr(Phis), _ptr(phis), _ptr(qN), _ptr(p_end),
+                                _stream(stream)), "rlqr_shard_p_end")
+
+
+def rlqr_shard_x_offset(nx: int, Phi, x_first, x_last, psi, stream=None):
+    _check(lib.rlqr_shard_x_offset(nx, _ptr(Phi), _ptr(x_first), _ptr(x_last), _ptr(psi),
+                                   _stream(stream)), "rlqr_shard_x_offset")
+
+
+def rlqr_shard_x_start(g: int, nx: int, Phis, psis, x_start, stream=None):
+    _check(lib.rlqr_shard_x_start(g, nx, _ptr(Phis), _ptr(psis), _ptr(x_start),
+                                  _stream(stream)), "rlqr_shard_x_start")
+
+
+def rlqr_shard_entry(nx: int, delta: float, P_start, x_start, x_first, c0, stream=None):
+    _check(lib.rlqr_shard_entry(nx, float(delta), _ptr(P_start), _ptr(x_start), _ptr(x_first),
+                                _ptr(c0), _stream(stream)), "rlqr_shard_entry")
