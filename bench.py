@@ -47,7 +47,7 @@ WORKLOAD = dict(workload="batch of 1024 dual-regularized LQRs, n_x=12, n_u=4, N=
                 instances=1024, N=256, n_x=12, n_u=4, l2="inputs 0.9 GB > L2 (no flush needed)")
 METRIC = "LQR stage-solves/s at KKT rel-resid <=1e-9 (mixed+batched; plain FP64 beside)"
 TOL = 1e-9
-FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12  # 2 DFMA/clk/SM (measured rate), max SM clock
+FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12  # 2 DFMA/clk/SM at the max SM clock (fallback)
 
 
 def _dist(backend: str = "nccl"):
@@ -155,7 +155,13 @@ def kernel_models(n, m, stages):
     }
 
 
-def roofline(report, steps, n, m, stages, peaks):
+def seq_flops_per_stage(n, m):
+    """Algorithmic FLOPs of one stage of the sequential recursion with
+    symmetry exploited: 16/3 n^3 + 5 n^2 m + 3 n m^2 + 1/3 m^3."""
+    return 16.0 / 3.0 * n ** 3 + 5.0 * n * n * m + 3.0 * n * m * m + m ** 3 / 3.0
+
+
+def roofline(report, steps, n, m, stages, peaks, fp64_tflops=None):
     k = [(ms, name, cnt) for name, (cnt, ms) in report.items() if name != "k_plan"]
     if not k:
         return None
@@ -168,8 +174,9 @@ def roofline(report, steps, n, m, stages, peaks):
         peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     else:
         achieved = work / per_launch_s / 1e12
-        peak = FP64_PEAK_TFLOPS
-        peak_src = "derived (148 SM x 2 FP64 FMA/clk x 2032 MHz)"
+        peak = fp64_tflops or FP64_PEAK_TFLOPS
+        peak_src = ("measured FP64 FMA rate (rlqr_measure_pipes)" if fp64_tflops
+                    else "derived (148 SM x 2 FP64 FMA/clk x 2032 MHz)")
     total = sum(v[1] for v in report.values())
     traffic = TRAFFIC_PER_STAGE.get(name)
     return {"kernel": name, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
@@ -177,6 +184,21 @@ def roofline(report, steps, n, m, stages, peaks):
             "traffic": None if traffic is None else traffic * stages,
             "algorithmic_bytes": work if bound == "hbm" else None,
             "launch_ms": round(ms / cnt, 4), "share": round(ms / total, 3)}
+
+
+def fp64_sweep_roofline(report, n, m, stages, pipes):
+    """The plain FP64 sweep against the measured FP64 FMA rate (the pipe that
+    bounds it on B300): algorithmic FLOPs of the recursion / launch time."""
+    name = "k_seq_fp64_solve"
+    if name not in report:
+        return None
+    cnt, ms = report[name]
+    achieved = seq_flops_per_stage(n, m) * stages / (ms / cnt / 1e3) / 1e12
+    peak = pipes["fp64_tflops"]
+    return {"kernel": name, "bound": "fp64", "achieved": round(achieved, 4),
+            "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+            "peak_source": "measured FP64 FMA rate (rlqr_measure_pipes)",
+            "flops_per_stage": round(seq_flops_per_stage(n, m), 1)}
 
 
 def load_peaks():
@@ -435,9 +457,12 @@ def run_ours(args):
         return ms, report, dict(max_rel=float(relv.max()), ok=ok, iters=int(it.max().item()),
                                 not_pd=int((stv == 1).sum()))
 
+    # the arithmetic pipes' measured rates (roofline denominators of the FP64
+    # and FP32 kernels), taken before the timed regions
+    pipes = rlqr.rlqr_measure_pipes()
     with ClockSampler(local) as clk:
         ms_mixed, report, chk_mixed = timed(rlqr.RLQR_MIXED, args.steps, args.warmup, True)
-    ms_fp64, _, chk_fp64 = timed(rlqr.RLQR_FP64, max(3, args.steps // 4), args.warmup)
+    ms_fp64, report64, chk_fp64 = timed(rlqr.RLQR_FP64, max(3, args.steps // 4), args.warmup, True)
 
     # end to end through the C ABI from pinned host buffers
     opts, ws, st, rel, it = setup(rlqr.RLQR_MIXED)
@@ -485,13 +510,15 @@ def run_ours(args):
         "dtype": "f32+f64 (FP32 sweep; FP64 certificate, residual, correction)",
         "data": "synthetic", "config": dict(WORKLOAD, parallelism=f"replicas x{world}",
                                               precision="mixed", max_refine=3, tol=TOL),
-        "roofline": roofline(report, args.steps, n, m, stages, load_peaks()),
+        "roofline": roofline(report, args.steps, n, m, stages, load_peaks(), pipes["fp64_tflops"]),
+        "pipes": {k: round(v, 2) for k, v in pipes.items()},
         "kernels": {k: {"launches": c, "ms_total": round(t, 4)} for k, (c, t) in report.items()},
         "gpu_launches": launches,
         "accuracy": {"max_rel_resid": chk_mixed["max_rel"], "all_le_tol": chk_mixed["ok"],
                      "max_refine_iters": chk_mixed["iters"], "not_pd_instances": chk_mixed["not_pd"]},
         "fp64_plain": {"value": fp64_value, "ms_per_step": ms_fp64,
-                       "max_rel_resid": chk_fp64["max_rel"], "all_le_tol": chk_fp64["ok"]},
+                       "max_rel_resid": chk_fp64["max_rel"], "all_le_tol": chk_fp64["ok"],
+                       "roofline": fp64_sweep_roofline(report64, n, m, stages, pipes)},
         "speedup_vs_fp64_plain": value / fp64_value,
         "e2e": {"value": job_rate(stages, world, ms_e2e), "unit": "stage-solves/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},

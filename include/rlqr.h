@@ -312,6 +312,14 @@ rlqr_status rlqr_instrument(int enable);
  * (entries beyond max are dropped), or -1 on a CUDA error. */
 int rlqr_instrument_report(int max, const char **names, int64_t *launches, double *ms);
 
+/* Microbenchmarks of the arithmetic pipes on the current device, for the
+ * roofline denominators: FP64 FMA, FP32 FMA and packed f32x2 FMA rates in
+ * TFLOP/s (2 flops per FMA lane-operation; independent chains over 4 CTAs
+ * of 256 threads per SM; best of 5 CUDA-event-timed launches).  Synchronous;
+ * allocates and frees a small device buffer (unlike the solver calls).
+ * RLQR_ERR_CUDA on any CUDA error. */
+rlqr_status rlqr_measure_pipes(double *fp64_tflops, double *fp32_tflops, double *fp32x2_tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,103 @@
+// pipes.cu -- microbenchmarks of the arithmetic pipes the hot path uses, for
+// the roofline denominators: FP64 FMA (the plain path and the certificates),
+// FP32 FMA and packed f32x2 FMA (the mixed path's sweeps).  Each thread runs
+// independent FMA chains (enough to cover the pipe latency) over a grid of
+// several CTAs per SM; rate = 2 flops per FMA lane-operation / CUDA-event time.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace rlqr {
+namespace {
+
+constexpr int kChains = 8;
+
+template <typename T>
+__global__ void k_pipe_fma(T *out, int iters, T a, T b) {
+  T acc[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) acc[c] = (T)(threadIdx.x + c);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) acc[c] = fma(acc[c], a, b);
+  }
+  T s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += acc[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void k_pipe_fma2(float *out, int iters, float a, float b) {
+  float2 acc[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) acc[c] = make_float2((float)threadIdx.x, (float)c);
+  const float2 a2 = bcast2(a), b2 = bcast2(b);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) acc[c] = fma2(acc[c], a2, b2);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += acc[c].x + acc[c].y;
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// Best of `reps` timed launches (after one warm-up) in milliseconds, or -1.
+template <typename F>
+float time_best(F launch, int reps) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1.f;
+  }
+  float best = -1.f;
+  launch();
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(e0);
+    launch();
+    cudaEventRecord(e1);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best < 0.f || ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return (cudaGetLastError() == cudaSuccess) ? best : -1.f;
+}
+
+}  // namespace
+}  // namespace rlqr
+
+using namespace rlqr;
+
+extern "C" rlqr_status rlqr_measure_pipes(double *fp64_tflops, double *fp32_tflops,
+                                          double *fp32x2_tflops) {
+  if (!fp64_tflops || !fp32_tflops || !fp32x2_tflops) return RLQR_ERR_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return RLQR_ERR_CUDA;
+  const int threads = 256, blocks = sms * 4;
+  void *buf = nullptr;
+  if (cudaMalloc(&buf, (size_t)blocks * threads * sizeof(double)) != cudaSuccess)
+    return RLQR_ERR_CUDA;
+  const double lanes = (double)blocks * threads * kChains;
+  const int it64 = 2048, it32 = 32768;
+  const float ms64 = time_best([&] {
+    k_pipe_fma<double><<<blocks, threads>>>((double *)buf, it64, 1.0000001, 1e-9);
+  }, 5);
+  const float ms32 = time_best([&] {
+    k_pipe_fma<float><<<blocks, threads>>>((float *)buf, it32, 1.0000001f, 1e-9f);
+  }, 5);
+  const float ms2 = time_best([&] {
+    k_pipe_fma2<<<blocks, threads>>>((float *)buf, it32, 1.0000001f, 1e-9f);
+  }, 5);
+  cudaFree(buf);
+  if (ms64 <= 0.f || ms32 <= 0.f || ms2 <= 0.f) return RLQR_ERR_CUDA;
+  *fp64_tflops = 2.0 * lanes * it64 / (ms64 * 1e-3) / 1e12;
+  *fp32_tflops = 2.0 * lanes * it32 / (ms32 * 1e-3) / 1e12;
+  *fp32x2_tflops = 2.0 * 2.0 * lanes * it32 / (ms2 * 1e-3) / 1e12;
+  return RLQR_OK;
+}

@@ -92,6 +92,8 @@ def _load():
             ("rlqr_shard_entry", [i32, dbl, _dp, _dp, _dp, _dp, _dp])):
         getattr(lib, name).restype = st
         getattr(lib, name).argtypes = args
+    lib.rlqr_measure_pipes.restype = st
+    lib.rlqr_measure_pipes.argtypes = [P(ctypes.c_double)] * 3
     lib.rlqr_instrument.restype = st
     lib.rlqr_instrument.argtypes = [ctypes.c_int]
     lib.rlqr_instrument_report.restype = ctypes.c_int
@@ -375,3 +377,11 @@ def rlqr_shard_x_start(g: int, nx: int, Phis, psis, x_start, stream=None):
 def rlqr_shard_entry(nx: int, delta: float, P_start, x_start, x_first, c0, stream=None):
     _check(lib.rlqr_shard_entry(nx, float(delta), _ptr(P_start), _ptr(x_start), _ptr(x_first),
                                 _ptr(c0), _stream(stream)), "rlqr_shard_entry")
+
+
+def rlqr_measure_pipes() -> dict:
+    """Measured FP64 / FP32 / packed-FP32 FMA rates of the current device in
+    TFLOP/s (synchronous microbenchmark)."""
+    v = [ctypes.c_double() for _ in range(3)]
+    _check(lib.rlqr_measure_pipes(*[ctypes.byref(x) for x in v]), "rlqr_measure_pipes")
+    return dict(fp64_tflops=v[0].value, fp32_tflops=v[1].value, fp32x2_tflops=v[2].value)

@@ -226,3 +226,13 @@ def test_fp32_cholesky_pd_proof(probe, n):
                 assert pas[k], (n, delta, k, lam_s)
         assert passed >= len(mats) // 4
 
+
+
+def test_measured_pipe_rates_are_consistent():
+    """rlqr_measure_pipes (the roofline denominators): positive rates, FP32
+    far above FP64 on this part, and the packed f32x2 FMA at least as fast
+    as the scalar one."""
+    from paper_2509_16370_b300 import rlqr
+    p = rlqr.rlqr_measure_pipes()
+    assert 0.0 < p["fp64_tflops"] < p["fp32_tflops"] / 10
+    assert p["fp32x2_tflops"] >= 0.9 * p["fp32_tflops"]
