@@ -49,7 +49,7 @@ static cudaError_t launch_grid_residual(const BatchArgs &a, const int64_t *spre,
   BatchArgs ab = a;
   ab.perm = nullptr;
   ab.goff = 0;
-  LaunchScope ls(mixed ? "k_residual_grid_ff" : "k_residual_grid_fp64", s);
+  LaunchScope ls("k_residual_grid", s);  // FP64 products in both precisions
   const int cb = (int)std::min<int64_t>((ab.count + 255) / 256, 148 * 16);
   k_resb_reset<<<cb, 256, 0, s>>>(ab);
   if (mixed && cert_g)

@@ -63,3 +63,11 @@ def solve_batch(dbatch, prec, max_refine=3, want_rel=True, tol=1e-9):
     torch.cuda.synchronize()
     return dict(status=status.cpu().numpy(), rel=None if rel is None else rel.cpu().numpy(),
                 iters=iters.cpu().numpy(), ws=ws)
+
+
+def workload4_item(arg):
+    """Instance b of the ragged workload with its (N, n, m) (a worker of a
+    spawn process pool)."""
+    from paper_2509_16370_b300 import inputs
+    b, (N, n, m) = arg
+    return inputs.workload4_instance(b, N, n, m)

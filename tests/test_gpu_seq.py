@@ -10,7 +10,8 @@ import torch
 import oracle
 from paper_2509_16370_b300 import inputs
 from paper_2509_16370_b300 import rlqr
-from tests.gpu_helpers import FWD_TOL, REL_TOL, check_against_oracle, solve_batch, solve_single
+from tests.gpu_helpers import (FWD_TOL, REL_TOL, check_against_oracle, solve_batch, solve_single,
+                               workload4_item)
 
 pytestmark = pytest.mark.gpu
 PRECS = [rlqr.RLQR_FP64, rlqr.RLQR_MIXED]
@@ -300,3 +301,29 @@ def test_uniform_batch_every_residual_route(dims, prec):
         np.testing.assert_array_equal(f, ref.flags)
         assert oracle.residual(p, x, u, y).rel <= REL_TOL
         assert out["rel"][b] <= 1e-9 or prec == rlqr.RLQR_FP64
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ragged_workload4_full_horizons(prec):
+    """The ragged bench's launch configuration at full size: the first 512
+    instances of the ragged batch (N up to 2048, n up to 48, barrier-scaled
+    diagonals) in one call.  Every instance's backward error on the GPU is
+    <= 1e-9; per state dimension the longest instance and three others are
+    checked by the oracle (flags byte-identical, oracle rel-resid <= 1e-9)."""
+    import multiprocessing as mp
+    import os
+    dims = inputs.workload4_dims(4096)[:512]
+    with mp.get_context("spawn").Pool(min(32, os.cpu_count() or 1)) as pool:
+        probs = pool.map(workload4_item, list(enumerate(dims)), chunksize=4)
+    db = rlqr.DeviceBatch.from_problems(probs)
+    out = solve_batch(db, prec, max_refine=6)
+    assert set(out["status"].tolist()) <= {rlqr.RLQR_OK, rlqr.RLQR_NOT_PD}
+    assert out["rel"].max() <= REL_TOL
+    for nx in (6, 12, 24, 48):
+        idx = [b for b, d in enumerate(dims) if d[1] == nx]
+        sample = sorted({max(idx, key=lambda b: dims[b][0])} | set(idx[:3]))
+        for b in sample:
+            x, u, y, f = db.instance_view(b)
+            ref = oracle.riccati(probs[b])
+            np.testing.assert_array_equal(f, ref.flags)
+            assert oracle.residual(probs[b], x, u, y).rel <= REL_TOL
