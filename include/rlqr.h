@@ -74,7 +74,11 @@ typedef enum {
  * affine x maps) has kernels for (nx, nu) in {(4,2), (6,2), (12,4), (32,8)},
  * needs delta > 0 and every R_i invertible, and applies to rlqr_factor /
  * rlqr_solve only (RLQR_ERR_ARG elsewhere or for other sizes).  AUTO takes
- * SCAN for N >= 4096 where it applies, SEQ otherwise; batches always run SEQ. */
+ * SCAN for N >= 4096 where it applies, SEQ otherwise; batches always run SEQ.
+ * An R_i with a zero or non-finite pivot in the scan's elimination makes the
+ * device status RLQR_ERR_SINGULAR (the host return stays RLQR_OK, as for
+ * every pivot decision); AUTO does not re-run such an instance with SEQ,
+ * which needs only the G_i invertible -- the caller can. */
 typedef enum {
   RLQR_ALGO_AUTO = 0,
   RLQR_ALGO_SEQ = 1,  /* sequential Riccati recursion, O(N) depth (Section "Sequential Algorithm") */

@@ -28,7 +28,7 @@ struct InstState {
   int32_t pivot_status;  // RLQR_OK / RLQR_NOT_PD / RLQR_ERR_SINGULAR from the sweep
   int32_t iters;         // refinement passes done
   int32_t converged;     // rel <= tol
-  int32_t pad;
+  int32_t r_singular;    // scan path: some R_i had a zero or non-finite pivot
 };
 
 // Byte offsets of the arrays of one instance's workspace.  `tsize` is the

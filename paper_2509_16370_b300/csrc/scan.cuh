@@ -260,6 +260,7 @@ struct CombSmem {
   T Q[NX * LD], A[NX * LD], B[NX * NU], M[NX * NU];
   T RX[NU * LDR];                            // [R | M^T | B^T]
   T rowbuf[2 * (3 * NX + 2)];                // pivot rows of the eliminations
+  int rbit, rsing;                           // pivot decisions of the R_i elimination
 };
 
 // The stage element (P, A, C)_{i->i+1} into (P1, A1, C1); eq. lqr-gpu-init-running.
@@ -289,7 +290,10 @@ __device__ void stage_element(const Inst &I, int i, CombSmem<T, NX, NU> &s) {
     s.RX[r * LDR + c] = to_T<T>(__ldg(R + (r <= c ? e : c * m + r)));
   }
   __syncthreads();
-  gjr<T, NU, NU + 2 * NX, kTH>(s.RX, LDR, s.rowbuf, nullptr, nullptr);  // R^{-1} [M^T | B^T]
+  // R^{-1} [M^T | B^T]; a zero or non-finite pivot of R_i is recorded in the
+  // instance state (the scan needs every R_i invertible)
+  gjr<T, NU, NU + 2 * NX, kTH>(s.RX, LDR, s.rowbuf, &s.rbit, &s.rsing);
+  if (tid == 0 && s.rsing) atomicOr(&I.st->r_singular, 1);
   // P = Q - M (R^{-1} M^T), A = A - B (R^{-1} M^T), C = delta I + B (R^{-1} B^T)
   mmt<T, NX, NX, NU, false, false>(s.P1, LD, s.M, m, s.RX + m, LDR, s.Q, LD, (T)-1);
   mmt<T, NX, NX, NU, false, false>(s.A1, LD, s.B, m, s.RX + m, LDR, s.A, LD, (T)-1);
@@ -371,6 +375,10 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_reduce(BatchArgs a, ScanLayo
   const int N = I.N, c = blockIdx.x;
   T *S0 = reinterpret_cast<T *>(I.ws + sbase + SL.S0);
   T *out = S0 + (size_t)c * 3 * nn;
+  if (threadIdx.x == 0) {
+    s.rbit = 1;
+    s.rsing = 0;
+  }
   if (c == SL.C) {  // terminal element (Q_N, 0, 0); instance state reset
     if (threadIdx.x == 0) {
       I.st->pivot_status = RLQR_OK;
@@ -698,6 +706,7 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_finalize(BatchArgs a, ScanLa
     }
   }
   if (tid == 0) {
+    if (__ldcg(&I.st->r_singular)) singular = 1;  // set by k_scan_reduce
     const int st = singular ? RLQR_ERR_SINGULAR : (notpd ? RLQR_NOT_PD : RLQR_OK);
     atomicMax(&I.st->pivot_status, st);
   }

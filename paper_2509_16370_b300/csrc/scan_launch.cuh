@@ -20,6 +20,10 @@ template <typename T, int NX, int NU>
 static cudaError_t scan_factor_sz(const BatchArgs &a, const ScanLayout &SL, size_t sbase,
                                   cudaStream_t s) {
   cudaError_t e;
+  // the R_i pivot record of this factorization starts clear
+  if ((e = cudaMemsetAsync(&reinterpret_cast<InstState *>(a.ws)->r_singular, 0, sizeof(int32_t),
+                           s)) != cudaSuccess)
+    return e;
   {
     auto k = k_scan_reduce<T, NX, NU>;
     const size_t b = sizeof(scan::CombSmem<T, NX, NU>);

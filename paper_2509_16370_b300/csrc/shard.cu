@@ -12,6 +12,9 @@ cudaError_t shard_element_sz(const BatchArgs &a, const ScanLayout &SL, size_t sb
                              double *elem, cudaStream_t s) {
   using CS = scan::CombSmem<double, NX, NU>;
   cudaError_t e;
+  if ((e = cudaMemsetAsync(&reinterpret_cast<InstState *>(a.ws)->r_singular, 0, sizeof(int32_t),
+                           s)) != cudaSuccess)
+    return e;
   {
     auto k = k_scan_reduce<double, NX, NU>;
     if ((e = set_smem(k, sizeof(CS))) != cudaSuccess) return e;
