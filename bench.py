@@ -15,6 +15,7 @@ is timed beside it, and the FP64 CPU oracle is the CPU baseline.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --profile-instances K   # profiling case, no bench line
     python bench.py --long-horizon          # the single long-horizon instance
+    python bench.py --latency               # latency of the small single instance
     python bench.py --ragged K              # the first K instances of the ragged batch
     python bench.py --ragged K --ragged-n 48   # only the n = 48 instances among them
 
@@ -271,6 +272,71 @@ def run_profile_case(args):
     torch.cuda.synchronize()
     print(f"profile case: {B} instances, max rel {rel.max().item():.3e}, "
           f"iters {it.max().item()}", flush=True)
+
+
+def run_latency(args):
+    """One JSON line for the small single instance (n=4, m=2, N=64): the
+    latency of rlqr_factor + rlqr_solve per call, launched one call after
+    another and replayed from a CUDA graph of the same calls, FP64 and mixed
+    (with refinement).  The configuration is bound by launch latency, not by
+    a pipe or HBM, so no roofline fraction is given."""
+    import torch
+    from paper_2509_16370_b300 import inputs, rlqr
+    p = inputs.workload1()
+    dp = rlqr.DeviceProblem.from_host(p)
+    N, n, m = p.N, p.n, p.m
+    out = {}
+    for name, prec, algo in (("fp64_seq", rlqr.RLQR_FP64, rlqr.RLQR_ALGO_SEQ),
+                             ("mixed_seq", rlqr.RLQR_MIXED, rlqr.RLQR_ALGO_SEQ),
+                             ("fp64_scan", rlqr.RLQR_FP64, rlqr.RLQR_ALGO_SCAN),
+                             ("mixed_scan", rlqr.RLQR_MIXED, rlqr.RLQR_ALGO_SCAN)):
+        opts = rlqr.make_opts(prec, algo=algo, tol=TOL, max_refine=3)
+        ws = rlqr.alloc_workspace(rlqr.rlqr_workspace_bytes(N, n, m, opts))
+        flags = torch.zeros(N + 1, dtype=torch.uint8, device="cuda")
+        x = torch.zeros(N + 1, n, dtype=torch.float64, device="cuda")
+        u = torch.zeros(N, m, dtype=torch.float64, device="cuda")
+        y = torch.zeros(N + 1, n, dtype=torch.float64, device="cuda")
+        rel = torch.zeros(1, dtype=torch.float64, device="cuda")
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+
+        def call():
+            rlqr.rlqr_factor(dp, opts, ws, flags)
+            rlqr.rlqr_solve(dp, opts, ws, x, u, y, rel)
+
+        with torch.cuda.stream(side):
+            for _ in range(args.warmup):
+                call()
+        torch.cuda.synchronize()
+        reps = max(args.steps, 20)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(side):
+            e0.record(side)
+            for _ in range(reps):
+                call()
+            e1.record(side)
+        torch.cuda.synchronize()
+        eager_us = e0.elapsed_time(e1) / reps * 1e3
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            call()
+        g.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        graph_us = e0.elapsed_time(e1) / reps * 1e3
+        out[name] = {"eager_us_per_call": round(eager_us, 2), "graph_us_per_call": round(graph_us, 2),
+                     "rel_resid": float(rel.item())}
+    best = min(out, key=lambda k: out[k]["graph_us_per_call"])
+    line = {"metric": "latency of one factor + solve (n=4, m=2, N=64)",
+            "value": out[best]["graph_us_per_call"], "unit": "us", "higher_is_better": False,
+            "n_gpus": 1, "steps": max(args.steps, 20), "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": "single instance n_x=4, n_u=2, N=64, delta=1e-6", "best": best},
+            **out}
+    print(json.dumps(line), flush=True)
 
 
 def run_long_horizon(args):
@@ -541,6 +607,8 @@ def main():
                     help="profiling case: the mixed solve on the first K instances only")
     ap.add_argument("--long-horizon", action="store_true",
                     help="the single long-horizon instance (associative scan)")
+    ap.add_argument("--latency", action="store_true",
+                    help="latency of one factor + solve of the small single instance")
     ap.add_argument("--ragged", type=int, default=0,
                     help="the first K instances of the ragged batch")
     ap.add_argument("--ragged-n", type=int, default=0,
@@ -554,6 +622,8 @@ def main():
         run_profile_case(args)
     elif args.long_horizon:
         run_long_horizon(args)
+    elif args.latency:
+        run_latency(args)
     elif args.ragged > 0:
         run_ragged(args)
     else:
