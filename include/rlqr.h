@@ -99,11 +99,16 @@ typedef struct {
   double delta; /* Delta_i = delta * I, delta >= 0 (0 = standard LQR, SEQ only) */
 } rlqr_problem;
 
+/* Option bits (rlqr_opts.flags). */
+#define RLQR_OPT_SYNC 1 /* single-instance calls wait for their stream and return the
+                           instance's status (see rlqr_factor / rlqr_solve) */
+
 typedef struct {
   int32_t max_refine; /* iterative-refinement passes after the first solve (MIXED); >= 0 */
   double tol;         /* target normwise backward error ||Kz+b|| / (||K|| ||z|| + ||b||) */
   rlqr_algo algo;
   rlqr_prec prec;
+  int32_t flags;      /* RLQR_OPT_* bits; 0 = stream-ordered, no host wait */
 } rlqr_opts;
 
 /* Default options: SEQ-or-SCAN automatic, FP64, tol 1e-9, max_refine 3. */
@@ -132,7 +137,10 @@ size_t rlqr_workspace_bytes(int32_t N, int32_t nx, int32_t nu, const rlqr_opts *
  * pivot_pd (device, N+1 bytes).  `ws` (device, >= rlqr_workspace_bytes,
  * 256-byte aligned) stays valid for rlqr_solve until the next rlqr_factor on
  * it.  The right-hand side (q, r, c) of `prob` is not read.  status (device
- * int32[1], may be NULL) receives the instance status. */
+ * int32[1], may be NULL) receives the instance status.  The host return
+ * covers argument and launch errors only, unless opts->flags has
+ * RLQR_OPT_SYNC: then the call waits for `stream` and returns the instance
+ * status (RLQR_NOT_PD, RLQR_ERR_SINGULAR) as well. */
 rlqr_status rlqr_factor(const rlqr_problem *prob, const rlqr_opts *opts, void *ws,
                         size_t ws_bytes, uint8_t *pivot_pd, int32_t *status,
                         rlqr_stream_t stream);
@@ -145,7 +153,10 @@ rlqr_status rlqr_factor(const rlqr_problem *prob, const rlqr_opts *opts, void *w
  * FP64 residual up to opts->max_refine times (Section "Residual
  * Computation").  rel_resid (device double[1], may be NULL in FP64 mode)
  * receives the final normwise backward error; iters (device int32[1], may be
- * NULL) the refinement passes taken.  `ws` is also used as solve scratch. */
+ * NULL) the refinement passes taken.  `ws` is also used as solve scratch.
+ * With RLQR_OPT_SYNC in opts->flags the call waits for `stream` and returns
+ * the instance status (RLQR_NOT_PD, RLQR_ERR_SINGULAR,
+ * RLQR_ERR_NOT_CONVERGED) instead of RLQR_OK. */
 rlqr_status rlqr_solve(const rlqr_problem *prob, const rlqr_opts *opts, void *ws,
                        size_t ws_bytes, double *x, double *u, double *y, double *rel_resid,
                        int32_t *iters, int32_t *status, rlqr_stream_t stream);
@@ -220,7 +231,8 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
  *   - Every call on a device shares the one array, which keeps the last
  *     call's contents; the per-instance state at its start is cleared by each
  *     call.  Calls whose executions overlap on the GPU (different streams,
- *     or host threads) race on the array: serialise them. */
+ *     or host threads) race on the array: serialise them.
+ *   - RLQR_OPT_SYNC in opts->flags works as for rlqr_solve. */
 rlqr_status rlqr_solve_noalloc(const rlqr_problem *prob, const rlqr_opts *opts, double *x,
                                double *u, double *y, uint8_t *pivot_pd, double *rel_resid,
                                int32_t *status, rlqr_stream_t stream);

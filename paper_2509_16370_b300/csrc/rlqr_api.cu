@@ -215,7 +215,23 @@ static bool valid_opts(const rlqr_opts *o) {
     return false;
   if (o->max_refine < 0 || o->max_refine > 64) return false;
   if (!(o->tol > 0.0) || !std::isfinite(o->tol)) return false;
+  if (o->flags & ~RLQR_OPT_SYNC) return false;
   return true;
+}
+
+// RLQR_OPT_SYNC: wait for the stream and turn the instance state at the
+// start of `ws` into the host return (factor: the pivot status; solve: the
+// status the device writes, convergence included for the mixed path).
+static rlqr_status sync_status(const rlqr_opts *o, const void *ws, bool solved, bool mixed,
+                               cudaStream_t s) {
+  if (!(o->flags & RLQR_OPT_SYNC)) return RLQR_OK;
+  InstState st;
+  if (cudaMemcpyAsync(&st, ws, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return RLQR_ERR_CUDA;
+  if (st.pivot_status == RLQR_ERR_SINGULAR) return RLQR_ERR_SINGULAR;
+  if (solved && mixed && !st.converged) return RLQR_ERR_NOT_CONVERGED;
+  return static_cast<rlqr_status>(st.pivot_status);
 }
 
 static bool valid_dims(int N, int n, int m) {
@@ -286,6 +302,7 @@ rlqr_opts rlqr_default_opts(void) {
   o.tol = 1e-9;
   o.algo = RLQR_ALGO_AUTO;
   o.prec = RLQR_FP64;
+  o.flags = 0;
   return o;
 }
 
@@ -337,15 +354,19 @@ rlqr_status rlqr_factor(const rlqr_problem *prob, const rlqr_opts *opts, void *w
     // mixed: FP64 certificate of the stored control pivots; status out
     e = mixed ? launch_scan_residual<float>(n, m, a, 1, 0, s)
               : launch_scan_residual<double>(n, m, a, 0, 0, s);
-    return cuda_status(e);
+    if (e != cudaSuccess) return RLQR_ERR_CUDA;
+    return sync_status(opts, ws, false, mixed, s);
   }
   if (opts->prec == RLQR_MIXED) {
     cudaError_t e = launch_seq<float, false>(n, m, true, a, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
     // FP64 certificate of the control pivots stored by the FP32 sweep
-    return cuda_status(launch_residual(a, 2 * n + m, 0, nullptr, nullptr, 0, 0, s, 1, 0));
+    e = launch_residual(a, 2 * n + m, 0, nullptr, nullptr, 0, 0, s, 1, 0);
+    if (e != cudaSuccess) return RLQR_ERR_CUDA;
+    return sync_status(opts, ws, false, true, s);
   }
-  return cuda_status(launch_seq<double, false>(n, m, true, a, s));
+  if (launch_seq<double, false>(n, m, true, a, s) != cudaSuccess) return RLQR_ERR_CUDA;
+  return sync_status(opts, ws, false, false, s);
 }
 
 rlqr_status rlqr_solve(const rlqr_problem *prob, const rlqr_opts *opts, void *ws,
@@ -383,7 +404,7 @@ rlqr_status rlqr_solve(const rlqr_problem *prob, const rlqr_opts *opts, void *ws
         if (e == cudaSuccess) e = launch_scan_norms<float>(a, s);
         if (e != cudaSuccess) return RLQR_ERR_CUDA;
       }
-    return RLQR_OK;
+    return sync_status(opts, ws, true, mixed, s);
   }
   cudaError_t e = mixed ? launch_solve<float, false>(n, m, true, a, s)
                         : launch_solve<double, false>(n, m, true, a, s);
@@ -397,7 +418,7 @@ rlqr_status rlqr_solve(const rlqr_problem *prob, const rlqr_opts *opts, void *ws
       e = launch_solve<float, true>(n, m, true, a, s);
       if (e != cudaSuccess) return RLQR_ERR_CUDA;
     }
-  return RLQR_OK;
+  return sync_status(opts, ws, true, mixed, s);
 }
 
 rlqr_status rlqr_residual(const rlqr_problem *prob, const double *x, const double *u,
@@ -635,7 +656,7 @@ rlqr_status rlqr_solve_noalloc(const rlqr_problem *prob, const rlqr_opts *opts, 
       e = launch_solve<float, true>(n, m, true, a, s);
       if (e != cudaSuccess) return RLQR_ERR_CUDA;
     }
-  return RLQR_OK;
+  return sync_status(opts, ws, true, mixed, s);
 }
 
 // ---- horizon shards of one long instance

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "librlqr.so")
 
 RLQR_OK, RLQR_NOT_PD, RLQR_ERR_ARG, RLQR_ERR_SINGULAR = 0, 1, 2, 3
 RLQR_ERR_NOT_CONVERGED, RLQR_ERR_TIMEOUT, RLQR_ERR_WORKSPACE, RLQR_ERR_CUDA = 4, 5, 6, 7
+RLQR_OPT_SYNC = 1
 RLQR_ALGO_AUTO, RLQR_ALGO_SEQ, RLQR_ALGO_SCAN = 0, 1, 2
 RLQR_FP64, RLQR_MIXED = 0, 1
 
@@ -42,7 +43,7 @@ class rlqr_problem(ctypes.Structure):
 
 class rlqr_opts(ctypes.Structure):
     _fields_ = [("max_refine", ctypes.c_int32), ("tol", ctypes.c_double), ("algo", ctypes.c_int),
-                ("prec", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("flags", ctypes.c_int32)]
 
 
 class rlqr_batch(ctypes.Structure):
@@ -114,6 +115,14 @@ def _check(code: int, what: str):
         raise RlqrError(f"{what}: {lib.rlqr_status_string(code).decode()} ({code})")
 
 
+def _check_call(code: int, what: str) -> int:
+    """Raise for a failed call (arguments, workspace, CUDA); return an
+    instance status (what RLQR_OPT_SYNC calls report) unchanged."""
+    if code in (RLQR_ERR_ARG, RLQR_ERR_WORKSPACE, RLQR_ERR_CUDA):
+        _check(code, what)
+    return int(code)
+
+
 def _ptr(t):
     if t is None:
         return None
@@ -131,9 +140,11 @@ def version() -> str:
     return lib.rlqr_version().decode()
 
 
-def make_opts(prec=RLQR_FP64, algo=RLQR_ALGO_AUTO, tol=1e-9, max_refine=3) -> rlqr_opts:
+def make_opts(prec=RLQR_FP64, algo=RLQR_ALGO_AUTO, tol=1e-9, max_refine=3,
+              sync=False) -> rlqr_opts:
     o = lib.rlqr_default_opts()
     o.prec, o.algo, o.tol, o.max_refine = int(prec), int(algo), float(tol), int(max_refine)
+    o.flags = RLQR_OPT_SYNC if sync else 0
     return o
 
 
@@ -196,16 +207,17 @@ def alloc_workspace(nbytes: int, device="cuda") -> torch.Tensor:
 def rlqr_factor(prob: DeviceProblem, opts: rlqr_opts, ws: torch.Tensor, pivot_pd: torch.Tensor,
                 status: torch.Tensor | None = None, stream=None):
     ps = prob.c_struct()
-    _check(lib.rlqr_factor(ctypes.byref(ps), ctypes.byref(opts), _ptr(ws), ws.numel(),
-                           _ptr(pivot_pd), _ptr(status), _stream(stream)), "rlqr_factor")
+    return _check_call(lib.rlqr_factor(ctypes.byref(ps), ctypes.byref(opts), _ptr(ws), ws.numel(),
+                                       _ptr(pivot_pd), _ptr(status), _stream(stream)),
+                       "rlqr_factor")
 
 
 def rlqr_solve(prob: DeviceProblem, opts: rlqr_opts, ws: torch.Tensor, x, u, y, rel_resid=None,
                iters=None, status=None, stream=None):
     ps = prob.c_struct()
-    _check(lib.rlqr_solve(ctypes.byref(ps), ctypes.byref(opts), _ptr(ws), ws.numel(), _ptr(x),
-                          _ptr(u), _ptr(y), _ptr(rel_resid), _ptr(iters), _ptr(status),
-                          _stream(stream)), "rlqr_solve")
+    return _check_call(lib.rlqr_solve(ctypes.byref(ps), ctypes.byref(opts), _ptr(ws), ws.numel(),
+                                      _ptr(x), _ptr(u), _ptr(y), _ptr(rel_resid), _ptr(iters),
+                                      _ptr(status), _stream(stream)), "rlqr_solve")
 
 
 def rlqr_residual(prob: DeviceProblem, x, u, y, res=None, norms=None, stream=None):
@@ -220,9 +232,10 @@ def rlqr_solve_noalloc(prob: DeviceProblem, opts: rlqr_opts, x, u, y, pivot_pd, 
     of a workspace: for callers that must not allocate device memory (see
     include/rlqr.h).  Concurrent calls on one device race on that scratch."""
     ps = prob.c_struct()
-    _check(lib.rlqr_solve_noalloc(ctypes.byref(ps), ctypes.byref(opts), _ptr(x), _ptr(u), _ptr(y),
-                                  _ptr(pivot_pd), _ptr(rel_resid), _ptr(status), _stream(stream)),
-           "rlqr_solve_noalloc")
+    return _check_call(lib.rlqr_solve_noalloc(ctypes.byref(ps), ctypes.byref(opts), _ptr(x),
+                                              _ptr(u), _ptr(y), _ptr(pivot_pd), _ptr(rel_resid),
+                                              _ptr(status), _stream(stream)),
+                       "rlqr_solve_noalloc")
 
 
 # ------------------------------------------------------------------- batches

@@ -80,3 +80,32 @@ def test_singular_R_scan_reports_sequential_solves(prec):
     ok = solve_single(inputs.random_instance(612, 64, 4, 2, 1e-3), prec,
                       algo=rlqr.RLQR_ALGO_SCAN)
     assert ok["status"] in (rlqr.RLQR_OK, rlqr.RLQR_NOT_PD)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_sync_option_returns_the_instance_status(prec):
+    """RLQR_OPT_SYNC: the single-instance calls wait for their stream and
+    return the instance status (here RLQR_ERR_SINGULAR for a NaN in the data,
+    RLQR_OK / RLQR_NOT_PD for a regular instance); without it the host return
+    stays RLQR_OK and the status is only on the device."""
+    for p, bad in ((inputs.random_instance(620, 40, 4, 2, 1e-3), False),
+                   (_poison(inputs.random_instance(621, 40, 4, 2, 1e-3), "Q", 9, np.nan), True)):
+        dp = rlqr.DeviceProblem.from_host(p)
+        for sync in (False, True):
+            opts = rlqr.make_opts(prec, sync=sync)
+            ws = rlqr.alloc_workspace(rlqr.rlqr_workspace_bytes(p.N, p.n, p.m, opts))
+            flags = torch.zeros(p.N + 1, dtype=torch.uint8, device="cuda")
+            x = torch.zeros(p.N + 1, p.n, dtype=torch.float64, device="cuda")
+            u = torch.zeros(p.N, p.m, dtype=torch.float64, device="cuda")
+            y = torch.zeros(p.N + 1, p.n, dtype=torch.float64, device="cuda")
+            rel = torch.zeros(1, dtype=torch.float64, device="cuda")
+            cf = rlqr.rlqr_factor(dp, opts, ws, flags)
+            cs = rlqr.rlqr_solve(dp, opts, ws, x, u, y, rel)
+            cn = rlqr.rlqr_solve_noalloc(dp, opts, x, u, y, flags, rel)
+            torch.cuda.synchronize()
+            if not sync:
+                assert (cf, cs, cn) == (rlqr.RLQR_OK,) * 3
+            elif bad:
+                assert (cf, cs, cn) == (rlqr.RLQR_ERR_SINGULAR,) * 3
+            else:
+                assert cf in (rlqr.RLQR_OK, rlqr.RLQR_NOT_PD) and cs == cn == cf
