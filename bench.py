@@ -426,10 +426,11 @@ def run_ragged(args):
     with mp.get_context("spawn").Pool(min(32, os.cpu_count() or 1)) as pool:
         probs = pool.map(_ragged_instance, items, chunksize=4)
     db = rlqr.DeviceBatch.from_problems(probs)
+    del probs  # the batch is on the device; at full size the host copy is ~76 GB
     stages = sum(N for N, _, _ in dims)
     data_gb = sum(8 * ((N + 1) * n * n + N * (2 * n * m + m * m + n * n) + (N + 1) * n * 2 + N * m)
                   for N, n, m in dims) / 1e9
-    B = len(probs)
+    B = len(dims)
 
     def timed(prec, steps, warmup, instrument=False):
         opts = rlqr.make_opts(prec, tol=TOL, max_refine=6)

@@ -109,10 +109,11 @@ static cudaError_t launch_solve_warp(const BatchArgs &a, cudaStream_t s) {
 
 // Certificate of the state pivots the FP32 CTA sweep left undecided: the
 // FP32 proof, then the FP64 decision for what it did not prove.  4 warps per
-// block, about 32 warps per SM over the grid.
+// block, about 32 warps per SM over the grid and at least 16 warps per
+// instance (its stages spread over them).
 template <int NX>
 cudaError_t launch_seqx_cert(const BatchArgs &a, cudaStream_t s) {
-  const int gy = std::max(1, std::min(65535, (148 * 8 + a.count - 1) / a.count));
+  const int gy = std::max(4, std::min(65535, (148 * 8 + a.count - 1) / a.count));
   auto k64 = k_seqx_cert64<NX>;
   const size_t bytes = (size_t)4 * NX * NX * sizeof(double);
   cudaError_t e = set_smem(k64, bytes);
