@@ -99,6 +99,9 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()  # the sampler runs before the timed region starts
+            while not self.rows and time.time() - t0 < 3.0:
+                time.sleep(0.02)
         except OSError:
             self.proc = None
         return self
@@ -599,7 +602,10 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 500 for the batch workload, so that the clock "
+                         "sampler sees the timed region; 20 for the reference arm and "
+                         "--latency, 3 for --ragged and --long-horizon)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -617,6 +623,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.steps is None:
+        args.steps = (20 if args.impl == "reference" or args.latency else
+                      3 if (args.ragged or args.long_horizon) else
+                      1 if args.profile_instances else 500)
     if args.impl == "reference":
         run_reference(args)
     elif args.profile_instances > 0:

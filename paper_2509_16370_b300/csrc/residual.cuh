@@ -21,18 +21,12 @@ namespace rlqr {
 // divergence, which on B300 would cost FP64 issue slots on idle lanes).  The
 // rows x_N and c_0 are a short epilogue.
 //
-// FF selects the arithmetic of the dot products: false = FP64 FMAs (plain
-// FP64 path and the public rlqr_residual); true = float-float on the FP32
-// pipes (mixed path), each term within about 2^-45 of |K_ij z_j|, which
-// leaves the backward error accurate to ~1e-13 against a 1e-9 target.
-//
 // `store` writes res into the workspace for a following correction solve.
 // `res_out` (single-instance API) is an optional caller buffer in the same
 // res_q | res_r | res_c layout, and `norms_out` receives
 // [rmax, kmax, zmax, bmax, rel].  `standalone`: no workspace (rlqr_residual);
 // the instance state is local.  `recompute_norms`: take ||K|| and ||b|| here
 // instead of from the sweep.
-template <bool FF>
 __global__ void k_residual(BatchArgs a, int store, double *res_out, double *norms_out,
                            int recompute_norms, int standalone, int rs_max, int cert_g,
                            int do_residual) {
@@ -111,103 +105,13 @@ __global__ void k_residual(BatchArgs a, int store, double *res_out, double *norm
   if (!do_residual) return;
 
   // the c-row x y-column block is identically zero
-  if constexpr (FF) {
-    float2 *Kf = reinterpret_cast<float2 *>(Kb);
-    for (int e = lane; e < n * n; e += 32)
-      Kf[(n + m + e / n) * ld + n + m + e % n] = make_float2(0.f, 0.f);
-  } else {
-    for (int e = lane; e < n * n; e += 32) Kb[(n + m + e / n) * ld + n + m + e % n] = 0.0;
-  }
+  for (int e = lane; e < n * n; e += 32) Kb[(n + m + e / n) * ld + n + m + e % n] = 0.0;
 
   for (int s = warp; s < N; s += nwarps) {
     const double *Qs = I.Q + (size_t)s * nn, *Ms = I.M + (size_t)s * nm;
     const double *Rs = I.R + (size_t)s * mmm, *As = I.A + (size_t)s * nn;
     const double *Bs = I.B + (size_t)s * nm;
     __syncwarp();
-    if constexpr (FF) {
-      // block entries as float-float pairs; ||K|| row sums from the hi parts
-      float2 *Kf = reinterpret_cast<float2 *>(Kb);
-      float2 *zf = reinterpret_cast<float2 *>(zb);
-      float2 *bf = reinterpret_cast<float2 *>(base);
-      for (int e = lane; e < nn; e += 32) {
-        const int i = e / n, j = e % n;
-        const float2 av = split_f64(__ldg(As + e));
-        if (i <= j) {
-          const float2 q = split_f64(__ldg(Qs + e));
-          Kf[i * ld + j] = q;
-          Kf[j * ld + i] = q;
-        }
-        Kf[(n + m + i) * ld + j] = av;
-        Kf[j * ld + n + m + i] = av;
-      }
-      for (int e = lane; e < nm; e += 32) {
-        const int i = e / m, j = e % m;
-        const float2 mv = split_f64(__ldg(Ms + e)), bv = split_f64(__ldg(Bs + e));
-        Kf[i * ld + n + j] = mv;
-        Kf[(n + j) * ld + i] = mv;
-        Kf[(n + m + i) * ld + n + j] = bv;
-        Kf[(n + j) * ld + n + m + i] = bv;
-      }
-      for (int e = lane; e < mmm; e += 32) {
-        const int i = e / m, j = e % m;
-        if (i <= j) {
-          const float2 rv = split_f64(__ldg(Rs + e));
-          Kf[(n + i) * ld + n + j] = rv;
-          Kf[(n + j) * ld + n + i] = rv;
-        }
-      }
-      for (int r = lane; r < rs; r += 32) {
-        double zv;
-        float bh = 0.f, bl = 0.f;
-        if (r < n) {
-          zv = __ldg(I.x + (size_t)s * n + r);
-          const double qv = __ldg(I.q + (size_t)s * n + r);
-          ff_add(bh, bl, split_f64(qv));
-          ff_add(bh, bl, ff_neg(split_f64(__ldg(I.y + (size_t)s * n + r))));
-          if (recompute_norms) bbits = max(bbits, abs_bits(qv));
-        } else if (r < n + m) {
-          zv = __ldg(I.u + (size_t)s * m + r - n);
-          const double rv = __ldg(I.r + (size_t)s * m + r - n);
-          ff_add(bh, bl, split_f64(rv));
-          if (recompute_norms) bbits = max(bbits, abs_bits(rv));
-        } else {
-          const size_t o = (size_t)(s + 1) * n + r - n - m;
-          zv = __ldg(I.y + o);
-          const double cv = __ldg(I.c + o);
-          ff_add(bh, bl, split_f64(cv));
-          ff_add(bh, bl, ff_neg(split_f64(__ldg(I.x + o))));
-          ff_fma(bh, bl, ff_neg(split_f64(delta)), split_f64(zv));
-          if (recompute_norms) bbits = max(bbits, abs_bits(cv));
-        }
-        zf[r] = split_f64(zv);
-        bf[r] = make_float2(bh, bl);
-        zbits = max(zbits, abs_bits(zv));
-      }
-      __syncwarp();
-      for (int r = lane; r < rs; r += 32) {
-        float sh = bf[r].x, sl = bf[r].y;
-        const float2 *row = Kf + r * ld;
-        for (int j = 0; j < rs; ++j) ff_fma(sh, sl, row[j], zf[j]);
-        if (recompute_norms) {
-          float ra = (r < n) ? 1.f : ((r < n + m) ? 0.f : 1.f + abs_f32_trunc(delta));
-          for (int j = 0; j < rs; ++j) ra += fabsf(row[j].x);
-          kmaxf = fmaxf(kmaxf, ra);
-        }
-        const double v = widen(sh) + widen(sl);
-        rbits = max(rbits, abs_bits(v));
-        if (r < n) {
-          if (store) rq[(size_t)s * n + r] = v;
-          if (oq) oq[(size_t)s * n + r] = v;
-        } else if (r < n + m) {
-          if (store) rr[(size_t)s * m + r - n] = v;
-          if (orr) orr[(size_t)s * m + r - n] = v;
-        } else {
-          if (store) rc[(size_t)(s + 1) * n + r - n - m] = v;
-          if (oc) oc[(size_t)(s + 1) * n + r - n - m] = v;
-        }
-      }
-      continue;
-    }
     for (int e = lane; e < nn; e += 32) {
       const int i = e / n, j = e % n;
       const double q = __ldg(Qs + e), av = __ldg(As + e);

@@ -25,16 +25,15 @@ Instr g_instr;
 // of the largest instance fit in shared memory.
 static cudaError_t launch_residual(const BatchArgs &a, int rs_max, int store, double *res_out,
                                    double *norms_out, int recompute, int standalone,
-                                   cudaStream_t s, int cert_g = 0, int do_residual = 1,
-                                   bool ff = false) {
+                                   cudaStream_t s, int cert_g = 0, int do_residual = 1) {
   const size_t per_warp = residual_warp_bytes(rs_max);
   int warps = (int)std::min<size_t>(8, (200u * 1024u) / per_warp);
   warps = std::max(warps, 1);
   const size_t bytes = per_warp * warps;
-  auto kern = ff ? k_residual<true> : k_residual<false>;
+  auto kern = k_residual;
   cudaError_t e = set_smem(kern, bytes);
   if (e != cudaSuccess) return e;
-  LaunchScope ls(!do_residual ? "k_cert_fp64" : (ff ? "k_residual_ff" : "k_residual_fp64"), s);
+  LaunchScope ls(!do_residual ? "k_cert_fp64" : "k_residual_fp64", s);
   kern<<<a.count, 32 * warps, bytes, s>>>(a, store, res_out, norms_out, recompute, standalone,
                                          rs_max, cert_g, do_residual);
   return cudaGetLastError();
