@@ -22,6 +22,9 @@ What it computes (citations are to the paper's sections and equations):
   pivoting in the interleaved order (for sizes where a dense factor is too big).
 * ``residual``     -- the stagewise residual of Section "Residual Computation"
   and the normwise backward error.
+* ``cross_stage_solve`` -- Section "Cross-Stage Variables": the bordered
+  system [[K, J], [J^T, H]] [dw; dtheta] = -[b; r_theta], assembled densely
+  from ``kkt_dense`` and solved by numpy (the plain definition).
 
 Pins (tests/test_oracle_*.py) tie every function to something other than
 itself: the paper's two worked examples, exact rational solves of the
@@ -244,6 +247,27 @@ def join_solution(prob, x, u, y):
             parts.append(np.asarray(u[i], dtype=np.float64))
     parts.append(np.asarray(y, dtype=np.float64).reshape(-1))
     return np.concatenate(parts)
+
+
+def cross_stage_solve(prob, Jq, Jr, Jc, H, r_theta):
+    """Section "Cross-Stage Variables", eq. cross-stage-kkt: with K, b of
+    ``kkt_dense`` and the p columns of J_theta given in the layout of the
+    right-hand side (Jq: (p, N+1, n) pairs with x, Jr: (p, N, m) with u,
+    Jc: (p, N+1, n) with y), solve [[K, J], [J^T, H]] [dw; dtheta] =
+    -[b; r_theta] densely.  Returns (x, u, y) of dw and dtheta."""
+    K, b = kkt_dense(prob)
+    p = len(r_theta)
+    J = np.stack([join_solution(prob, Jq[j], Jr[j], Jc[j]) for j in range(p)], axis=1)
+    dim = K.shape[0]
+    big = np.zeros((dim + p, dim + p))
+    big[:dim, :dim] = K
+    big[:dim, dim:] = J
+    big[dim:, :dim] = J.T
+    big[dim:, dim:] = np.asarray(H, dtype=np.float64)
+    rhs = -np.concatenate([b, np.asarray(r_theta, dtype=np.float64)])
+    sol = np.linalg.solve(big, rhs)
+    x, u, y = split_solution(prob, sol[:dim])
+    return x, u, y, sol[dim:]
 
 
 def bk_factor(K):

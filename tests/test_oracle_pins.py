@@ -410,3 +410,59 @@ def test_pins_detect_planted_mistakes(mutation):
     r = oracle.riccati(bad)
     assert oracle.forward_error(truth, r.x, r.u, r.y) > 1e-3
     assert oracle.residual(p, r.x, r.u, r.y).rel > 1e-6
+
+
+# ------------------------------------------- cross-stage variables
+
+def _cross_terms(seed, prob, p_theta):
+    rng = np.random.default_rng(seed)
+    N, n, m = prob.N, prob.n, prob.m
+    ri = lambda *s: rng.integers(-2, 3, size=s).astype(float)  # noqa: E731
+    Hs = ri(p_theta, p_theta)
+    H = Hs + Hs.T + 5 * np.eye(p_theta)
+    return ri(p_theta, N + 1, n), ri(p_theta, N, m), ri(p_theta, N + 1, n), H, ri(p_theta)
+
+
+@pytest.mark.parametrize("seed,N,n,m,delta,p_theta", [(21, 2, 2, 1, 0.5, 1), (22, 2, 1, 1, 1.0, 2),
+                                                       (23, 1, 2, 1, 0.25, 2)])
+def test_cross_stage_exact_rational(seed, N, n, m, delta, p_theta):
+    """Section "Cross-Stage Variables": the saddle function of eq.
+    min-max-with-ys extended by theta^T J^T w + theta^T H theta / 2 +
+    r_theta^T theta (J's (q, r, c) parts paired with (x, u, y)) has the
+    Hessian [[K, J], [J^T, H]] and the gradient [b; r_theta] at zero; its
+    exact rational stationary point equals the oracle's bordered solve."""
+    prob = _rational_problem(seed, N, n, m, delta)
+    Jq, Jr, Jc, H, rt = _cross_terms(seed, prob, p_theta)
+    F = lambda v: sp.Rational(Fraction(float(v)).limit_denominator(1 << 20))  # noqa: E731
+    Hw, g0, _ = _lagrangian_solution(prob)
+    # unknown order of _lagrangian_solution: x_0, u_0, ..., x_N, y_0, ..., y_N
+    J = sp.Matrix([[F(v) for v in oracle.join_solution(prob, Jq[j], Jr[j], Jc[j])]
+                   for j in range(p_theta)]).T
+    Hb = Hw.row_join(J).col_join(J.T.row_join(sp.Matrix(H.tolist()).applyfunc(F)))
+    gb = g0.col_join(sp.Matrix([F(v) for v in rt]))
+    sol = Hb.LUsolve(-gb)
+    x, u, y, dth = oracle.cross_stage_solve(prob, Jq, Jr, Jc, H, rt)
+    dim = Hw.shape[0]
+    exact_w = np.array([float(v) for v in sol[:dim]])
+    np.testing.assert_allclose(oracle.join_solution(prob, x, u, y), exact_w, rtol=1e-10,
+                               atol=1e-12)
+    np.testing.assert_allclose(dth, [float(v) for v in sol[dim:]], rtol=1e-10, atol=1e-12)
+
+
+def test_cross_stage_without_coupling_reduces_to_the_recursion():
+    """J = 0 decouples the bordered system: dw is the LQR solution of the
+    sequential recursion and dtheta = -H^{-1} r_theta."""
+    prob = inputs.random_instance(31, 12, 3, 2, 1e-2)
+    p_theta = 3
+    rng = np.random.default_rng(31)
+    H = rng.standard_normal((p_theta, p_theta))
+    H = H @ H.T + np.eye(p_theta)
+    rt = rng.standard_normal(p_theta)
+    Z = lambda *s: np.zeros(s)  # noqa: E731
+    x, u, y, dth = oracle.cross_stage_solve(prob, Z(p_theta, 13, 3), Z(p_theta, 12, 2),
+                                            Z(p_theta, 13, 3), H, rt)
+    ref = oracle.riccati(prob)
+    np.testing.assert_allclose(x, ref.x, rtol=1e-9, atol=1e-10)
+    np.testing.assert_allclose(u, ref.u, rtol=1e-9, atol=1e-10)
+    np.testing.assert_allclose(y, ref.y, rtol=1e-9, atol=1e-10)
+    np.testing.assert_allclose(dth, -np.linalg.solve(H, rt), rtol=1e-12)
