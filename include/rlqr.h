@@ -238,6 +238,39 @@ rlqr_status rlqr_solve_noalloc(const rlqr_problem *prob, const rlqr_opts *opts, 
                                int32_t *status, rlqr_stream_t stream);
 
 /* ------------------------------------------------------------------ *
+ * Cross-stage variables (Section "Cross-Stage Variables").            *
+ * ------------------------------------------------------------------ */
+
+/* Scratch bytes of rlqr_solve_cross (0 for invalid dimensions or p outside
+ * 1..31). */
+size_t rlqr_cross_scratch_bytes(int32_t N, int32_t nx, int32_t nu, int32_t p);
+
+/* The bordered system of eq. cross-stage-kkt for p cross-stage variables
+ * theta shared by every stage:
+ *   [K    J ] [dw    ]     [b      ]
+ *   [J^T  H ] [dtheta] = - [r_theta],
+ * K the instance's KKT matrix factored in `ws` by rlqr_factor, b its
+ * right-hand side (q, r, c of prob).  J (device, p columns of length
+ * L = (N+1) nx + N nu + (N+1) nx, column j at J + j L): each column in the
+ * layout of the right-hand side, q-part (pairs with x), r-part (with u),
+ * c-part (with y).  H (device, p x p row-major), r_theta (device, p).
+ * Steps (eq. cross-stage-schur): p + 1 solves with the factor (the columns
+ * of J and b, each as rlqr_solve, refined in RLQR_MIXED mode), the Schur
+ * complement S = H - J^T K^{-1} J and g = r_theta - J^T K^{-1} b from FP64
+ * dot products in a fixed order, S dtheta = -g by Gaussian elimination with
+ * partial pivoting (FP64, one warp), and dw = -K^{-1}(b + J dtheta) written
+ * to x, u, y (device) with dtheta (device, p).  scratch (device, >=
+ * rlqr_cross_scratch_bytes, 256-byte aligned).  status (device int32[1], may
+ * be NULL): the worst status of the p + 1 solves, or RLQR_ERR_SINGULAR for a
+ * zero or non-finite pivot of S (dtheta = 0 then).  RLQR_OPT_SYNC works as
+ * for rlqr_solve.  p must be 1..31. */
+rlqr_status rlqr_solve_cross(const rlqr_problem *prob, const rlqr_opts *opts, void *ws,
+                             size_t ws_bytes, int32_t p, const double *J, const double *H,
+                             const double *r_theta, void *scratch, size_t scratch_bytes,
+                             double *x, double *u, double *y, double *dtheta, int32_t *status,
+                             rlqr_stream_t stream);
+
+/* ------------------------------------------------------------------ *
  * Horizon shards of one long instance (one GPU per shard).            *
  * ------------------------------------------------------------------ */
 

@@ -12,6 +12,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "cross.cuh"
 #include "launch.cuh"
 #include "residual.cuh"
 #include "residual_grid.cuh"
@@ -729,6 +730,83 @@ rlqr_status rlqr_shard_entry(int32_t nx, double delta, const double *P_start,
     return RLQR_ERR_ARG;
   return cuda_status(launch_shard_entry(nx, delta, P_start, x_start, x_first, c0,
                                         reinterpret_cast<cudaStream_t>(stream)));
+}
+
+// ---- cross-stage variables (Section "Cross-Stage Variables")
+// Scratch: V (p columns of length L), the dot-product partials, p + 2 status
+// slots (the p + 1 solves, then the combined status).
+static size_t cross_len(int N, int n, int m) { return (size_t)(N + 1) * n * 2 + (size_t)N * m; }
+
+size_t rlqr_cross_scratch_bytes(int32_t N, int32_t nx, int32_t nu, int32_t p) {
+  if (!valid_dims(N, nx, nu) || p < 1 || p > kCrossMaxP) return 0;
+  const size_t L = cross_len(N, nx, nu);
+  return align_up((size_t)p * L * sizeof(double)) +
+         align_up((size_t)kCrossBlocks * p * (p + 1) * sizeof(double)) +
+         align_up((size_t)(p + 2) * sizeof(int32_t));
+}
+
+rlqr_status rlqr_solve_cross(const rlqr_problem *prob, const rlqr_opts *opts, void *ws,
+                             size_t ws_bytes, int32_t p, const double *J, const double *H,
+                             const double *r_theta, void *scratch, size_t scratch_bytes,
+                             double *x, double *u, double *y, double *dtheta, int32_t *status,
+                             rlqr_stream_t stream) {
+  if (!valid_problem(prob) || !valid_opts(opts) || p < 1 || p > kCrossMaxP || !J || !H ||
+      !r_theta || !x || !u || !y || !dtheta)
+    return RLQR_ERR_ARG;
+  const size_t need = rlqr_cross_scratch_bytes(prob->N, prob->nx, prob->nu, p);
+  if (!scratch || scratch_bytes < need || (reinterpret_cast<uintptr_t>(scratch) % kAlign) != 0)
+    return RLQR_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int N = prob->N, n = prob->nx, m = prob->nu;
+  const size_t L = cross_len(N, n, m);
+  const int64_t nX = (int64_t)(N + 1) * n, nU = (int64_t)N * m;
+  char *sc = static_cast<char *>(scratch);
+  double *V = reinterpret_cast<double *>(sc);
+  double *part = reinterpret_cast<double *>(sc + align_up((size_t)p * L * sizeof(double)));
+  int32_t *sst = reinterpret_cast<int32_t *>(
+      sc + align_up((size_t)p * L * sizeof(double)) +
+      align_up((size_t)kCrossBlocks * p * (p + 1) * sizeof(double)));
+  rlqr_opts o = *opts;
+  o.flags &= ~RLQR_OPT_SYNC;  // the inner solves stay stream-ordered
+  // status slots start at RLQR_OK (a solve that takes no decision leaves its
+  // slot alone; the factor's pivot status comes from the instance state)
+  if (cudaMemsetAsync(sst, 0, (size_t)(p + 2) * sizeof(int32_t), s) != cudaSuccess)
+    return RLQR_ERR_CUDA;
+  // V_j = -K^{-1} J_j: the solve with J's column j as right-hand side
+  for (int j = 0; j < p; ++j) {
+    rlqr_problem pj = *prob;
+    pj.q = J + (size_t)j * L;
+    pj.r = pj.q + nX;
+    pj.c = pj.r + nU;
+    double *xj = V + (size_t)j * L;
+    const rlqr_status st = rlqr_solve(&pj, &o, ws, ws_bytes, xj, xj + nX, xj + nX + nU, nullptr,
+                                      nullptr, sst + j, stream);
+    if (st != RLQR_OK) return st;
+  }
+  // z_b = -K^{-1} b into x, u, y
+  rlqr_status st = rlqr_solve(prob, &o, ws, ws_bytes, x, u, y, nullptr, nullptr, sst + p, stream);
+  if (st != RLQR_OK) return st;
+  {
+    LaunchScope ls("k_cross", s);
+    k_cross_dots<<<kCrossBlocks, 256, 0, s>>>(p, (int64_t)L, nX, nU, J, V, x, u, y, part);
+    k_cross_theta<<<1, 1024, 0, s>>>(p, kCrossBlocks, H, r_theta, part,
+                                     reinterpret_cast<const InstState *>(ws), sst, dtheta,
+                                     sst + p + 1);
+    k_cross_combine<<<(int)std::min<size_t>((L + 255) / 256, 148 * 8), 256, 0, s>>>(
+        p, (int64_t)L, nX, nU, V, dtheta, x, u, y);
+    if (status && cudaMemcpyAsync(status, sst + p + 1, sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                  s) != cudaSuccess)
+      return RLQR_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return RLQR_ERR_CUDA;
+  }
+  if (opts->flags & RLQR_OPT_SYNC) {
+    int32_t h = 0;
+    if (cudaMemcpyAsync(&h, sst + p + 1, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return RLQR_ERR_CUDA;
+    return static_cast<rlqr_status>(h);
+  }
+  return RLQR_OK;
 }
 
 rlqr_status rlqr_instrument(int enable) {

@@ -93,6 +93,11 @@ def _load():
             ("rlqr_shard_entry", [i32, dbl, _dp, _dp, _dp, _dp, _dp])):
         getattr(lib, name).restype = st
         getattr(lib, name).argtypes = args
+    lib.rlqr_cross_scratch_bytes.restype = sz
+    lib.rlqr_cross_scratch_bytes.argtypes = [ctypes.c_int32] * 4
+    lib.rlqr_solve_cross.restype = st
+    lib.rlqr_solve_cross.argtypes = [P(rlqr_problem), P(rlqr_opts), _dp, sz, ctypes.c_int32, _dp,
+                                     _dp, _dp, _dp, sz, _dp, _dp, _dp, _dp, _dp, _dp]
     lib.rlqr_measure_pipes.restype = st
     lib.rlqr_measure_pipes.argtypes = [P(ctypes.c_double)] * 3
     lib.rlqr_instrument.restype = st
@@ -398,3 +403,19 @@ def rlqr_measure_pipes() -> dict:
     v = [ctypes.c_double() for _ in range(3)]
     _check(lib.rlqr_measure_pipes(*[ctypes.byref(x) for x in v]), "rlqr_measure_pipes")
     return dict(fp64_tflops=v[0].value, fp32_tflops=v[1].value, fp32x2_tflops=v[2].value)
+
+
+def rlqr_cross_scratch_bytes(N: int, nx: int, nu: int, p: int) -> int:
+    return int(lib.rlqr_cross_scratch_bytes(N, nx, nu, p))
+
+
+def rlqr_solve_cross(prob: "DeviceProblem", opts: rlqr_opts, ws: torch.Tensor, J, H, r_theta,
+                     scratch: torch.Tensor, x, u, y, dtheta, status=None, stream=None) -> int:
+    """Cross-stage variables (include/rlqr.h): J is a (p, L) FP64 tensor of
+    columns in the right-hand side's layout, H (p, p), r_theta (p,)."""
+    ps = prob.c_struct()
+    return _check_call(lib.rlqr_solve_cross(
+        ctypes.byref(ps), ctypes.byref(opts), _ptr(ws), ws.numel(), int(J.shape[0]), _ptr(J),
+        _ptr(H), _ptr(r_theta), _ptr(scratch), scratch.numel(), _ptr(x), _ptr(u), _ptr(y),
+        _ptr(dtheta), _ptr(status), _stream(stream)), "rlqr_solve_cross")
+
