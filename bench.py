@@ -16,6 +16,7 @@ is timed beside it, and the FP64 CPU oracle is the CPU baseline.
     python bench.py --profile-instances K   # profiling case, no bench line
     python bench.py --long-horizon          # the single long-horizon instance
     python bench.py --latency               # latency of the small single instance
+    python bench.py --cross P               # cross-stage variables, p = P
     python bench.py --ragged K              # the first K instances of the ragged batch
     python bench.py --ragged K --ragged-n 48   # only the n = 48 instances among them
 
@@ -342,6 +343,58 @@ def run_latency(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cross(args):
+    """One JSON line for cross-stage variables (Section "Cross-Stage
+    Variables"): one instance of the batch workload (n=12, m=4, N=256),
+    factored once; the time of rlqr_solve_cross for p shared variables (p + 1
+    solves with the factor, the Schur complement and the combination) beside
+    one plain rlqr_solve, mixed precision with refinement."""
+    import torch
+    from paper_2509_16370_b300 import inputs, rlqr
+    prob = inputs.random_instance(900, 256, 12, 4, 1e-4)
+    dp = rlqr.DeviceProblem.from_host(prob)
+    N, n, m, p = prob.N, prob.n, prob.m, args.cross
+    opts = rlqr.make_opts(rlqr.RLQR_MIXED, algo=rlqr.RLQR_ALGO_SEQ, tol=TOL, max_refine=3)
+    ws = rlqr.alloc_workspace(rlqr.rlqr_workspace_bytes(N, n, m, opts))
+    flags = torch.zeros(N + 1, dtype=torch.uint8, device="cuda")
+    rlqr.rlqr_factor(dp, opts, ws, flags)
+    g = torch.Generator(device="cpu").manual_seed(900)
+    L = 2 * (N + 1) * n + N * m
+    J = torch.randn(p, L, generator=g, dtype=torch.float64).cuda()
+    Hs = torch.randn(p, p, generator=g, dtype=torch.float64)
+    H = (Hs + Hs.T + 2 * p * torch.eye(p, dtype=torch.float64)).cuda()
+    rt = torch.randn(p, generator=g, dtype=torch.float64).cuda()
+    sc = rlqr.alloc_workspace(rlqr.rlqr_cross_scratch_bytes(N, n, m, p, opts))
+    x = torch.zeros(N + 1, n, dtype=torch.float64, device="cuda")
+    u = torch.zeros(N, m, dtype=torch.float64, device="cuda")
+    y = torch.zeros(N + 1, n, dtype=torch.float64, device="cuda")
+    dth = torch.zeros(p, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def timeit(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_cross = timeit(lambda: rlqr.rlqr_solve_cross(dp, opts, ws, J, H, rt, sc, x, u, y, dth, st))
+    ms_solve = timeit(lambda: rlqr.rlqr_solve(dp, opts, ws, x, u, y))
+    line = {"metric": "cross-stage solve time (p shared variables, one factor)",
+            "value": ms_cross, "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": "single instance n_x=12, n_u=4, N=256, delta=1e-4",
+                       "p": p, "precision": "mixed"},
+            "plain_solve_ms": ms_solve, "ratio_to_plain_solve": ms_cross / ms_solve,
+            "status": int(st.item())}
+    print(json.dumps(line), flush=True)
+
+
 def run_long_horizon(args):
     """One JSON line for the long-horizon instance (stage-solves/s of factor +
     solve + refinement; SCAN mixed vs SEQ FP64 on the GPU)."""
@@ -614,6 +667,8 @@ def main():
                     help="profiling case: the mixed solve on the first K instances only")
     ap.add_argument("--long-horizon", action="store_true",
                     help="the single long-horizon instance (associative scan)")
+    ap.add_argument("--cross", type=int, default=0,
+                    help="cross-stage variables: time rlqr_solve_cross with p = CROSS")
     ap.add_argument("--latency", action="store_true",
                     help="latency of one factor + solve of the small single instance")
     ap.add_argument("--ragged", type=int, default=0,
@@ -624,7 +679,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.steps is None:
-        args.steps = (20 if args.impl == "reference" or args.latency else
+        args.steps = (20 if args.impl == "reference" or args.latency or args.cross else
                       3 if (args.ragged or args.long_horizon) else
                       1 if args.profile_instances else 500)
     if args.impl == "reference":
@@ -635,6 +690,8 @@ def main():
         run_long_horizon(args)
     elif args.latency:
         run_latency(args)
+    elif args.cross:
+        run_cross(args)
     elif args.ragged > 0:
         run_ragged(args)
     else:

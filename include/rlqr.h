@@ -241,9 +241,12 @@ rlqr_status rlqr_solve_noalloc(const rlqr_problem *prob, const rlqr_opts *opts, 
  * Cross-stage variables (Section "Cross-Stage Variables").            *
  * ------------------------------------------------------------------ */
 
-/* Scratch bytes of rlqr_solve_cross (0 for invalid dimensions or p outside
- * 1..31). */
-size_t rlqr_cross_scratch_bytes(int32_t N, int32_t nx, int32_t nu, int32_t p);
+/* Scratch bytes of rlqr_solve_cross (0 for invalid dimensions, options or
+ * p outside 1..31): p + 1 solution columns, the Schur complement's partial
+ * sums and p + 1 copies of the instance's workspace (the solves run
+ * concurrently). */
+size_t rlqr_cross_scratch_bytes(int32_t N, int32_t nx, int32_t nu, int32_t p,
+                                const rlqr_opts *opts);
 
 /* The bordered system of eq. cross-stage-kkt for p cross-stage variables
  * theta shared by every stage:
@@ -255,7 +258,9 @@ size_t rlqr_cross_scratch_bytes(int32_t N, int32_t nx, int32_t nu, int32_t p);
  * layout of the right-hand side, q-part (pairs with x), r-part (with u),
  * c-part (with y).  H (device, p x p row-major), r_theta (device, p).
  * Steps (eq. cross-stage-schur): p + 1 solves with the factor (the columns
- * of J and b, each as rlqr_solve, refined in RLQR_MIXED mode), the Schur
+ * of J and b, each as rlqr_solve on its own copy of the factored workspace
+ * and its own stream, forked from and joined back to `stream`, refined in
+ * RLQR_MIXED mode), the Schur
  * complement S = H - J^T K^{-1} J and g = r_theta - J^T K^{-1} b from FP64
  * dot products in a fixed order, S dtheta = -g by Gaussian elimination with
  * partial pivoting (FP64, one warp), and dw = -K^{-1}(b + J dtheta) written

@@ -5,8 +5,7 @@
 //   S dtheta = -g,   S = H + J^T V = H - J^T K^{-1} J,   g = r_theta + J^T z_b,
 //   dw = z_b + V dtheta.
 // J and V columns share the layout of the right-hand side (q | r | c, paired
-// with x | u | y); z_b sits in the caller's x, u, y.  Included by one
-// translation unit (rlqr_api.cu).
+// with x | u | y).  Included by one translation unit (rlqr_api.cu).
 #pragma once
 
 #include "common.cuh"
@@ -118,16 +117,16 @@ __global__ void __launch_bounds__(1024) k_cross_theta(int p, int nblk, const dou
   }
 }
 
-// dw = z_b + V dtheta, in place in x | u | y.
+// dw = z_b + V dtheta into x | u | y (z_b is column p of V).
 __global__ void k_cross_combine(int p, int64_t L, int64_t nX, int64_t nU, const double *V,
                                 const double *dtheta, double *x, double *u, double *y) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L;
        e += (int64_t)gridDim.x * blockDim.x) {
-    double t = 0.0;
+    double t = V[(size_t)p * L + e];
     for (int j = 0; j < p; ++j) t = fma(V[(size_t)j * L + e], __ldg(dtheta + j), t);
-    if (e < nX) x[e] += t;
-    else if (e < nX + nU) u[e - nX] += t;
-    else y[e - nX - nU] += t;
+    if (e < nX) x[e] = t;
+    else if (e < nX + nU) u[e - nX] = t;
+    else y[e - nX - nU] = t;
   }
 }
 

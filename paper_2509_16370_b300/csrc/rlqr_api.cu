@@ -733,16 +733,62 @@ rlqr_status rlqr_shard_entry(int32_t nx, double delta, const double *P_start,
 }
 
 // ---- cross-stage variables (Section "Cross-Stage Variables")
-// Scratch: V (p columns of length L), the dot-product partials, p + 2 status
-// slots (the p + 1 solves, then the combined status).
+// Scratch: V and z_b (p + 1 columns of length L), the dot-product partials,
+// p + 2 status slots (the p + 1 solves, then the combined status), and one
+// copy of the factored workspace per solve, so that the p + 1 solves run
+// concurrently on their own streams.
 static size_t cross_len(int N, int n, int m) { return (size_t)(N + 1) * n * 2 + (size_t)N * m; }
 
-size_t rlqr_cross_scratch_bytes(int32_t N, int32_t nx, int32_t nu, int32_t p) {
-  if (!valid_dims(N, nx, nu) || p < 1 || p > kCrossMaxP) return 0;
-  const size_t L = cross_len(N, nx, nu);
-  return align_up((size_t)p * L * sizeof(double)) +
-         align_up((size_t)kCrossBlocks * p * (p + 1) * sizeof(double)) +
-         align_up((size_t)(p + 2) * sizeof(int32_t));
+struct CrossScratch {
+  size_t V, part, st, ws, ws_each, total;
+};
+
+static CrossScratch cross_scratch(int N, int n, int m, int p, const rlqr_opts *o) {
+  CrossScratch c{};
+  const size_t L = cross_len(N, n, m);
+  c.ws_each = align_up(rlqr_workspace_bytes(N, n, m, o));
+  size_t off = 0;
+  c.V = off;
+  off += align_up((size_t)(p + 1) * L * sizeof(double));
+  c.part = off;
+  off += align_up((size_t)kCrossBlocks * p * (p + 1) * sizeof(double));
+  c.st = off;
+  off += align_up((size_t)(p + 2) * sizeof(int32_t));
+  c.ws = off;
+  off += (size_t)(p + 1) * c.ws_each;
+  c.total = off;
+  return c;
+}
+
+// Streams of the concurrent solves (per device, created once, like the
+// size-class streams).
+struct CrossStreams {
+  bool ok = false;
+  cudaStream_t st[kCrossMaxP + 1];
+  cudaEvent_t fork, join[kCrossMaxP + 1];
+};
+static CrossStreams g_cross_streams[kMaxClassDevices];
+static std::mutex g_cross_mu;
+
+static CrossStreams *cross_streams_locked() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxClassDevices) return nullptr;
+  CrossStreams &cs = g_cross_streams[dev];
+  if (!cs.ok) {
+    for (int j = 0; j <= kCrossMaxP; ++j)
+      if (cudaStreamCreateWithFlags(&cs.st[j], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&cs.join[j], cudaEventDisableTiming) != cudaSuccess)
+        return nullptr;
+    if (cudaEventCreateWithFlags(&cs.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    cs.ok = true;
+  }
+  return &cs;
+}
+
+size_t rlqr_cross_scratch_bytes(int32_t N, int32_t nx, int32_t nu, int32_t p,
+                                const rlqr_opts *opts) {
+  if (!valid_dims(N, nx, nu) || p < 1 || p > kCrossMaxP || !valid_opts(opts)) return 0;
+  return cross_scratch(N, nx, nu, p, opts).total;
 }
 
 rlqr_status rlqr_solve_cross(const rlqr_problem *prob, const rlqr_opts *opts, void *ws,
@@ -753,42 +799,66 @@ rlqr_status rlqr_solve_cross(const rlqr_problem *prob, const rlqr_opts *opts, vo
   if (!valid_problem(prob) || !valid_opts(opts) || p < 1 || p > kCrossMaxP || !J || !H ||
       !r_theta || !x || !u || !y || !dtheta)
     return RLQR_ERR_ARG;
-  const size_t need = rlqr_cross_scratch_bytes(prob->N, prob->nx, prob->nu, p);
-  if (!scratch || scratch_bytes < need || (reinterpret_cast<uintptr_t>(scratch) % kAlign) != 0)
+  const int N = prob->N, n = prob->nx, m = prob->nu;
+  const CrossScratch C = cross_scratch(N, n, m, p, opts);
+  const size_t need = rlqr_workspace_bytes(N, n, m, opts);
+  if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
+    return RLQR_ERR_WORKSPACE;
+  if (!scratch || scratch_bytes < C.total || (reinterpret_cast<uintptr_t>(scratch) % kAlign) != 0)
     return RLQR_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int N = prob->N, n = prob->nx, m = prob->nu;
   const size_t L = cross_len(N, n, m);
   const int64_t nX = (int64_t)(N + 1) * n, nU = (int64_t)N * m;
   char *sc = static_cast<char *>(scratch);
-  double *V = reinterpret_cast<double *>(sc);
-  double *part = reinterpret_cast<double *>(sc + align_up((size_t)p * L * sizeof(double)));
-  int32_t *sst = reinterpret_cast<int32_t *>(
-      sc + align_up((size_t)p * L * sizeof(double)) +
-      align_up((size_t)kCrossBlocks * p * (p + 1) * sizeof(double)));
+  double *V = reinterpret_cast<double *>(sc + C.V);  // columns 0..p-1: V, column p: z_b
+  double *part = reinterpret_cast<double *>(sc + C.part);
+  int32_t *sst = reinterpret_cast<int32_t *>(sc + C.st);
   rlqr_opts o = *opts;
   o.flags &= ~RLQR_OPT_SYNC;  // the inner solves stay stream-ordered
   // status slots start at RLQR_OK (a solve that takes no decision leaves its
-  // slot alone; the factor's pivot status comes from the instance state)
+  // slot alone; the factor's pivot status comes from the instance state);
+  // every solve gets its own copy of the factored workspace
   if (cudaMemsetAsync(sst, 0, (size_t)(p + 2) * sizeof(int32_t), s) != cudaSuccess)
     return RLQR_ERR_CUDA;
-  // V_j = -K^{-1} J_j: the solve with J's column j as right-hand side
-  for (int j = 0; j < p; ++j) {
+  for (int j = 0; j <= p; ++j)
+    if (cudaMemcpyAsync(sc + C.ws + (size_t)j * C.ws_each, ws, need, cudaMemcpyDeviceToDevice,
+                        s) != cudaSuccess)
+      return RLQR_ERR_CUDA;
+  std::unique_lock<std::mutex> lock(g_cross_mu);
+  CrossStreams *cs = cross_streams_locked();
+  auto tstream = [&](int j) { return cs ? cs->st[j] : s; };
+  if (cs) {
+    if (cudaEventRecord(cs->fork, s) != cudaSuccess) return RLQR_ERR_CUDA;
+    for (int j = 0; j <= p; ++j)
+      if (cudaStreamWaitEvent(cs->st[j], cs->fork, 0) != cudaSuccess) return RLQR_ERR_CUDA;
+  }
+  // column j < p: V_j = -K^{-1} J_j; column p: z_b = -K^{-1} b
+  for (int j = 0; j <= p; ++j) {
     rlqr_problem pj = *prob;
-    pj.q = J + (size_t)j * L;
-    pj.r = pj.q + nX;
-    pj.c = pj.r + nU;
+    if (j < p) {
+      pj.q = J + (size_t)j * L;
+      pj.r = pj.q + nX;
+      pj.c = pj.r + nU;
+    }
     double *xj = V + (size_t)j * L;
-    const rlqr_status st = rlqr_solve(&pj, &o, ws, ws_bytes, xj, xj + nX, xj + nX + nU, nullptr,
-                                      nullptr, sst + j, stream);
+    const rlqr_status st =
+        rlqr_solve(&pj, &o, sc + C.ws + (size_t)j * C.ws_each, C.ws_each, xj, xj + nX,
+                   xj + nX + nU, nullptr, nullptr, sst + j,
+                   reinterpret_cast<rlqr_stream_t>(tstream(j)));
     if (st != RLQR_OK) return st;
   }
-  // z_b = -K^{-1} b into x, u, y
-  rlqr_status st = rlqr_solve(prob, &o, ws, ws_bytes, x, u, y, nullptr, nullptr, sst + p, stream);
-  if (st != RLQR_OK) return st;
+  if (cs) {
+    for (int j = 0; j <= p; ++j)
+      if (cudaEventRecord(cs->join[j], cs->st[j]) != cudaSuccess ||
+          cudaStreamWaitEvent(s, cs->join[j], 0) != cudaSuccess)
+        return RLQR_ERR_CUDA;
+  }
+  lock.unlock();
   {
+    const double *zb = V + (size_t)p * L;
     LaunchScope ls("k_cross", s);
-    k_cross_dots<<<kCrossBlocks, 256, 0, s>>>(p, (int64_t)L, nX, nU, J, V, x, u, y, part);
+    k_cross_dots<<<kCrossBlocks, 256, 0, s>>>(p, (int64_t)L, nX, nU, J, V, zb, zb + nX,
+                                             zb + nX + nU, part);
     k_cross_theta<<<1, 1024, 0, s>>>(p, kCrossBlocks, H, r_theta, part,
                                      reinterpret_cast<const InstState *>(ws), sst, dtheta,
                                      sst + p + 1);

@@ -94,7 +94,7 @@ def _load():
         getattr(lib, name).restype = st
         getattr(lib, name).argtypes = args
     lib.rlqr_cross_scratch_bytes.restype = sz
-    lib.rlqr_cross_scratch_bytes.argtypes = [ctypes.c_int32] * 4
+    lib.rlqr_cross_scratch_bytes.argtypes = [ctypes.c_int32] * 4 + [P(rlqr_opts)]
     lib.rlqr_solve_cross.restype = st
     lib.rlqr_solve_cross.argtypes = [P(rlqr_problem), P(rlqr_opts), _dp, sz, ctypes.c_int32, _dp,
                                      _dp, _dp, _dp, sz, _dp, _dp, _dp, _dp, _dp, _dp]
@@ -405,8 +405,8 @@ def rlqr_measure_pipes() -> dict:
     return dict(fp64_tflops=v[0].value, fp32_tflops=v[1].value, fp32x2_tflops=v[2].value)
 
 
-def rlqr_cross_scratch_bytes(N: int, nx: int, nu: int, p: int) -> int:
-    return int(lib.rlqr_cross_scratch_bytes(N, nx, nu, p))
+def rlqr_cross_scratch_bytes(N: int, nx: int, nu: int, p: int, opts: rlqr_opts) -> int:
+    return int(lib.rlqr_cross_scratch_bytes(N, nx, nu, p, ctypes.byref(opts)))
 
 
 def rlqr_solve_cross(prob: "DeviceProblem", opts: rlqr_opts, ws: torch.Tensor, J, H, r_theta,

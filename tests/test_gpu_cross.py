@@ -32,7 +32,7 @@ def _gpu_cross(prob, prec, algo, Jq, Jr, Jc, H, rt, sync=False):
     rlqr.rlqr_factor(dp, opts, ws, flags)
     J = torch.from_numpy(np.concatenate([Jq.reshape(p, -1), Jr.reshape(p, -1), Jc.reshape(p, -1)],
                                         axis=1)).cuda().contiguous()
-    scratch = rlqr.alloc_workspace(rlqr.rlqr_cross_scratch_bytes(N, n, m, p))
+    scratch = rlqr.alloc_workspace(rlqr.rlqr_cross_scratch_bytes(N, n, m, p, opts))
     x = torch.zeros(N + 1, n, dtype=torch.float64, device="cuda")
     u = torch.zeros(N, m, dtype=torch.float64, device="cuda")
     y = torch.zeros(N + 1, n, dtype=torch.float64, device="cuda")
@@ -95,8 +95,48 @@ def test_cross_stage_singular_schur_complement(prec):
 
 
 def test_cross_scratch_sizing():
-    assert rlqr.rlqr_cross_scratch_bytes(16, 4, 2, 0) == 0
-    assert rlqr.rlqr_cross_scratch_bytes(16, 4, 2, 32) == 0
-    a = rlqr.rlqr_cross_scratch_bytes(16, 4, 2, 1)
-    b = rlqr.rlqr_cross_scratch_bytes(16, 4, 2, 4)
+    o = rlqr.make_opts(rlqr.RLQR_MIXED)
+    assert rlqr.rlqr_cross_scratch_bytes(16, 4, 2, 0, o) == 0
+    assert rlqr.rlqr_cross_scratch_bytes(16, 4, 2, 32, o) == 0
+    a = rlqr.rlqr_cross_scratch_bytes(16, 4, 2, 1, o)
+    b = rlqr.rlqr_cross_scratch_bytes(16, 4, 2, 4, o)
     assert 0 < a < b and a % 256 == 0
+
+
+def test_cross_stage_graph_replay():
+    """The p + 1 solves run on the library's own streams, forked from and
+    joined back to the caller's stream: the call can be captured into a CUDA
+    graph and a replay reproduces the eager result bit for bit."""
+    prob = inputs.random_instance(807, 48, 12, 4, 1e-4)
+    p = 3
+    Jq, Jr, Jc, H, rt = _cross_inputs(807, p, prob)
+    dp = rlqr.DeviceProblem.from_host(prob)
+    opts = rlqr.make_opts(rlqr.RLQR_MIXED, algo=rlqr.RLQR_ALGO_SEQ, tol=1e-9, max_refine=4)
+    N, n, m = prob.N, prob.n, prob.m
+    ws = rlqr.alloc_workspace(rlqr.rlqr_workspace_bytes(N, n, m, opts))
+    flags = torch.zeros(N + 1, dtype=torch.uint8, device="cuda")
+    rlqr.rlqr_factor(dp, opts, ws, flags)
+    J = torch.from_numpy(np.concatenate([Jq.reshape(p, -1), Jr.reshape(p, -1), Jc.reshape(p, -1)],
+                                        axis=1)).cuda().contiguous()
+    Hd, rtd = torch.from_numpy(H).cuda(), torch.from_numpy(rt).cuda()
+    scratch = rlqr.alloc_workspace(rlqr.rlqr_cross_scratch_bytes(N, n, m, p, opts))
+    outs = [torch.zeros(N + 1, n, dtype=torch.float64, device="cuda"),
+            torch.zeros(N, m, dtype=torch.float64, device="cuda"),
+            torch.zeros(N + 1, n, dtype=torch.float64, device="cuda"),
+            torch.zeros(p, dtype=torch.float64, device="cuda")]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        rlqr.rlqr_solve_cross(dp, opts, ws, J, Hd, rtd, scratch, *outs)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    eager = [t.clone() for t in outs]
+    for t in outs:
+        t.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rlqr.rlqr_solve_cross(dp, opts, ws, J, Hd, rtd, scratch, *outs)
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(eager, outs):
+        assert torch.equal(a, b)
