@@ -36,6 +36,9 @@ Workloads
   4  ragged batch of 4096: N ~ U{32..2048}, n ~ U{6,12,24,48}, m = n/3, base as
      workload 1 plus M = 0.1 N(0,1), delta = 10^U(-8,-2), and a barrier term
      10^U(-6,6) added to every diagonal entry of Q_i and R_i.
+  5  8192 cart-double-pendulum trajectory problems (CDP_MODEL): initial state
+     at rest at p = 0 with both link angles uniform in [-pi, pi], goal state
+     (p_goal, 0, 0, 0, 0, 0) with p_goal uniform in [-1, 1].
 """
 from __future__ import annotations
 
@@ -268,3 +271,33 @@ def random_instance(seed: int, N: int, n: int, m: int, delta: float, with_M: boo
         p.M = 0.3 * rng.standard_normal((N, n, m))
     p.meta = dict(workload=99, instance=seed)
     return p
+
+
+# The cart-double-pendulum problem of workload 5 (plain data: masses in kg,
+# lengths in m, the RK4 step dt in s, N steps, bounds, diagonal cost weights;
+# the stage weights are per step, i.e. the continuous weights times dt).
+CDP_MODEL = dict(N=128, dt=0.02, m0=1.0, m1=0.5, m2=0.5, l1=0.5, l2=0.5, grav=9.81,
+                 u_max=20.0, p_max=2.0, wx=(0.02, 0.02, 0.02, 0.002, 0.002, 0.002),
+                 wu=2e-4, wf=(10.0, 10.0, 10.0, 1.0, 1.0, 1.0))
+
+
+def workload5_instance(b: int):
+    """Initial state and goal of instance b of the cart-double-pendulum batch
+    (8192 instances): cart at rest at p = 0, both link angles uniform in
+    [-pi, pi] from the upright, rates zero; goal state (p_goal, 0, 0, 0, 0, 0)
+    with p_goal uniform in [-1, 1]."""
+    rng = rng_for(5, b)
+    th = rng.uniform(-np.pi, np.pi, size=2)
+    pg = rng.uniform(-1.0, 1.0)
+    x0 = np.array([0.0, th[0], th[1], 0.0, 0.0, 0.0])
+    xg = np.array([pg, 0.0, 0.0, 0.0, 0.0, 0.0])
+    return x0, xg
+
+
+def workload5(count: int = 8192):
+    """Stacked initial states (count, 6) and goals (count, 6)."""
+    x0 = np.zeros((count, 6))
+    xg = np.zeros((count, 6))
+    for b in range(count):
+        x0[b], xg[b] = workload5_instance(b)
+    return x0, xg
