@@ -1,5 +1,6 @@
 """CPU checks of the C ABI library: it loads, exports every entry point that
-include/rlqr.h declares, and validates arguments on the host (no GPU call)."""
+include/rlqr.h and include/rlqr_ipm.h declare, and validates arguments on the
+host (no GPU call)."""
 import ctypes
 import os
 import re
@@ -10,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "rlqr.h")).read()
+    src = "".join(open(os.path.join(ROOT, "include", h)).read() for h in ("rlqr.h", "rlqr_ipm.h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"\b(rlqr_[a-z_]+)\s*\(", src)
     return sorted(set(names))
@@ -29,6 +30,26 @@ def test_library_exports_every_declared_symbol():
     for name in _declared():
         assert hasattr(lib, name), name
     assert set(rlqr.EXPORTED) <= set(_declared())
+    from paper_2509_16370_b300 import ipm
+    assert set(ipm.EXPORTED) <= set(_declared())
+
+
+def test_ipm_host_side_validation_and_sizes():
+    from paper_2509_16370_b300 import ipm
+    m, o = ipm.make_model(), ipm.make_ipm_opts()
+    a = ipm.rlqr_ipm_workspace_bytes(16, m, o)
+    b = ipm.rlqr_ipm_workspace_bytes(32, m, o)
+    assert 0 < a < b and a % 256 == 0
+    assert ipm.rlqr_ipm_workspace_bytes(0, m, o) == 0
+    assert ipm.rlqr_ipm_workspace_bytes(16, ipm.make_model(N=0), o) == 0
+    assert ipm.rlqr_ipm_workspace_bytes(16, ipm.make_model(N=5000), o) == 0
+    assert ipm.rlqr_ipm_workspace_bytes(16, m, ipm.make_ipm_opts(tau=1.0)) == 0
+    assert ipm.rlqr_ipm_workspace_bytes(16, m, ipm.make_ipm_opts(hessian=3)) == 0
+    assert ipm.rlqr_ipm_workspace_bytes(16, m, ipm.make_ipm_opts(ls_steps=0)) == 0
+    st = ipm.rlqr_ipm_state()
+    code = ipm.lib.rlqr_ipm_iterate(16, ctypes.byref(m), ctypes.byref(o), None, None,
+                                    ctypes.byref(st), None, 0, None, None)
+    assert code == 2   # RLQR_ERR_ARG before any device work
 
 
 def test_host_side_validation_and_sizes():
