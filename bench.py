@@ -17,6 +17,7 @@ is timed beside it, and the FP64 CPU oracle is the CPU baseline.
     python bench.py --long-horizon          # the single long-horizon instance
     python bench.py --latency               # latency of the small single instance
     python bench.py --cross P               # cross-stage variables, p = P
+    python bench.py --ipm K                 # the nonlinear IPM on K cart-double-pendulum instances
     python bench.py --ragged K              # the first K instances of the ragged batch
     python bench.py --ragged K --ragged-n 48   # only the n = 48 instances among them
 
@@ -395,6 +396,77 @@ def run_cross(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ipm(args):
+    """One JSON line for the regularized interior-point method (Section "The
+    Regularized Interior Point Method", Section "Applying the regularized IPM
+    to optimal control") on the first K cart-double-pendulum instances
+    (N = 128, n_x = 6, n_u = 1, RK4 dt = 0.02; angles uniform in [-pi, pi]).
+    One step = one whole solve from the cold start (rollout of u = 0) to
+    convergence or the iteration limit, with the FP32 Hessian and the
+    mixed-precision LQR solves; warm-up = one solve of 64 instances.  Reports
+    instance-iterations/s, the LQR stage-solves/s inside the IPM, the share
+    converged and their mean iteration count, beside the oracle's IPM on the
+    host cores (a few instances)."""
+    import torch
+    from paper_2509_16370_b300 import inputs, ipm
+    count = args.ipm
+    x0, xg = inputs.workload5(count)
+    model = ipm.make_model()
+    opts = ipm.make_ipm_opts(**({"max_iter": args.ipm_max_iter} if args.ipm_max_iter else {}))
+    st = ipm.IpmState(count, model.N)
+    ws = ipm.alloc_ipm_workspace(count, model, opts)
+    dx0, dxg = torch.from_numpy(x0).cuda(), torch.from_numpy(xg).cuda()
+    wst = ipm.IpmState(64, model.N)
+    wws = ipm.alloc_ipm_workspace(64, model, opts)
+    ipm.rlqr_ipm_init(model, opts, dx0[:64].contiguous(), wst)
+    ipm.rlqr_ipm_solve(model, opts, dx0[:64].contiguous(), dxg[:64].contiguous(), wst, wws)
+    torch.cuda.synchronize()
+    ms, n_it = [], 0
+    with ClockSampler(0) as clocks:
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ipm.rlqr_ipm_init(model, opts, dx0, st)
+            n_it = ipm.rlqr_ipm_solve(model, opts, dx0, dxg, st, ws)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    status = st.status.cpu().numpy()
+    iters = st.iters.cpu().numpy()
+    facts = st.factorizations.cpu().numpy()
+    t = float(np.median(ms)) / 1e3
+    conv = status == ipm.CONVERGED
+    line = {"metric": "IPM instance-iterations/s (regularized IPM, cart-double-pendulum)",
+            "value": float(iters.sum()) / t, "unit": "instance-iterations/s",
+            "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": 1,
+            "ms_per_step": t * 1e3, "dtype": "f64 (FP32 Hessian term, mixed LQR)",
+            "data": "synthetic",
+            "config": {"workload": f"{count} cart-double-pendulum trajectories, N=128, n_x=6, "
+                                   "n_u=1, RK4 dt=0.02, |u|<=20, |p|<=2, angles U[-pi,pi]",
+                       "instances": count, "max_iter": opts.max_iter, "tol": opts.tol},
+            "iterations_run": n_it, "ms_per_iteration": t * 1e3 / max(n_it, 1),
+            "lqr_stage_solves_per_s": float(facts.sum()) * model.N / t,
+            "factorizations_per_iteration": float(facts.sum() / max(iters.sum(), 1)),
+            "converged_fraction": float(conv.mean()),
+            "mean_iterations_converged": float(iters[conv].mean()) if conv.any() else None,
+            "status_counts": {k: int((status == v).sum()) for k, v in
+                              (("converged", 1), ("iteration_limit", 2), ("rho_limit", 3))},
+            "clocks": clocks.summary()}
+    if not args.no_cpu_baseline:
+        import oracle.ipm as O
+        md, op = O.Model(), O.Options()
+        t0, done, it_sum = time.time(), 0, 0
+        while time.time() - t0 < args.cpu_seconds and done < count:
+            r = O.solve(md, op, x0[done], xg[done])
+            it_sum += r.iters
+            done += 1
+        el = time.time() - t0
+        line["cpu_baseline"] = {"value": it_sum / el, "unit": "instance-iterations/s",
+                                "cores": 1, "kind": "oracle",
+                                "sample": f"{done} whole solves (instances 0..{done - 1})"}
+    print(json.dumps(line), flush=True)
+
+
 def run_long_horizon(args):
     """One JSON line for the long-horizon instance (stage-solves/s of factor +
     solve + refinement; SCAN mixed vs SEQ FP64 on the GPU)."""
@@ -669,6 +741,10 @@ def main():
                     help="the single long-horizon instance (associative scan)")
     ap.add_argument("--cross", type=int, default=0,
                     help="cross-stage variables: time rlqr_solve_cross with p = CROSS")
+    ap.add_argument("--ipm", type=int, default=0,
+                    help="the regularized IPM on the first IPM cart-double-pendulum instances")
+    ap.add_argument("--ipm-max-iter", type=int, default=0,
+                    help="with --ipm: iteration limit (default 300; smaller for profiling)")
     ap.add_argument("--latency", action="store_true",
                     help="latency of one factor + solve of the small single instance")
     ap.add_argument("--ragged", type=int, default=0,
@@ -681,6 +757,7 @@ def main():
     if args.steps is None:
         args.steps = (20 if args.impl == "reference" or args.latency or args.cross else
                       3 if (args.ragged or args.long_horizon) else
+                      1 if args.ipm else
                       1 if args.profile_instances else 500)
     if args.impl == "reference":
         run_reference(args)
@@ -692,6 +769,8 @@ def main():
         run_latency(args)
     elif args.cross:
         run_cross(args)
+    elif args.ipm:
+        run_ipm(args)
     elif args.ragged > 0:
         run_ragged(args)
     else:

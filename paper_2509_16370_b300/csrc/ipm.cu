@@ -140,16 +140,12 @@ __device__ __forceinline__ void ineq(const rlqr_cdp_model &md, int i, int N, dou
   g[3] = -p - md.p_max;
 }
 
-// Pair (j, k), j <= k, of the 28 entries of a symmetric 7 x 7 Hessian.
-__device__ __forceinline__ void pair_of(int p, int &j, int &k) {
-  j = 0;
-  int rem = p;
-  while (rem >= 7 - j) {
-    rem -= 7 - j;
-    ++j;
-  }
-  k = j + rem;
-}
+// Variables of (x_i, u_i) that the right-hand side depends on, and the 15
+// pairs (j <= k) among them.
+__constant__ int kDirs[5] = {1, 2, 4, 5, 6};
+__constant__ int kPairs[15][2] = {{1, 1}, {1, 2}, {1, 4}, {1, 5}, {1, 6}, {2, 2}, {2, 4},
+                                  {2, 5}, {2, 6}, {4, 4}, {4, 5}, {4, 6}, {5, 5}, {5, 6},
+                                  {6, 6}};
 
 // ---- initial point
 __global__ void k_ipm_init(Args a, const double *U0, const double *X0, CdpConst<double> kd) {
@@ -218,8 +214,23 @@ __global__ void __launch_bounds__(kThreads)
   double *B = a.B + (size_t)b * N * 6, *c = a.c + b * n1 * 6;
   const rlqr_cdp_model &md = a.md;
 
-  for (int t = threadIdx.x; t < 7 * N; t += kThreads) {
-    const int i = t / 7, j = t - 7 * i;
+  // The right-hand side depends on neither p (w_0) nor dp (w_3), so the RK4
+  // map is affine in them with constant coefficients: d phi / d p = e_0,
+  // d phi / d dp = dt e_0 + e_3, and every second derivative involving them
+  // vanishes.  Those columns are written directly; forward mode runs over
+  // the other five directions (kDirs) and the 15 pairs among them (kPairs).
+  for (int t = threadIdx.x; t < 2 * N; t += kThreads) {
+    const int i = t >> 1, j = (t & 1) ? 3 : 0;
+    const double y0 = Y[(i + 1) * 6], gj = j == 0 ? y0 : md.dt * y0 + Y[(i + 1) * 6 + 3];
+#pragma unroll
+    for (int l = 0; l < 6; ++l)
+      A[i * 36 + l * 6 + j] = j == 0 ? (l == 0 ? 1.0 : 0.0) : (l == 0 ? md.dt : (l == 3 ? 1.0 : 0.0));
+    double g = md.wx[j] * (X[i * 6 + j] - xg[j]) + gj - Y[i * 6 + j];
+    if (j == 0) g += Z[i * 4 + 2] - Z[i * 4 + 3];
+    q[i * 6 + j] = g;
+  }
+  for (int t = threadIdx.x; t < 5 * N; t += kThreads) {
+    const int i = t / 5, j = kDirs[t - 5 * i];
     D1<double> x[6], u, o[6];
 #pragma unroll
     for (int l = 0; l < 6; ++l) x[l] = {X[i * 6 + l], l == j ? 1.0 : 0.0};
@@ -231,10 +242,8 @@ __global__ void __launch_bounds__(kThreads)
     if (j < 6) {
 #pragma unroll
       for (int l = 0; l < 6; ++l) A[i * 36 + l * 6 + j] = o[l].d;
-      double g = md.wx[j] * (X[i * 6 + j] - xg[j]) + gj - Y[i * 6 + j];
-      if (j == 0) g += Z[i * 4 + 2] - Z[i * 4 + 3];
-      q[i * 6 + j] = g;
-      if (j == 0) {
+      q[i * 6 + j] = md.wx[j] * (X[i * 6 + j] - xg[j]) + gj - Y[i * 6 + j];
+      if (j == 1) {
 #pragma unroll
         for (int l = 0; l < 6; ++l) c[(i + 1) * 6 + l] = o[l].v - X[(i + 1) * 6 + l];
       }
@@ -253,10 +262,19 @@ __global__ void __launch_bounds__(kThreads)
   }
   for (int e = threadIdx.x; e < 36; e += kThreads) Q[(size_t)N * 36 + e] = 0.0;
   if (EXACT) {
-    for (int t = threadIdx.x; t < 28 * N; t += kThreads) {
-      const int i = t / 28;
-      int j, k;
-      pair_of(t - 28 * i, j, k);
+    for (int t = threadIdx.x; t < 13 * N; t += kThreads) {  // the zero entries
+      const int i = t / 13, e = t - 13 * i;
+      if (e < 11) {                       // rows/columns 0 and 3 of Q_i
+        const int r = e < 6 ? 0 : 3, cc = e < 6 ? e : e - 5;   // row 3: columns 1..5
+        Q[i * 36 + r * 6 + cc] = 0.0;
+        Q[i * 36 + cc * 6 + r] = 0.0;
+      } else {
+        Mx[i * 6 + (e == 11 ? 0 : 3)] = 0.0;
+      }
+    }
+    for (int t = threadIdx.x; t < 15 * N; t += kThreads) {
+      const int i = t / 15;
+      const int j = kPairs[t - 15 * i][0], k = kPairs[t - 15 * i][1];
       HD<HT> x[6], u, o[6];
 #pragma unroll
       for (int l = 0; l < 6; ++l)
