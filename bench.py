@@ -18,6 +18,7 @@ is timed beside it, and the FP64 CPU oracle is the CPU baseline.
     python bench.py --latency               # latency of the small single instance
     python bench.py --cross P               # cross-stage variables, p = P
     python bench.py --ipm K                 # the nonlinear IPM on K cart-double-pendulum instances
+    python bench.py --warm-start K          # learned warm start trained on K IPM runs
     python bench.py --ragged K              # the first K instances of the ragged batch
     python bench.py --ragged K --ragged-n 48   # only the n = 48 instances among them
 
@@ -467,6 +468,76 @@ def run_ipm(args):
     print(json.dumps(line), flush=True)
 
 
+def run_warm_start(args):
+    """One JSON line for the learned warm start of the IPM: cold-start solves
+    of the first K cart-double-pendulum instances give the training set (the
+    converged ones: (x0, goal) -> (X, U)); the BF16 network of
+    include/rlqr_mlp.h (3 layers, width 256) is trained on the GPU by its own
+    kernels; then 8192 held-out instances (from index 1,000,000) are solved
+    from the cold start and from the network's proposal.  Reports converged
+    share and mean iterations, cold vs warm."""
+    import torch
+    from paper_2509_16370_b300 import inputs, ipm, mlp
+    K, B = args.warm_start, 8192
+    model, opts = ipm.make_model(), ipm.make_ipm_opts()
+    N = model.N
+    st = ipm.IpmState(B, N)
+    ws = ipm.alloc_ipm_workspace(B, model, opts)
+    t0 = time.time()
+    feats, outs, solved = [], [], 0
+    for s0 in range(0, K, B):
+        x0, xg = inputs.workload5(B, s0)
+        dx0, dxg = torch.from_numpy(x0).cuda(), torch.from_numpy(xg).cuda()
+        ipm.rlqr_ipm_init(model, opts, dx0, st)
+        ipm.rlqr_ipm_solve(model, opts, dx0, dxg, st, ws)
+        ok = (st.status == ipm.CONVERGED).cpu().numpy()
+        solved += int(ok.sum())
+        feats.append(mlp.features(x0[ok], xg[ok]))
+        outs.append(mlp.targets(st.X.cpu().numpy()[ok], st.U.cpu().numpy()[ok]))
+    t_data = time.time() - t0
+    F, T = np.concatenate(feats), np.concatenate(outs)
+    norm = mlp.Normalizer(T)
+    d = mlp.make_dims(mlp.N_IN, 256, T.shape[1], 256)
+    net = mlp.WarmStartNet(d, mlp.init_params(d, 2025))
+    Xd = torch.from_numpy(F).cuda()
+    Td = torch.from_numpy(norm.encode(T)).cuda()
+    torch.cuda.synchronize()
+    t1 = time.time()
+    losses = mlp.train(net, Xd, Td, steps=args.ws_steps, batch=256, lr=1e-3, lr_final=5e-5,
+                       seed=7)
+    torch.cuda.synchronize()
+    t_train = time.time() - t1
+    x0, xg = inputs.workload5(B, 1_000_000)
+    dx0, dxg = torch.from_numpy(x0).cuda(), torch.from_numpy(xg).cuda()
+    res = {}
+    for kind in ("cold", "warm"):
+        t2 = time.time()
+        if kind == "cold":
+            ipm.rlqr_ipm_init(model, opts, dx0, st)
+        else:
+            X0, U0 = mlp.propose(net, norm, x0, xg, N)
+            ipm.rlqr_ipm_init(model, opts, dx0, st, U0=U0, X0=X0)
+        ipm.rlqr_ipm_solve(model, opts, dx0, dxg, st, ws)
+        torch.cuda.synchronize()
+        status, iters = st.status.cpu().numpy(), st.iters.cpu().numpy()
+        conv = status == ipm.CONVERGED
+        res[kind] = {"converged_fraction": float(conv.mean()),
+                     "mean_iterations_converged": float(iters[conv].mean()) if conv.any() else None,
+                     "mean_iterations_all": float(iters.mean()),
+                     "solve_s": time.time() - t2}
+    line = {"metric": "IPM mean iterations to convergence, cold vs learned warm start",
+            "value": res["warm"]["mean_iterations_all"], "unit": "iterations (all instances, "
+            "capped at max_iter)", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "cart-double-pendulum, N=128, angles U[-pi,pi]; training "
+                                   f"runs {K}, held-out 8192",
+                       "network": "3 layers, width 256, BF16 weights/activations, Adam",
+                       "train_steps": args.ws_steps, "batch": 256},
+            "cold": res["cold"], "warm": res["warm"], "training_solutions": int(F.shape[0]),
+            "training_runs": K, "data_s": t_data, "train_s": t_train,
+            "loss_first": losses[0], "loss_last": losses[-1]}
+    print(json.dumps(line), flush=True)
+
+
 def run_long_horizon(args):
     """One JSON line for the long-horizon instance (stage-solves/s of factor +
     solve + refinement; SCAN mixed vs SEQ FP64 on the GPU)."""
@@ -743,6 +814,10 @@ def main():
                     help="cross-stage variables: time rlqr_solve_cross with p = CROSS")
     ap.add_argument("--ipm", type=int, default=0,
                     help="the regularized IPM on the first IPM cart-double-pendulum instances")
+    ap.add_argument("--warm-start", type=int, default=0,
+                    help="learned warm start: IPM runs for the training set (multiple of 8192)")
+    ap.add_argument("--ws-steps", type=int, default=6000,
+                    help="with --warm-start: Adam steps")
     ap.add_argument("--ipm-max-iter", type=int, default=0,
                     help="with --ipm: iteration limit (default 300; smaller for profiling)")
     ap.add_argument("--latency", action="store_true",
@@ -771,6 +846,8 @@ def main():
         run_cross(args)
     elif args.ipm:
         run_ipm(args)
+    elif args.warm_start:
+        run_warm_start(args)
     elif args.ragged > 0:
         run_ragged(args)
     else:

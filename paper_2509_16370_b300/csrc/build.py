@@ -11,7 +11,7 @@ PKG = os.path.dirname(HERE)
 OUT_DIR = os.path.join(PKG, "_lib")
 OUT = os.path.join(OUT_DIR, "librlqr.so")
 SOURCES = ["rlqr_api.cu", "launch_fp32.cu", "launch_fp64.cu", "scan_fp32.cu", "scan_fp64.cu",
-           "shard.cu", "pipes.cu", "ipm.cu"]
+           "shard.cu", "pipes.cu", "ipm.cu", "mlp.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
          "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-Xptxas", "-v"]
@@ -22,7 +22,7 @@ def _stale():
         return True
     t = os.path.getmtime(OUT)
     deps = [os.path.join(HERE, d) for d in os.listdir(HERE) if d.endswith((".cu", ".cuh"))]
-    deps += [os.path.join(os.path.dirname(PKG), "include", h) for h in ("rlqr.h", "rlqr_ipm.h")]
+    deps += [os.path.join(os.path.dirname(PKG), "include", h) for h in ("rlqr.h", "rlqr_ipm.h", "rlqr_mlp.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -294,10 +294,11 @@ def workload5_instance(b: int):
     return x0, xg
 
 
-def workload5(count: int = 8192):
-    """Stacked initial states (count, 6) and goals (count, 6)."""
+def workload5(count: int = 8192, start: int = 0):
+    """Stacked initial states (count, 6) and goals (count, 6) of instances
+    start .. start + count - 1."""
     x0 = np.zeros((count, 6))
     xg = np.zeros((count, 6))
     for b in range(count):
-        x0[b], xg[b] = workload5_instance(b)
+        x0[b], xg[b] = workload5_instance(start + b)
     return x0, xg

@@ -1,0 +1,177 @@
+"""Thin ctypes binding of include/rlqr_mlp.h (the IPM warm-start network) and
+the warm-start helpers around it.
+
+Marshalling only: the forward pass, the gradient and the Adam step run in the
+CUDA kernels of librlqr.so.  ``WarmStartNet`` holds the parameters (FP32
+master, BF16 copy, Adam moments) as torch CUDA tensors; ``train`` loops over
+shuffled mini-batches calling rlqr_mlp_grad and rlqr_mlp_adam; ``propose``
+maps (x0, goal) to an initial trajectory (X, U) for rlqr_ipm_init.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from .rlqr import _check, _ptr, _stream, lib
+
+EXPORTED = ("rlqr_mlp_param_count", "rlqr_mlp_workspace_bytes", "rlqr_mlp_sync_bf16",
+            "rlqr_mlp_forward", "rlqr_mlp_grad", "rlqr_mlp_adam")
+
+
+class rlqr_mlp_dims(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int32), ("width", ctypes.c_int32), ("n_out", ctypes.c_int32),
+                ("max_rows", ctypes.c_int32)]
+
+
+_P, _dp, _i, _f = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int32, ctypes.c_float
+lib.rlqr_mlp_param_count.restype = ctypes.c_size_t
+lib.rlqr_mlp_param_count.argtypes = [_P(rlqr_mlp_dims)]
+lib.rlqr_mlp_workspace_bytes.restype = ctypes.c_size_t
+lib.rlqr_mlp_workspace_bytes.argtypes = [_P(rlqr_mlp_dims)]
+lib.rlqr_mlp_sync_bf16.restype = ctypes.c_int
+lib.rlqr_mlp_sync_bf16.argtypes = [_P(rlqr_mlp_dims), _dp, _dp, _dp]
+lib.rlqr_mlp_forward.restype = ctypes.c_int
+lib.rlqr_mlp_forward.argtypes = [_P(rlqr_mlp_dims), _dp, _dp, _i, _dp, _dp, ctypes.c_size_t, _dp]
+lib.rlqr_mlp_grad.restype = ctypes.c_int
+lib.rlqr_mlp_grad.argtypes = [_P(rlqr_mlp_dims), _dp, _dp, _dp, _dp, _i, _dp, _dp, _dp,
+                              ctypes.c_size_t, _dp]
+lib.rlqr_mlp_adam.restype = ctypes.c_int
+lib.rlqr_mlp_adam.argtypes = [_P(rlqr_mlp_dims), _dp, _dp, _dp, _dp, _dp, _i, _f, _f, _f, _f, _dp]
+
+
+def make_dims(n_in, width, n_out, max_rows) -> rlqr_mlp_dims:
+    return rlqr_mlp_dims(n_in, width, n_out, max_rows)
+
+
+def rlqr_mlp_param_count(d) -> int:
+    return int(lib.rlqr_mlp_param_count(ctypes.byref(d)))
+
+
+def rlqr_mlp_workspace_bytes(d) -> int:
+    return int(lib.rlqr_mlp_workspace_bytes(ctypes.byref(d)))
+
+
+class WarmStartNet:
+    """Parameters, BF16 copy, Adam moments and workspace of one network."""
+
+    def __init__(self, d: rlqr_mlp_dims, params: np.ndarray, device="cuda"):
+        self.d = d
+        n = rlqr_mlp_param_count(d)
+        assert params.size == n
+        self.p = torch.from_numpy(np.asarray(params, np.float32)).to(device)
+        self.q = torch.zeros(n, dtype=torch.int16, device=device)   # BF16 bit patterns
+        self.m = torch.zeros(n, dtype=torch.float32, device=device)
+        self.v = torch.zeros(n, dtype=torch.float32, device=device)
+        self.g = torch.zeros(n, dtype=torch.float32, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.ws = torch.empty(rlqr_mlp_workspace_bytes(d), dtype=torch.uint8, device=device)
+        self.step = 0
+        _check(lib.rlqr_mlp_sync_bf16(ctypes.byref(d), _ptr(self.p), _ptr(self.q),
+                                      _stream(None)), "rlqr_mlp_sync_bf16")
+
+    def forward(self, x: torch.Tensor) -> torch.Tensor:
+        rows = x.shape[0]
+        y = torch.empty(rows, self.d.n_out, dtype=torch.float32, device=x.device)
+        _check(lib.rlqr_mlp_forward(ctypes.byref(self.d), _ptr(self.q), _ptr(x), rows, _ptr(y),
+                                    _ptr(self.ws), self.ws.numel(), _stream(None)),
+               "rlqr_mlp_forward")
+        return y
+
+    def grad(self, x, t, idx):
+        _check(lib.rlqr_mlp_grad(ctypes.byref(self.d), _ptr(self.q), _ptr(x), _ptr(t), _ptr(idx),
+                                 idx.numel(), _ptr(self.loss), _ptr(self.g), _ptr(self.ws),
+                                 self.ws.numel(), _stream(None)), "rlqr_mlp_grad")
+        return self.loss, self.g
+
+    def adam(self, lr, b1=0.9, b2=0.999, eps=1e-8):
+        self.step += 1
+        _check(lib.rlqr_mlp_adam(ctypes.byref(self.d), _ptr(self.p), _ptr(self.q), _ptr(self.m),
+                                 _ptr(self.v), _ptr(self.g), self.step, lr, b1, b2, eps,
+                                 _stream(None)), "rlqr_mlp_adam")
+
+
+def init_params(d: rlqr_mlp_dims, seed: int) -> np.ndarray:
+    """He-uniform weights, zero biases, zero padding (host, seeded)."""
+    rng = np.random.default_rng(seed)
+    W, npad = d.width, (d.n_out + 15) // 16 * 16
+    parts = []
+    W1 = np.zeros((W, 16))
+    W1[:, :d.n_in] = rng.uniform(-1, 1, (W, d.n_in)) * np.sqrt(6.0 / d.n_in)
+    W2 = rng.uniform(-1, 1, (W, W)) * np.sqrt(6.0 / W)
+    W3 = np.zeros((npad, W))
+    W3[:d.n_out] = rng.uniform(-1, 1, (d.n_out, W)) * np.sqrt(3.0 / W)
+    for a in (W1, np.zeros(W), W2, np.zeros(W), W3, np.zeros(npad)):
+        parts.append(a.ravel())
+    return np.concatenate(parts).astype(np.float32)
+
+
+def train(net: WarmStartNet, x: torch.Tensor, t: torch.Tensor, steps: int, batch: int,
+          lr: float, seed: int = 0, lr_final: float | None = None) -> list:
+    """Mini-batch Adam on (x, t) (device FP32 tensors); the shuffled index
+    batches come from a seeded host permutation.  Returns the loss every 100
+    steps."""
+    n = x.shape[0]
+    g = torch.Generator().manual_seed(seed)
+    losses, perm, at = [], torch.randperm(n, generator=g), 0
+    for s in range(steps):
+        if at + batch > n:
+            perm, at = torch.randperm(n, generator=g), 0
+        idx = perm[at:at + batch].to(torch.int32).to(x.device)
+        at += batch
+        loss, _ = net.grad(x, t, idx)
+        rate = lr if lr_final is None else lr * (lr_final / lr) ** (s / max(steps - 1, 1))
+        net.adam(rate)
+        if s % 100 == 0 or s == steps - 1:
+            losses.append(float(loss.item()))
+    return losses
+
+
+# ---- warm start of the cart-double-pendulum IPM
+N_IN = 7          # x0 (6) and the goal cart position
+
+
+def features(x0: np.ndarray, xg: np.ndarray) -> np.ndarray:
+    """Network input of each instance: its initial state and goal position."""
+    return np.concatenate([x0, xg[:, :1]], axis=1).astype(np.float32)
+
+
+def targets(X: np.ndarray, U: np.ndarray) -> np.ndarray:
+    """Network output of each instance: its state trajectory and controls."""
+    return np.concatenate([X.reshape(X.shape[0], -1), U], axis=1)
+
+
+class Normalizer:
+    """Per-column mean and standard deviation of the training targets."""
+
+    def __init__(self, T: np.ndarray):
+        self.mean = T.mean(axis=0)
+        self.std = np.maximum(T.std(axis=0), 1e-6)
+
+    def encode(self, T):
+        return ((T - self.mean) / self.std).astype(np.float32)
+
+    def decode(self, Y):
+        return Y * self.std + self.mean
+
+
+def propose(net: WarmStartNet, norm: Normalizer, x0: np.ndarray, xg: np.ndarray, N: int):
+    """Initial trajectories (X [count][N+1][6], U [count][N], FP64 device
+    tensors) for rlqr_ipm_init, in chunks of the network's max_rows."""
+    count = x0.shape[0]
+    feats = torch.from_numpy(features(x0, xg)).cuda()
+    R = net.d.max_rows
+    outs = []
+    for s in range(0, count, R):
+        n = min(R, count - s)
+        rows = (n + 15) // 16 * 16
+        chunk = torch.zeros(rows, N_IN, dtype=torch.float32, device="cuda")
+        chunk[:n] = feats[s:s + n]
+        outs.append(net.forward(chunk)[:n])
+    Y = norm.decode(torch.cat(outs).double().cpu().numpy())
+    X = Y[:, :(N + 1) * 6].reshape(count, N + 1, 6)
+    X[:, 0] = x0                       # the initial state is known exactly
+    U = Y[:, (N + 1) * 6:]
+    return torch.from_numpy(np.ascontiguousarray(X)).cuda(), \
+        torch.from_numpy(np.ascontiguousarray(U)).cuda()

@@ -1,5 +1,5 @@
 """CPU checks of the C ABI library: it loads, exports every entry point that
-include/rlqr.h and include/rlqr_ipm.h declare, and validates arguments on the
+include/rlqr.h, include/rlqr_ipm.h and include/rlqr_mlp.h declare, and validates arguments on the
 host (no GPU call)."""
 import ctypes
 import os
@@ -11,9 +11,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = "".join(open(os.path.join(ROOT, "include", h)).read() for h in ("rlqr.h", "rlqr_ipm.h"))
+    src = "".join(open(os.path.join(ROOT, "include", h)).read() for h in ("rlqr.h", "rlqr_ipm.h", "rlqr_mlp.h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"\b(rlqr_[a-z_]+)\s*\(", src)
+    names = re.findall(r"\b(rlqr_[a-z0-9_]+)\s*\(", src)
     return sorted(set(names))
 
 
@@ -32,6 +32,8 @@ def test_library_exports_every_declared_symbol():
     assert set(rlqr.EXPORTED) <= set(_declared())
     from paper_2509_16370_b300 import ipm
     assert set(ipm.EXPORTED) <= set(_declared())
+    from paper_2509_16370_b300 import mlp
+    assert set(mlp.EXPORTED) <= set(_declared())
 
 
 def test_ipm_host_side_validation_and_sizes():
