@@ -19,6 +19,7 @@ is timed beside it, and the FP64 CPU oracle is the CPU baseline.
     python bench.py --cross P               # cross-stage variables, p = P
     python bench.py --ipm K                 # the nonlinear IPM on K cart-double-pendulum instances
     python bench.py --warm-start K          # learned warm start trained on K IPM runs
+    python bench.py --diag                  # general diagonal Delta_i
     python bench.py --ragged K              # the first K instances of the ragged batch
     python bench.py --ragged K --ragged-n 48   # only the n = 48 instances among them
 
@@ -538,6 +539,52 @@ def run_warm_start(args):
     print(json.dumps(line), flush=True)
 
 
+def run_diag(args):
+    """One JSON line for the general diagonal Delta_i (rlqr_solve_diag: the
+    congruence scaling, factor + solve of the scaled copy, the map back)
+    beside rlqr_factor + rlqr_solve with scalar delta, on one instance of the
+    batch workload's size (n=12, m=4, N=256), mixed precision."""
+    import torch
+    from paper_2509_16370_b300 import inputs, rlqr
+    prob = inputs.random_instance(901, 256, 12, 4, 1e-4)
+    N, n, m = prob.N, prob.n, prob.m
+    dp = rlqr.DeviceProblem.from_host(prob)
+    opts = rlqr.make_opts(rlqr.RLQR_MIXED, algo=rlqr.RLQR_ALGO_SEQ, tol=TOL, max_refine=3)
+    d = torch.from_numpy(10.0 ** np.random.default_rng(901).uniform(-6, -2, (N + 1, n))).cuda()
+    wsd = rlqr.alloc_workspace(rlqr.rlqr_diag_workspace_bytes(N, n, m, opts))
+    ws = rlqr.alloc_workspace(rlqr.rlqr_workspace_bytes(N, n, m, opts))
+    f = dict(dtype=torch.float64, device="cuda")
+    x, u, y = torch.zeros(N + 1, n, **f), torch.zeros(N, m, **f), torch.zeros(N + 1, n, **f)
+    flags = torch.zeros(N + 1, dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def timeit(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    def plain():
+        rlqr.rlqr_factor(dp, opts, ws, flags)
+        rlqr.rlqr_solve(dp, opts, ws, x, u, y)
+
+    ms_diag = timeit(lambda: rlqr.rlqr_solve_diag(dp, d, opts, wsd, x, u, y, flags, None, st))
+    ms_plain = timeit(plain)
+    line = {"metric": "factor + solve time with diagonal Delta_i (scaled copy) vs scalar delta",
+            "value": ms_diag, "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": "single instance n_x=12, n_u=4, N=256, Delta_i entries "
+                                   "10^U(-6,-2)", "precision": "mixed"},
+            "scalar_delta_ms": ms_plain, "ratio": ms_diag / ms_plain, "status": int(st.item())}
+    print(json.dumps(line), flush=True)
+
+
 def run_long_horizon(args):
     """One JSON line for the long-horizon instance (stage-solves/s of factor +
     solve + refinement; SCAN mixed vs SEQ FP64 on the GPU)."""
@@ -814,6 +861,8 @@ def main():
                     help="cross-stage variables: time rlqr_solve_cross with p = CROSS")
     ap.add_argument("--ipm", type=int, default=0,
                     help="the regularized IPM on the first IPM cart-double-pendulum instances")
+    ap.add_argument("--diag", action="store_true",
+                    help="general diagonal Delta_i: rlqr_solve_diag beside the scalar-delta solve")
     ap.add_argument("--warm-start", type=int, default=0,
                     help="learned warm start: IPM runs for the training set (multiple of 8192)")
     ap.add_argument("--ws-steps", type=int, default=6000,
@@ -830,7 +879,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.steps is None:
-        args.steps = (20 if args.impl == "reference" or args.latency or args.cross else
+        args.steps = (20 if args.impl == "reference" or args.latency or args.cross or args.diag else
                       3 if (args.ragged or args.long_horizon) else
                       1 if args.ipm else
                       1 if args.profile_instances else 500)
@@ -848,6 +897,8 @@ def main():
         run_ipm(args)
     elif args.warm_start:
         run_warm_start(args)
+    elif args.diag:
+        run_diag(args)
     elif args.ragged > 0:
         run_ragged(args)
     else:

@@ -207,6 +207,36 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
                                int32_t *iters, rlqr_stream_t stream);
 
 /* ------------------------------------------------------------------ *
+ * General diagonal dual regularization Delta_i = diag(d_i).            *
+ * ------------------------------------------------------------------ */
+
+/* Workspace bytes of rlqr_solve_diag (0 for invalid dimensions). */
+size_t rlqr_diag_workspace_bytes(int32_t N, int32_t nx, int32_t nu, const rlqr_opts *opts);
+
+/* Factor + solve one instance whose dual regularization is Delta_i =
+ * diag(delta_diag[i]) (device (N+1)*nx doubles, every entry > 0) instead of
+ * prob->delta * I (prob->delta is ignored): the problem statement of Section
+ * "Dual-Regularized LQR" allows any SPD Delta_i, and the certificate of
+ * Section "Inertia Certification" then tests S_i = I + Delta_i^{1/2} P_i
+ * Delta_i^{1/2}.  Method: with D_i = Delta_i^{1/2}, the congruence
+ * x_i = D_i x~_i, y_i = D_i^{-1} y~_i maps the system to one with Delta = I
+ * (Q~ = D Q D, M~ = D M, q~ = D q, A~_i = D_{i+1}^{-1} A_i D_i,
+ * B~_i = D_{i+1}^{-1} B_i, c~ = D^{-1} c), whose pivots are exactly S_i and
+ * G_i; the scaled copy lives in `ws` and is solved with rlqr_factor /
+ * rlqr_solve (opts as there), then x, y are mapped back.  In RLQR_MIXED
+ * mode one more refinement pass follows against the FP64 residual of the
+ * ORIGINAL system (the refinement inside rlqr_solve measures the scaled
+ * system).  pivot_pd (N+1 bytes), x, u, y as for rlqr_solve; rel_resid (may
+ * be NULL) receives the normwise backward error of the original system;
+ * status (device int32[1], may be NULL) the instance status.  A d_i entry
+ * that is not positive and finite makes the pivots non-finite:
+ * RLQR_ERR_SINGULAR.  RLQR_OPT_SYNC in opts->flags returns the status. */
+rlqr_status rlqr_solve_diag(const rlqr_problem *prob, const double *delta_diag,
+                            const rlqr_opts *opts, void *ws, size_t ws_bytes, double *x, double *u,
+                            double *y, uint8_t *pivot_pd, double *rel_resid, int32_t *status,
+                            rlqr_stream_t stream);
+
+/* ------------------------------------------------------------------ *
  * Allocation-free solve (no counterpart in the paper).                 *
  * ------------------------------------------------------------------ */
 

@@ -22,6 +22,9 @@ What it computes (citations are to the paper's sections and equations):
   pivoting in the interleaved order (for sizes where a dense factor is too big).
 * ``residual``     -- the stagewise residual of Section "Residual Computation"
   and the normwise backward error.
+* ``kkt_dense_diag`` / ``riccati_diag`` -- a general diagonal Delta_i
+  (Section "Dual-Regularized LQR" allows any SPD Delta_i): the dense system
+  and the recursion with S_i = I + Delta_i^{1/2} P_i Delta_i^{1/2}.
 * ``cross_stage_solve`` -- Section "Cross-Stage Variables": the bordered
   system [[K, J], [J^T, H]] [dw; dtheta] = -[b; r_theta], assembled densely
   from ``kkt_dense`` and solved by numpy (the plain definition).
@@ -221,6 +224,88 @@ def kkt_dense(prob):
     K[:nxp, nxp:] = Cm.T
     K[nxp:, nxp:] = -float(prob.delta) * np.eye(nyd)
     return K, b
+
+
+class _Shallow:
+    def __init__(self, prob, **kw):
+        self.__dict__.update({k: getattr(prob, k) for k in
+                              ("N", "n", "m", "Q", "M", "R", "q", "r", "A", "B", "c", "delta")})
+        self.__dict__.update(kw)
+
+
+def kkt_dense_diag(prob, dvec):
+    """K and b of eq. primal-dual-linear-system with a general diagonal
+    Delta_i = diag(dvec[i]) (dvec (N+1, n), positive) in place of delta I:
+    the problem statement of Section "Dual-Regularized LQR" allows any
+    symmetric positive-definite Delta_i."""
+    K, b = kkt_dense(_Shallow(prob, delta=0.0))
+    nxp, _ = kkt_dims(prob.N, prob.n, prob.m)
+    K[nxp:, nxp:] = -np.diag(np.asarray(dvec, float).ravel())
+    return K, b
+
+
+def _ldl_d(S):
+    """D of the unpivoted LDL^T of a symmetric matrix (the pivots)."""
+    S = np.array(S, dtype=float)
+    n = S.shape[0]
+    d = np.zeros(n)
+    L = np.eye(n)
+    for j in range(n):
+        d[j] = S[j, j] - np.sum(L[j, :j] ** 2 * d[:j])
+        for i in range(j + 1, n):
+            L[i, j] = (S[i, j] - np.sum(L[i, :j] * L[j, :j] * d[:j])) / d[j]
+    return d
+
+
+def riccati_diag(prob, dvec):
+    """The sequential recursion of Theorem main-seq-theorem with a general
+    diagonal Delta_i (numpy, plain): W = P (I + Delta P)^{-1}, g = p + W (c -
+    Delta p), G = R + B^T W B, H = B^T W A + M^T, K = -G^{-1} H, k = -G^{-1} h,
+    P = Q + A^T W A + H^T K, p = q + A^T g + H^T k; x_0 = (I + Delta_0 P_0)^{-1}
+    (c_0 - Delta_0 p_0), u = K x + k, x_+ = (I + Delta P_+)^{-1}(A x + B u +
+    c_+ - Delta p_+), y = P x + p.  Flags from the unpivoted LDL^T of
+    S_i = I + Delta_i^{1/2} P_i Delta_i^{1/2} (Section "Inertia
+    Certification") and of G_i.  Returns (x, u, y, flags)."""
+    N, n, m = prob.N, prob.n, prob.m
+    Q, M, R, q, r, A, B, c = _data(prob)
+    D = [np.diag(np.asarray(dvec[i], float)) for i in range(N + 1)]
+    Dh = [np.diag(np.sqrt(np.asarray(dvec[i], float))) for i in range(N + 1)]
+    I = np.eye(n)
+    P = [None] * (N + 1)
+    p = [None] * (N + 1)
+    K = [None] * N
+    k = [None] * N
+    flags = np.zeros(N + 1, dtype=np.uint8)
+    P[N] = 0.5 * (Q[N] + Q[N].T)
+    p[N] = q[N].copy()
+    for i in range(N - 1, -1, -1):
+        Pn = P[i + 1]
+        Wm = Pn @ np.linalg.inv(I + D[i + 1] @ Pn)
+        Wm = 0.5 * (Wm + Wm.T)
+        g = p[i + 1] + Wm @ (c[i + 1] - D[i + 1] @ p[i + 1])
+        G = 0.5 * (R[i] + R[i].T) + B[i].T @ Wm @ B[i]
+        H = B[i].T @ Wm @ A[i] + M[i].T
+        h = r[i] + B[i].T @ g
+        if np.all(_ldl_d(G) > 0):
+            flags[i] |= 2
+        K[i] = -np.linalg.solve(G, H)
+        k[i] = -np.linalg.solve(G, h)
+        Pi = 0.5 * (Q[i] + Q[i].T) + A[i].T @ Wm @ A[i] + H.T @ K[i]
+        P[i] = 0.5 * (Pi + Pi.T)
+        p[i] = q[i] + A[i].T @ g + H.T @ k[i]
+    flags[N] |= 2
+    for i in range(N + 1):
+        if np.all(_ldl_d(I + Dh[i] @ P[i] @ Dh[i]) > 0):
+            flags[i] |= 1
+    x = np.zeros((N + 1, n))
+    u = np.zeros((N, m))
+    x[0] = np.linalg.solve(I + D[0] @ P[0], c[0] - D[0] @ p[0])
+    for i in range(N):
+        u[i] = K[i] @ x[i] + k[i]
+        x[i + 1] = np.linalg.solve(I + D[i + 1] @ P[i + 1],
+                                   A[i] @ x[i] + B[i] @ u[i] + c[i + 1] - D[i + 1] @ p[i + 1])
+    y = np.stack([P[i] @ x[i] + p[i] for i in range(N + 1)])
+    return x, u, y, flags
 
 
 def split_solution(prob, z):

@@ -11,7 +11,7 @@ PKG = os.path.dirname(HERE)
 OUT_DIR = os.path.join(PKG, "_lib")
 OUT = os.path.join(OUT_DIR, "librlqr.so")
 SOURCES = ["rlqr_api.cu", "launch_fp32.cu", "launch_fp64.cu", "scan_fp32.cu", "scan_fp64.cu",
-           "shard.cu", "pipes.cu", "ipm.cu", "mlp.cu"]
+           "shard.cu", "pipes.cu", "ipm.cu", "mlp.cu", "diag.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
          "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-Xptxas", "-v"]

@@ -98,6 +98,11 @@ def _load():
     lib.rlqr_solve_cross.restype = st
     lib.rlqr_solve_cross.argtypes = [P(rlqr_problem), P(rlqr_opts), _dp, sz, ctypes.c_int32, _dp,
                                      _dp, _dp, _dp, sz, _dp, _dp, _dp, _dp, _dp, _dp]
+    lib.rlqr_diag_workspace_bytes.restype = sz
+    lib.rlqr_diag_workspace_bytes.argtypes = [ctypes.c_int32] * 3 + [P(rlqr_opts)]
+    lib.rlqr_solve_diag.restype = st
+    lib.rlqr_solve_diag.argtypes = [P(rlqr_problem), _dp, P(rlqr_opts), _dp, sz, _dp, _dp, _dp,
+                                    _dp, _dp, _dp, _dp]
     lib.rlqr_measure_pipes.restype = st
     lib.rlqr_measure_pipes.argtypes = [P(ctypes.c_double)] * 3
     lib.rlqr_instrument.restype = st
@@ -419,3 +424,17 @@ def rlqr_solve_cross(prob: "DeviceProblem", opts: rlqr_opts, ws: torch.Tensor, J
         _ptr(H), _ptr(r_theta), _ptr(scratch), scratch.numel(), _ptr(x), _ptr(u), _ptr(y),
         _ptr(dtheta), _ptr(status), _stream(stream)), "rlqr_solve_cross")
 
+
+
+def rlqr_diag_workspace_bytes(N: int, nx: int, nu: int, opts: rlqr_opts) -> int:
+    return int(lib.rlqr_diag_workspace_bytes(N, nx, nu, ctypes.byref(opts)))
+
+
+def rlqr_solve_diag(prob: "DeviceProblem", delta_diag, opts: rlqr_opts, ws: torch.Tensor, x, u, y,
+                    pivot_pd, rel_resid=None, status=None, stream=None) -> int:
+    """General diagonal Delta_i (delta_diag: device (N+1, nx) FP64)."""
+    ps = prob.c_struct()
+    return _check_call(lib.rlqr_solve_diag(ctypes.byref(ps), _ptr(delta_diag), ctypes.byref(opts),
+                                           _ptr(ws), ws.numel(), _ptr(x), _ptr(u), _ptr(y),
+                                           _ptr(pivot_pd), _ptr(rel_resid), _ptr(status),
+                                           _stream(stream)), "rlqr_solve_diag")
