@@ -414,7 +414,10 @@ def run_ipm(args):
     count = args.ipm
     x0, xg = inputs.workload5(count)
     model = ipm.make_model()
-    opts = ipm.make_ipm_opts(**({"max_iter": args.ipm_max_iter} if args.ipm_max_iter else {}))
+    kw = {"max_iter": args.ipm_max_iter} if args.ipm_max_iter else {}
+    kw["hessian"] = {"fp32": ipm.RLQR_IPM_HESS_EXACT_FP32, "fp64": ipm.RLQR_IPM_HESS_EXACT_FP64,
+                     "gn": ipm.RLQR_IPM_HESS_GAUSS_NEWTON}[args.ipm_hessian]
+    opts = ipm.make_ipm_opts(**kw)
     st = ipm.IpmState(count, model.N)
     ws = ipm.alloc_ipm_workspace(count, model, opts)
     dx0, dxg = torch.from_numpy(x0).cuda(), torch.from_numpy(xg).cuda()
@@ -441,7 +444,10 @@ def run_ipm(args):
     line = {"metric": "IPM instance-iterations/s (regularized IPM, cart-double-pendulum)",
             "value": float(iters.sum()) / t, "unit": "instance-iterations/s",
             "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": 1,
-            "ms_per_step": t * 1e3, "dtype": "f64 (FP32 Hessian term, mixed LQR)",
+            "ms_per_step": t * 1e3, "dtype": {"fp32": "f64 (FP32 Hessian term, mixed LQR)",
+                                                    "fp64": "f64 (FP64 Hessian term, mixed LQR)",
+                                                    "gn": "f64 (Gauss-Newton Hessian, mixed LQR)"
+                                                    }[args.ipm_hessian],
             "data": "synthetic",
             "config": {"workload": f"{count} cart-double-pendulum trajectories, N=128, n_x=6, "
                                    "n_u=1, RK4 dt=0.02, |u|<=20, |p|<=2, angles U[-pi,pi]",
@@ -867,6 +873,9 @@ def main():
                     help="learned warm start: IPM runs for the training set (multiple of 8192)")
     ap.add_argument("--ws-steps", type=int, default=6000,
                     help="with --warm-start: Adam steps")
+    ap.add_argument("--ipm-hessian", choices=["fp32", "fp64", "gn"], default="fp32",
+                    help="with --ipm: the Hessian of the Lagrangian (exact in FP32 or FP64, or "
+                         "Gauss-Newton)")
     ap.add_argument("--ipm-max-iter", type=int, default=0,
                     help="with --ipm: iteration limit (default 300; smaller for profiling)")
     ap.add_argument("--latency", action="store_true",

@@ -69,7 +69,7 @@ inline Ws ws_layout(const rlqr_mlp_dims &d) {
   w.dz2 = take(R * W * 2);
   w.dz1 = take(R * W * 2);
   w.dh = take(R * W * 4);
-  w.part = take((R / 16 + 1) * 4);
+  w.part = take((R + 1) * 4);
   w.total = at;
   return w;
 }
@@ -121,16 +121,15 @@ __global__ void k_bias_out(const float *C, const bf16 *b, int rows, int npad, in
 }
 
 // dy = bf16(2 (y - t) / (rows n_out)) on the real columns (0 on the padding),
-// per-block partial sums of (y - t)^2 (one block per 16 rows).
+// per-row partial sums of (y - t)^2 (one block per row).
 __global__ void __launch_bounds__(256) k_loss_grad(const float *C, const bf16 *b, const float *t,
                                                    const int32_t *idx, int rows, int npad,
                                                    int n_out, bf16 *dy, float *part) {
   __shared__ float sh[8];
-  const int r0 = blockIdx.x * 16;
+  const int r = blockIdx.x;
   const float scale = 2.0f / ((float)rows * (float)n_out);
   float acc = 0.0f;
-  for (int e = threadIdx.x; e < 16 * npad; e += blockDim.x) {
-    const int r = r0 + e / npad, c = e % npad;
+  for (int c = threadIdx.x; c < npad; c += blockDim.x) {
     float g = 0.0f;
     if (c < n_out) {
       const int64_t src = idx ? idx[r] : r;
@@ -163,13 +162,22 @@ __global__ void k_relu_back(const float *dh, const bf16 *h, int n, bf16 *dz) {
   dz[e] = __float2bfloat16_rn(__bfloat162float(h[e]) > 0.0f ? dh[e] : 0.0f);
 }
 
-// out[c] = sum_r src[r][c] (FP32, rows in order).
-__global__ void k_colsum(const bf16 *src, int rows, int cols, float *out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
+// out[c] = sum_r src[r][c] (FP32): block (32, 8) per 32 columns, thread
+// (c, j) sums rows j, j + 8, ... (coalesced across c), then the 8 partial
+// sums in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) k_colsum(const bf16 *src, int rows, int cols, float *out) {
+  __shared__ float sh[8][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
   float s = 0.0f;
-  for (int r = 0; r < rows; ++r) s += __bfloat162float(src[(size_t)r * cols + c]);
-  out[c] = s;
+  if (c < cols)
+    for (int r = threadIdx.y; r < rows; r += 8) s += __bfloat162float(src[(size_t)r * cols + c]);
+  sh[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < cols) {
+    float t = 0.0f;
+    for (int j = 0; j < 8; ++j) t += sh[j][threadIdx.x];
+    out[c] = t;
+  }
 }
 
 __global__ void k_to_bf16(const float *p, size_t n, bf16 *q) {
@@ -283,24 +291,24 @@ rlqr_status rlqr_mlp_grad(const rlqr_mlp_dims *d, const uint16_t *params_bf16, c
   bf16 *h2 = reinterpret_cast<bf16 *>(w + L.h2), *dy = reinterpret_cast<bf16 *>(w + L.dy);
   bf16 *dz2 = reinterpret_cast<bf16 *>(w + L.dz2), *dz1 = reinterpret_cast<bf16 *>(w + L.dz1);
   float *dh = reinterpret_cast<float *>(w + L.dh), *part = reinterpret_cast<float *>(w + L.part);
-  k_loss_grad<<<rows / 16, 256, 0, s>>>(reinterpret_cast<float *>(w + L.y), q + o.b3, t, idx,
-                                        rows, P, d->n_out, dy, part);
-  k_loss_final<<<1, 32, 0, s>>>(part, rows / 16, rows, d->n_out, loss);
+  k_loss_grad<<<rows, 256, 0, s>>>(reinterpret_cast<float *>(w + L.y), q + o.b3, t, idx, rows,
+                                   P, d->n_out, dy, part);
+  k_loss_final<<<1, 32, 0, s>>>(part, rows, rows, d->n_out, loss);
   if (gemm<true, false>(P, W, rows, dy, P, h2, W, grad + o.W3, s) != cudaSuccess)
     return RLQR_ERR_CUDA;
-  k_colsum<<<blocks(P), 256, 0, s>>>(dy, rows, P, grad + o.b3);
+  k_colsum<<<(P + 31) / 32, dim3(32, 8), 0, s>>>(dy, rows, P, grad + o.b3);
   if (gemm<false, false>(rows, W, P, dy, P, q + o.W3, W, dh, s) != cudaSuccess)
     return RLQR_ERR_CUDA;
   k_relu_back<<<blocks((size_t)rows * W), 256, 0, s>>>(dh, h2, rows * W, dz2);
   if (gemm<true, false>(W, W, rows, dz2, W, h1, W, grad + o.W2, s) != cudaSuccess)
     return RLQR_ERR_CUDA;
-  k_colsum<<<blocks(W), 256, 0, s>>>(dz2, rows, W, grad + o.b2);
+  k_colsum<<<(W + 31) / 32, dim3(32, 8), 0, s>>>(dz2, rows, W, grad + o.b2);
   if (gemm<false, false>(rows, W, W, dz2, W, q + o.W2, W, dh, s) != cudaSuccess)
     return RLQR_ERR_CUDA;
   k_relu_back<<<blocks((size_t)rows * W), 256, 0, s>>>(dh, h1, rows * W, dz1);
   if (gemm<true, false>(W, 16, rows, dz1, W, a0, 16, grad + o.W1, s) != cudaSuccess)
     return RLQR_ERR_CUDA;
-  k_colsum<<<blocks(W), 256, 0, s>>>(dz1, rows, W, grad + o.b1);
+  k_colsum<<<(W + 31) / 32, dim3(32, 8), 0, s>>>(dz1, rows, W, grad + o.b1);
   return cudaGetLastError() == cudaSuccess ? RLQR_OK : RLQR_ERR_CUDA;
 }
 

@@ -68,17 +68,20 @@ def test_initial_point_matches_the_oracle():
         assert got.mu == ref.mu and got.iters == 0 and got.status == 0
 
 
+@pytest.mark.parametrize("N", [1, 40, 300])
 @pytest.mark.parametrize("hess", [G.RLQR_IPM_HESS_EXACT_FP64, G.RLQR_IPM_HESS_EXACT_FP32,
                                   G.RLQR_IPM_HESS_GAUSS_NEWTON])
-def test_linearization_matches_the_oracle(hess):
+def test_linearization_matches_the_oracle(hess, N):
+    """Horizons of one stage, of a partial pass and of several passes of the
+    128-thread CTA over the stages."""
     bs = [0, 3, 7]
-    model, opts, st, ws, dx0, dxg, x0, xg = _setup(bs, N=40, hessian=hess)
+    model, opts, st, ws, dx0, dxg, x0, xg = _setup(bs, N=N, hessian=hess)
     rng = np.random.default_rng(5)
     # a point away from the rollout: perturbed states, controls, duals
     st.X += 0.05 * torch.from_numpy(rng.standard_normal(tuple(st.X.shape))).cuda()
     st.U += torch.from_numpy(rng.standard_normal(tuple(st.U.shape))).cuda()
     st.Y += torch.from_numpy(rng.standard_normal(tuple(st.Y.shape))).cuda()
-    md, op = O.Model(N=40), _oracle_opts(opts)
+    md, op = O.Model(N=N), _oracle_opts(opts)
     before = [_oracle_state(st, i, x0, xg) for i in range(len(bs))]
     G.rlqr_ipm_linearize(model, opts, dx0, dxg, st, ws)
     v = G.rlqr_ipm_lqr_view(model, opts, st, ws)
@@ -100,10 +103,11 @@ def test_linearization_matches_the_oracle(hess):
             assert _rel(got, getattr(prob, k)) <= htol, k
 
 
-def test_iterations_match_the_oracle_one_at_a_time():
+@pytest.mark.parametrize("N", [128, 300])
+def test_iterations_match_the_oracle_one_at_a_time(N):
     bs = [0, 1, 2, 5]
-    model, opts, st, ws, dx0, dxg, x0, xg = _setup(bs)
-    md, op = O.Model(), _oracle_opts(opts)
+    model, opts, st, ws, dx0, dxg, x0, xg = _setup(bs, N=N)
+    md, op = O.Model(N=N), _oracle_opts(opts)
     worst = 0.0
     for it in range(40):
         before = [_oracle_state(st, i, x0, xg) for i in range(len(bs))]
