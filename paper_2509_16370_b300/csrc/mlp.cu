@@ -149,11 +149,12 @@ __global__ void __launch_bounds__(256) k_loss_grad(const float *C, const bf16 *b
   }
 }
 
+// Sum of the per-row partials by one warp in a fixed order (deterministic).
 __global__ void k_loss_final(const float *part, int nblk, int rows, int n_out, float *loss) {
-  if (threadIdx.x != 0) return;
   double s = 0.0;
-  for (int i = 0; i < nblk; ++i) s += part[i];
-  *loss = (float)(s / ((double)rows * (double)n_out));
+  for (int i = threadIdx.x; i < nblk; i += 32) s += part[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) *loss = (float)(s / ((double)rows * (double)n_out));
 }
 
 __global__ void k_relu_back(const float *dh, const bf16 *h, int n, bf16 *dz) {
