@@ -86,8 +86,8 @@ def test_learned_warm_start_beats_the_cold_start():
     """The network trained (by these kernels) on the converged cold-start
     solutions of 32768 instances, against the plain cold start on 4096
     held-out instances: more of them converge within the iteration limit and
-    the mean iteration count drops (the IPM from either starting point is the
-    judge of the result)."""
+    the mean iteration count drops (the IPM from either starting point decides
+    the result)."""
     from paper_2509_16370_b300 import inputs, ipm
     B = 4096
     model, opts = ipm.make_model(), ipm.make_ipm_opts()
