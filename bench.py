@@ -395,6 +395,17 @@ def run_cross(args):
                        "p": p, "precision": "mixed"},
             "plain_solve_ms": ms_solve, "ratio_to_plain_solve": ms_cross / ms_solve,
             "status": int(st.item())}
+    if not args.no_cpu_baseline:
+        import oracle
+        Jh = J.cpu().numpy()
+        nX, nU = (N + 1) * n, N * m
+        Jq = Jh[:, :nX].reshape(p, N + 1, n)
+        Jr = Jh[:, nX:nX + nU].reshape(p, N, m)
+        Jc = Jh[:, nX + nU:].reshape(p, N + 1, n)
+        t0 = time.time()
+        oracle.cross_stage_solve(prob, Jq, Jr, Jc, H.cpu().numpy(), rt.cpu().numpy())
+        line["cpu_baseline"] = {"value": (time.time() - t0) * 1e3, "unit": "ms", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": "one dense bordered solve (numpy LAPACK)"}
     print(json.dumps(line), flush=True)
 
 
@@ -542,6 +553,23 @@ def run_warm_start(args):
             "cold": res["cold"], "warm": res["warm"], "training_solutions": int(F.shape[0]),
             "training_runs": K, "data_s": t_data, "train_s": t_train,
             "loss_first": losses[0], "loss_last": losses[-1]}
+    if not args.no_cpu_baseline:
+        import oracle.mlp as OM
+        p = net.p.cpu().numpy().astype(np.float64)
+        mm, vv = np.zeros_like(p), np.zeros_like(p)
+        Tn = norm.encode(T).astype(np.float64)
+        rng = np.random.default_rng(7)
+        t0, k = time.time(), 0
+        while time.time() - t0 < 10.0:
+            idx = rng.choice(F.shape[0], 256, replace=False)
+            _, g = OM.loss_and_grad(p, F[idx].astype(np.float64), Tn[idx], T.shape[1], 256)
+            p, mm, vv = OM.adam(p, mm, vv, g, k + 1, 1e-3)
+            k += 1
+        el = time.time() - t0
+        line["cpu_baseline"] = {"value": k / el, "unit": "training steps/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": f"{k} oracle training steps (batch 256, "
+                                "FP64 numpy with BF16 rounding)"}
+        line["gpu_training_steps_per_s"] = args.ws_steps / t_train
     print(json.dumps(line), flush=True)
 
 
@@ -588,6 +616,15 @@ def run_diag(args):
             "config": {"workload": "single instance n_x=12, n_u=4, N=256, Delta_i entries "
                                    "10^U(-6,-2)", "precision": "mixed"},
             "scalar_delta_ms": ms_plain, "ratio": ms_diag / ms_plain, "status": int(st.item())}
+    if not args.no_cpu_baseline:
+        import oracle
+        dh = d.cpu().numpy()
+        t0, k = time.time(), 0
+        while time.time() - t0 < 2.0:
+            oracle.riccati_diag(prob, dh)
+            k += 1
+        line["cpu_baseline"] = {"value": (time.time() - t0) * 1e3 / k, "unit": "ms", "cores": 1,
+                                "kind": "oracle", "sample": f"{k} general-Delta recursions (numpy)"}
     print(json.dumps(line), flush=True)
 
 
