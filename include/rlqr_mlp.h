@@ -21,7 +21,9 @@
  * b3 (rlqr_mlp_param_count values), a BF16 copy of the weights (raw uint16
  * bits, same order, biases included) refreshed by every update, and the Adam
  * moments (two FP32 arrays of the same length).  All pointers DEVICE; rows a
- * multiple of 16, at most max_rows; the workspace holds activations and
+ * multiple of 16, at most max_rows; params_bf16 and grad 32-byte aligned,
+ * the workspace 256-byte aligned (RLQR_ERR_ARG / RLQR_ERR_WORKSPACE
+ * otherwise); the workspace holds activations and
  * gradients for max_rows rows.
  */
 #ifndef RLQR_MLP_H_

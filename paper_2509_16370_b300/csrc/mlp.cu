@@ -277,8 +277,10 @@ rlqr_status rlqr_mlp_forward(const rlqr_mlp_dims *d, const uint16_t *params_bf16
 rlqr_status rlqr_mlp_grad(const rlqr_mlp_dims *d, const uint16_t *params_bf16, const float *x,
                           const float *t, const int32_t *idx, int32_t rows, float *loss,
                           float *grad, void *ws, size_t ws_bytes, rlqr_stream_t stream) {
+  // the tensor-core tiles load and store 32-byte aligned fragments
   if (!valid(d) || !params_bf16 || !x || !t || !loss || !grad || rows < 16 || rows % 16 ||
-      rows > d->max_rows || reinterpret_cast<uintptr_t>(params_bf16) % 32)
+      rows > d->max_rows || reinterpret_cast<uintptr_t>(params_bf16) % 32 ||
+      reinterpret_cast<uintptr_t>(grad) % 32)
     return RLQR_ERR_ARG;
   if (!ws_ok(d, ws, ws_bytes)) return RLQR_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
