@@ -179,3 +179,41 @@ def test_full_batch_invariants_and_sampled_kkt():
             continue
         lin = O.linearize(md, op, _oracle_state(st, b, x0, xg))
         assert abs(float(probe.kkt[b]) - lin.err0) <= 1e-10 * max(1.0, lin.err0)
+
+
+def test_bench_configuration_matches_the_oracle_on_sampled_instances():
+    """The configuration the bench times (8192 instances, FP32 Hessian term,
+    mixed-precision LQR solves with FP64 refinement to 1e-9): for 16 sampled
+    instances and each of 4 iterations, the oracle's iteration (FP64
+    throughout) from the GPU's state before it gives the GPU's state after it.
+    The FP32 Hessian term perturbs the Newton matrix by ~1e-7 relative, so the
+    states agree to 1e-5 relative, except where that perturbation moves an
+    Armijo test across its threshold (the accepted step then differs by a
+    power of two): at most 2 such near-ties among the 64 comparisons."""
+    count = 8192
+    x0, xg = inputs.workload5(count)
+    model = G.make_model()
+    opts = G.make_ipm_opts()
+    st = G.IpmState(count, model.N)
+    ws = G.alloc_ipm_workspace(count, model, opts)
+    dx0, dxg = torch.from_numpy(x0).cuda(), torch.from_numpy(xg).cuda()
+    G.rlqr_ipm_init(model, opts, dx0, st)
+    sample = np.random.default_rng(3).choice(count, 16, replace=False)
+    md, op = O.Model(), _oracle_opts(opts)
+    ties, compared = 0, 0
+    for it in range(4):
+        before = [_oracle_state(st, b, x0, xg) for b in sample]
+        G.rlqr_ipm_iterate(model, opts, dx0, dxg, st, ws)
+        torch.cuda.synchronize()
+        for b, s0 in zip(sample, before):
+            if s0.status != 0:
+                continue
+            ref = O.iterate(md, op, s0.copy())
+            got = _oracle_state(st, b, x0, xg)
+            compared += 1
+            assert got.status == ref.status and got.iters == ref.iters
+            e = max(_rel(getattr(got, k), getattr(ref, k)) for k in ("X", "U", "S", "Y", "Z"))
+            if e > 1e-5:
+                ties += 1
+    assert compared >= 48
+    assert ties <= 2, ties
