@@ -19,6 +19,12 @@ namespace rlqr {
 namespace ipm {
 
 constexpr int kThreads = 128;  // CTA size of the per-instance kernels
+// Control dimension of the LQR data: the force plus a decoupled dummy control
+// (zero columns of B and M, R = diag(R_uu, 1), r = 0, so its component of
+// every solution is 0 and the control pivot is diag(G_11, 1): the same
+// Newton step and certificate), which routes the batched solve to the FP32
+// block-pivot warp sweep (it needs an even control dimension).
+constexpr int kNu = 2;
 constexpr int kMaxN = 4096;
 constexpr size_t kAlignB = 256;
 
@@ -60,15 +66,15 @@ inline Layout layout(int count, int N, size_t lqr_ws_bytes) {
   };
   const size_t C = (size_t)count, n1 = (size_t)N + 1, n0 = (size_t)N;
   L.Q = take(C * n1 * 36 * 8);
-  L.M = take(C * n0 * 6 * 8);
-  L.R = take(C * n0 * 8);
+  L.M = take(C * n0 * 6 * kNu * 8);
+  L.R = take(C * n0 * kNu * kNu * 8);
   L.q = take(C * n1 * 6 * 8);
-  L.r = take(C * n0 * 8);
+  L.r = take(C * n0 * kNu * 8);
   L.A = take(C * n0 * 36 * 8);
-  L.B = take(C * n0 * 6 * 8);
+  L.B = take(C * n0 * 6 * kNu * 8);
   L.c = take(C * n1 * 6 * 8);
   L.dx = take(C * n1 * 6 * 8);
-  L.du = take(C * n0 * 8);
+  L.du = take(C * n0 * kNu * 8);
   L.dy = take(C * n1 * 6 * 8);
   L.flags = take(C * n1);
   L.dimN = take(C * 4);
@@ -209,9 +215,10 @@ __global__ void __launch_bounds__(kThreads)
   const double *X = a.X + b * n1 * 6, *U = a.U + (size_t)b * N, *Y = a.Y + b * n1 * 6;
   const double *S = a.S + b * n1 * 4, *Z = a.Z + b * n1 * 4;
   const double *x0 = a.x0 + (size_t)b * 6, *xg = a.xg + (size_t)b * 6;
-  double *Q = a.Q + b * n1 * 36, *Mx = a.M + (size_t)b * N * 6, *R = a.R + (size_t)b * N;
-  double *q = a.q + b * n1 * 6, *r = a.r + (size_t)b * N, *A = a.A + (size_t)b * N * 36;
-  double *B = a.B + (size_t)b * N * 6, *c = a.c + b * n1 * 6;
+  double *Q = a.Q + b * n1 * 36, *Mx = a.M + (size_t)b * N * 6 * kNu;
+  double *R = a.R + (size_t)b * N * kNu * kNu;
+  double *q = a.q + b * n1 * 6, *r = a.r + (size_t)b * N * kNu, *A = a.A + (size_t)b * N * 36;
+  double *B = a.B + (size_t)b * N * 6 * kNu, *c = a.c + b * n1 * 6;
   const rlqr_cdp_model &md = a.md;
 
   // The right-hand side depends on neither p (w_0) nor dp (w_3), so the RK4
@@ -249,8 +256,12 @@ __global__ void __launch_bounds__(kThreads)
       }
     } else {
 #pragma unroll
-      for (int l = 0; l < 6; ++l) B[i * 6 + l] = o[l].d;
-      r[i] = md.wu * U[i] + gj + Z[i * 4 + 0] - Z[i * 4 + 1];
+      for (int l = 0; l < 6; ++l) {
+        B[(i * 6 + l) * kNu] = o[l].d;
+        B[(i * 6 + l) * kNu + 1] = 0.0;
+      }
+      r[i * kNu] = md.wu * U[i] + gj + Z[i * 4 + 0] - Z[i * 4 + 1];
+      r[i * kNu + 1] = 0.0;
     }
   }
   if (threadIdx.x < 6) {
@@ -269,7 +280,7 @@ __global__ void __launch_bounds__(kThreads)
         Q[i * 36 + r * 6 + cc] = 0.0;
         Q[i * 36 + cc * 6 + r] = 0.0;
       } else {
-        Mx[i * 6 + (e == 11 ? 0 : 3)] = 0.0;
+        Mx[(i * 6 + (e == 11 ? 0 : 3)) * kNu] = 0.0;
       }
     }
     for (int t = threadIdx.x; t < 15 * N; t += kThreads) {
@@ -288,15 +299,22 @@ __global__ void __launch_bounds__(kThreads)
         Q[i * 36 + j * 6 + k] = h;
         Q[i * 36 + k * 6 + j] = h;
       } else if (j < 6) {
-        Mx[i * 6 + j] = h;
+        Mx[(i * 6 + j) * kNu] = h;
       } else {
-        R[i] = h;
+        R[i * kNu * kNu] = h;
       }
     }
   } else {
     for (int e = threadIdx.x; e < 36 * N; e += kThreads) Q[e] = 0.0;
-    for (int e = threadIdx.x; e < 6 * N; e += kThreads) Mx[e] = 0.0;
-    for (int e = threadIdx.x; e < N; e += kThreads) R[e] = 0.0;
+    for (int e = threadIdx.x; e < 6 * N; e += kThreads) Mx[e * kNu] = 0.0;
+    for (int e = threadIdx.x; e < N; e += kThreads) R[e * kNu * kNu] = 0.0;
+  }
+  // the dummy control: zero column of M, R row / column (0, 1)
+  for (int e = threadIdx.x; e < 6 * N; e += kThreads) Mx[e * kNu + 1] = 0.0;
+  for (int i = threadIdx.x; i < N; i += kThreads) {
+    R[i * 4 + 1] = 0.0;
+    R[i * 4 + 2] = 0.0;
+    R[i * 4 + 3] = 1.0;
   }
   __syncthreads();
 
@@ -306,7 +324,7 @@ __global__ void __launch_bounds__(kThreads)
   for (int i = threadIdx.x; i <= N; i += kThreads) {
 #pragma unroll
     for (int j = 0; j < 6; ++j) m_base = fmax(m_base, fmax(fabs(q[i * 6 + j]), fabs(c[i * 6 + j])));
-    if (i < N) m_base = fmax(m_base, fabs(r[i]));
+    if (i < N) m_base = fmax(m_base, fabs(r[i * kNu]));
     double g[4];
     ineq(md, i, N, X[i * 6], i < N ? U[i] : 0.0, g);
 #pragma unroll
@@ -375,8 +393,8 @@ __global__ void __launch_bounds__(kThreads)
     q[i * 6] += Dg[2] * rz[2] - Dg[3] * rz[3];
     if (i < N) {
       cst += md.wu * u * u;
-      R[i] += md.wu + Dg[0] + Dg[1];
-      r[i] += Dg[0] * rz[0] - Dg[1] * rz[1];
+      R[i * 4] += md.wu + Dg[0] + Dg[1];
+      r[i * kNu] += Dg[0] * rz[0] - Dg[1] * rz[1];
     }
     macc += 0.5 * cst;
   }
@@ -414,15 +432,15 @@ __global__ void k_ipm_offsets(Args a, const int32_t *list, int n, int64_t *oQ, i
   if (t >= n) return;
   const int64_t b = list[t], N = a.N, n1 = N + 1;
   oQ[t] = b * n1 * 36;
-  oM[t] = b * N * 6;
-  oR[t] = b * N;
+  oM[t] = b * N * 6 * kNu;
+  oR[t] = b * N * kNu * kNu;
   oq[t] = b * n1 * 6;
-  or_[t] = b * N;
+  or_[t] = b * N * kNu;
   oA[t] = b * N * 36;
-  oB[t] = b * N * 6;
+  oB[t] = b * N * 6 * kNu;
   oc[t] = b * n1 * 6;
   ox[t] = b * n1 * 6;
-  ou[t] = b * N;
+  ou[t] = b * N * kNu;
   oy[t] = b * n1 * 6;
   of[t] = b * n1;
 }
@@ -457,9 +475,9 @@ __global__ void k_ipm_cert(Args a, const int32_t *list, int n, int32_t *retry, i
     return;
   }
   const double add = nr - old;
-  double *Q = a.Q + (size_t)b * (N + 1) * 36, *R = a.R + (size_t)b * N;
+  double *Q = a.Q + (size_t)b * (N + 1) * 36, *R = a.R + (size_t)b * N * kNu * kNu;
   for (int e = lane; e < (N + 1) * 6; e += 32) Q[(e / 6) * 36 + (e % 6) * 7] += add;
-  for (int i = lane; i < N; i += 32) R[i] += add;
+  for (int i = lane; i < N; i += 32) R[i * kNu * kNu] += add;
   if (lane == 0) {
     a.rho_try[b] = nr;
     retry[atomicAdd(nretry, 1)] = b;
@@ -481,15 +499,16 @@ __global__ void __launch_bounds__(kThreads)
   double *X = a.X + b * n1 * 6, *U = a.U + (size_t)b * N, *Y = a.Y + b * n1 * 6;
   double *S = a.S + b * n1 * 4, *Z = a.Z + b * n1 * 4;
   const double *x0 = a.x0 + (size_t)b * 6, *xg = a.xg + (size_t)b * 6;
-  const double *A = a.A + (size_t)b * N * 36, *B = a.B + (size_t)b * N * 6, *c = a.c + b * n1 * 6;
-  const double *dX = a.dx + b * n1 * 6, *dU = a.du + (size_t)b * N, *dY = a.dy + b * n1 * 6;
+  const double *A = a.A + (size_t)b * N * 36, *B = a.B + (size_t)b * N * 6 * kNu;
+  const double *c = a.c + b * n1 * 6;
+  const double *dX = a.dx + b * n1 * 6, *dU = a.du + (size_t)b * N * kNu, *dY = a.dy + b * n1 * 6;
   double *dS = a.dS + b * n1 * 4, *dZ = a.dZ + b * n1 * 4;
   const rlqr_cdp_model &md = a.md;
   const double mu = a.mu[b], eta = a.op.eta, ieta = 1.0 / eta, tau = a.op.tau;
 
   double as = 1.0, az = 1.0, slope = 0.0;
   for (int i = threadIdx.x; i <= N; i += kThreads) {
-    const double du = i < N ? dU[i] : 0.0, u = i < N ? U[i] : 0.0;
+    const double du = i < N ? dU[i * kNu] : 0.0, u = i < N ? U[i] : 0.0;
     double g[4];
     ineq(md, i, N, X[i * 6], u, g);
     const double Gdx[4] = {du, -du, dX[i * 6], -dX[i * 6]};
@@ -517,7 +536,7 @@ __global__ void __launch_bounds__(kThreads)
       if (i == 0) {
         cd = -dX[j];
       } else {
-        cd = B[(i - 1) * 6 + j] * dU[i - 1] - dX[i * 6 + j];
+        cd = B[((i - 1) * 6 + j) * kNu] * dU[(i - 1) * kNu] - dX[i * 6 + j];
 #pragma unroll
         for (int l = 0; l < 6; ++l) cd += A[(i - 1) * 36 + j * 6 + l] * dX[(i - 1) * 6 + l];
       }
@@ -538,7 +557,7 @@ __global__ void __launch_bounds__(kThreads)
       double xt[6];
 #pragma unroll
       for (int j = 0; j < 6; ++j) xt[j] = X[i * 6 + j] + alpha * dX[i * 6 + j];
-      const double ut = i < N ? U[i] + alpha * dU[i] : 0.0;
+      const double ut = i < N ? U[i] + alpha * dU[i * kNu] : 0.0;
       double ct[6];
       if (i == 0) {
 #pragma unroll
@@ -547,7 +566,7 @@ __global__ void __launch_bounds__(kThreads)
         double xp[6], ph[6];
 #pragma unroll
         for (int j = 0; j < 6; ++j) xp[j] = X[(i - 1) * 6 + j] + alpha * dX[(i - 1) * 6 + j];
-        const double up_ = U[i - 1] + alpha * dU[i - 1];
+        const double up_ = U[i - 1] + alpha * dU[(i - 1) * kNu];
         cdp_rk4<double, double>(kd, xp, up_, ph);
 #pragma unroll
         for (int j = 0; j < 6; ++j) ct[j] = ph[j] - xt[j];
@@ -582,7 +601,7 @@ __global__ void __launch_bounds__(kThreads)
       X[i * 6 + j] += alpha * dX[i * 6 + j];
       Y[i * 6 + j] += alpha * dY[i * 6 + j];
     }
-    if (i < N) U[i] += alpha * dU[i];
+    if (i < N) U[i] += alpha * dU[i * kNu];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (i == N && k < 2) continue;
@@ -604,7 +623,7 @@ __global__ void k_ipm_dims(int count, int N, double delta, int32_t *dN, int32_t 
   if (t >= count) return;
   dN[t] = N;
   dn[t] = 6;
-  dm[t] = 1;
+  dm[t] = kNu;
   dd[t] = delta;
 }
 
@@ -642,7 +661,7 @@ rlqr_opts lqr_opts(const rlqr_ipm_opts *op) {
 
 struct HostDims {
   std::vector<int32_t> N, n, m;
-  HostDims(int count, int NN) : N(count, NN), n(count, 6), m(count, 1) {}
+  HostDims(int count, int NN) : N(count, NN), n(count, 6), m(count, kNu) {}
 };
 
 size_t lqr_ws_bytes(int count, const rlqr_cdp_model *md, const rlqr_ipm_opts *op) {
