@@ -236,33 +236,49 @@ __global__ void __launch_bounds__(kThreads)
     if (j == 0) g += Z[i * 4 + 2] - Z[i * 4 + 3];
     q[i * 6 + j] = g;
   }
-  for (int t = threadIdx.x; t < 5 * N; t += kThreads) {
-    const int i = t / 5, j = kDirs[t - 5 * i];
-    D1<double> x[6], u, o[6];
+  // Stages in chunks of kThreads: one plain FP64 RK4 per stage gives phi_i
+  // (the defect c_{i+1}) and records the 12 sines / cosines of its four
+  // right-hand sides; the five forward-mode directions of the stage replay
+  // them (their value path is the same RK4) instead of evaluating them again.
+  __shared__ double trig_rec[kThreads][24];
+  for (int c0 = 0; c0 < N; c0 += kThreads) {
+    const int nc = min(kThreads, N - c0);
+    if (threadIdx.x < nc) {
+      const int i = c0 + threadIdx.x;
+      double xv[6], ov[6];
 #pragma unroll
-    for (int l = 0; l < 6; ++l) x[l] = {X[i * 6 + l], l == j ? 1.0 : 0.0};
-    u = {U[i], j == 6 ? 1.0 : 0.0};
-    cdp_rk4<D1<double>, double>(kd, x, u, o);
-    double gj = 0.0;
+      for (int l = 0; l < 6; ++l) xv[l] = X[i * 6 + l];
+      const double uv = U[i];
+      cdp_rk4<double, double>(kd, xv, uv, ov, TrigRecord{trig_rec[threadIdx.x]});
 #pragma unroll
-    for (int l = 0; l < 6; ++l) gj += Y[(i + 1) * 6 + l] * o[l].d;
-    if (j < 6) {
-#pragma unroll
-      for (int l = 0; l < 6; ++l) A[i * 36 + l * 6 + j] = o[l].d;
-      q[i * 6 + j] = md.wx[j] * (X[i * 6 + j] - xg[j]) + gj - Y[i * 6 + j];
-      if (j == 1) {
-#pragma unroll
-        for (int l = 0; l < 6; ++l) c[(i + 1) * 6 + l] = o[l].v - X[(i + 1) * 6 + l];
-      }
-    } else {
-#pragma unroll
-      for (int l = 0; l < 6; ++l) {
-        B[(i * 6 + l) * kNu] = o[l].d;
-        B[(i * 6 + l) * kNu + 1] = 0.0;
-      }
-      r[i * kNu] = md.wu * U[i] + gj + Z[i * 4 + 0] - Z[i * 4 + 1];
-      r[i * kNu + 1] = 0.0;
+      for (int l = 0; l < 6; ++l) c[(i + 1) * 6 + l] = ov[l] - X[(i + 1) * 6 + l];
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 5 * nc; t += kThreads) {
+      const int il = t / 5, i = c0 + il, j = kDirs[t - 5 * il];
+      D1<double> x[6], u, o[6];
+#pragma unroll
+      for (int l = 0; l < 6; ++l) x[l] = {X[i * 6 + l], l == j ? 1.0 : 0.0};
+      u = {U[i], j == 6 ? 1.0 : 0.0};
+      cdp_rk4<D1<double>, double>(kd, x, u, o, TrigReplay{trig_rec[il]});
+      double gj = 0.0;
+#pragma unroll
+      for (int l = 0; l < 6; ++l) gj += Y[(i + 1) * 6 + l] * o[l].d;
+      if (j < 6) {
+#pragma unroll
+        for (int l = 0; l < 6; ++l) A[i * 36 + l * 6 + j] = o[l].d;
+        q[i * 6 + j] = md.wx[j] * (X[i * 6 + j] - xg[j]) + gj - Y[i * 6 + j];
+      } else {
+#pragma unroll
+        for (int l = 0; l < 6; ++l) {
+          B[(i * 6 + l) * kNu] = o[l].d;
+          B[(i * 6 + l) * kNu + 1] = 0.0;
+        }
+        r[i * kNu] = md.wu * U[i] + gj + Z[i * 4 + 0] - Z[i * 4 + 1];
+        r[i * kNu + 1] = 0.0;
+      }
+    }
+    __syncthreads();
   }
   if (threadIdx.x < 6) {
     const int j = threadIdx.x;

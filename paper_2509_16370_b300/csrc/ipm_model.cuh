@@ -133,14 +133,57 @@ inline CdpConst<T> cdp_const(const rlqr_cdp_model &md) {
   return k;
 }
 
+// The sines and cosines of one right-hand side (of th1, th2, th1 - th2):
+// computed (TrigCompute), computed and recorded as plain doubles
+// (TrigRecord), or replayed from a record with the derivative parts formed
+// from the caller's numbers (TrigReplay) -- the value path of every forward
+// direction of a stage is the same RK4, so its transcendental evaluations are
+// done once per stage.
+struct TrigCompute {
+  template <class Num>
+  __device__ __forceinline__ void operator()(const Num &a, const Num &b, const Num &d, Num *sc) {
+    sin_cos(a, sc[0], sc[1]);
+    sin_cos(b, sc[2], sc[3]);
+    sin_cos(d, sc[4], sc[5]);
+  }
+};
+
+struct TrigRecord {
+  double *rec;  // 6 values per right-hand side, appended
+  __device__ __forceinline__ void operator()(const double &a, const double &b, const double &d,
+                                             double *sc) {
+    sin_cos(a, sc[0], sc[1]);
+    sin_cos(b, sc[2], sc[3]);
+    sin_cos(d, sc[4], sc[5]);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) rec[j] = sc[j];
+    rec += 6;
+  }
+};
+
+struct TrigReplay {
+  const double *rec;
+  __device__ __forceinline__ void one(const D1<double> &x, double s, double c, D1<double> &S,
+                                      D1<double> &C) {
+    S = {s, c * x.d};
+    C = {c, -s * x.d};
+  }
+  __device__ __forceinline__ void operator()(const D1<double> &a, const D1<double> &b,
+                                             const D1<double> &d, D1<double> *sc) {
+    one(a, rec[0], rec[1], sc[0], sc[1]);
+    one(b, rec[2], rec[3], sc[2], sc[3]);
+    one(d, rec[4], rec[5], sc[4], sc[5]);
+    rec += 6;
+  }
+};
+
 // xdot = f(x, u) for any number type Num over the scalar type T.
-template <class Num, class T>
+template <class Num, class T, class Trig = TrigCompute>
 __device__ __forceinline__ void cdp_rhs(const CdpConst<T> &k, const Num x[6], const Num &u,
-                                        Num f[6]) {
-  Num s1, c1, s2, c2, s12, c12;
-  sin_cos(x[1], s1, c1);
-  sin_cos(x[2], s2, c2);
-  sin_cos(x[1] - x[2], s12, c12);
+                                        Num f[6], Trig &&trig = Trig{}) {
+  Num sc[6];
+  trig(x[1], x[2], x[1] - x[2], sc);
+  const Num &s1 = sc[0], &c1 = sc[1], &s2 = sc[2], &c2 = sc[3], &s12 = sc[4], &c12 = sc[5];
   const Num w1s = x[4] * x[4], w2s = x[5] * x[5];
   const Num M12 = c1 * k.a1, M13 = c2 * k.a2, M23 = c12 * k.b12;
   const Num t1 = u + (s1 * w1s * k.a1 + s2 * w2s * k.a2);
@@ -162,29 +205,29 @@ __device__ __forceinline__ void cdp_rhs(const CdpConst<T> &k, const Num x[6], co
 }
 
 // One classical RK4 step of length dt with the control held.
-template <class Num, class T>
+template <class Num, class T, class Trig = TrigCompute>
 __device__ __forceinline__ void cdp_rk4(const CdpConst<T> &k, const Num x[6], const Num &u,
-                                        Num out[6]) {
+                                        Num out[6], Trig &&trig = Trig{}) {
   Num kk[6], acc[6], z[6];
-  cdp_rhs(k, x, u, kk);
+  cdp_rhs(k, x, u, kk, trig);
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     acc[j] = kk[j];
     z[j] = x[j] + kk[j] * k.h2;
   }
-  cdp_rhs(k, z, u, kk);
+  cdp_rhs(k, z, u, kk, trig);
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     acc[j] = acc[j] + kk[j] * T(2);
     z[j] = x[j] + kk[j] * k.h2;
   }
-  cdp_rhs(k, z, u, kk);
+  cdp_rhs(k, z, u, kk, trig);
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
     acc[j] = acc[j] + kk[j] * T(2);
     z[j] = x[j] + kk[j] * k.h;
   }
-  cdp_rhs(k, z, u, kk);
+  cdp_rhs(k, z, u, kk, trig);
 #pragma unroll
   for (int j = 0; j < 6; ++j) out[j] = x[j] + (acc[j] + kk[j]) * k.h6;
 }
