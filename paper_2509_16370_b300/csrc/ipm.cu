@@ -52,7 +52,7 @@ struct Args {
 struct Layout {
   size_t Q, M, R, q, r, A, B, c, dx, du, dy, flags;
   size_t dimN, dimn, dimm, oQ, oM, oR, oq, or_, oA, oB, oc, ox, ou, oy, of, delta;
-  size_t rho_try, merit0, alpha, lqr_status, lqr_rel, lqr_iters, list, list2, list3, counter, dS, dZ;
+  size_t rho_try, merit0, alpha, lqr_status, list, list2, list3, counter, dS, dZ;
   size_t lqr_ws, total;
 };
 
@@ -97,8 +97,6 @@ inline Layout layout(int count, int N, size_t lqr_ws_bytes) {
   L.merit0 = take(C * 8);
   L.alpha = take(C * 8);
   L.lqr_status = take(C * 4);
-  L.lqr_rel = take(C * 8);
-  L.lqr_iters = take(C * 4);
   L.list = take(C * 4);
   L.list2 = take(C * 4);
   L.list3 = take(C * 4);

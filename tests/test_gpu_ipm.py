@@ -68,12 +68,12 @@ def test_initial_point_matches_the_oracle():
         assert got.mu == ref.mu and got.iters == 0 and got.status == 0
 
 
-@pytest.mark.parametrize("N", [1, 40, 300])
+@pytest.mark.parametrize("N", [1, 40, 300, 4096])
 @pytest.mark.parametrize("hess", [G.RLQR_IPM_HESS_EXACT_FP64, G.RLQR_IPM_HESS_EXACT_FP32,
                                   G.RLQR_IPM_HESS_GAUSS_NEWTON])
 def test_linearization_matches_the_oracle(hess, N):
-    """Horizons of one stage, of a partial pass and of several passes of the
-    128-thread CTA over the stages."""
+    """Horizons of one stage, of a partial pass, of several passes of the
+    128-thread CTA over the stages, and the largest the ABI accepts."""
     bs = [0, 3, 7]
     model, opts, st, ws, dx0, dxg, x0, xg = _setup(bs, N=N, hessian=hess)
     rng = np.random.default_rng(5)
