@@ -527,7 +527,7 @@ def run_warm_start(args):
     t_train = time.time() - t1
     x0, xg = inputs.workload5(B, 1_000_000)
     dx0, dxg = torch.from_numpy(x0).cuda(), torch.from_numpy(xg).cuda()
-    res = {}
+    res, per = {}, {}
     for kind in ("cold", "warm"):
         t2 = time.time()
         if kind == "cold":
@@ -539,10 +539,12 @@ def run_warm_start(args):
         torch.cuda.synchronize()
         status, iters = st.status.cpu().numpy(), st.iters.cpu().numpy()
         conv = status == ipm.CONVERGED
+        per[kind] = (conv, iters)
         res[kind] = {"converged_fraction": float(conv.mean()),
                      "mean_iterations_converged": float(iters[conv].mean()) if conv.any() else None,
                      "mean_iterations_all": float(iters.mean()),
                      "solve_s": time.time() - t2}
+    both = per["cold"][0] & per["warm"][0]
     line = {"metric": "IPM mean iterations to convergence, cold vs learned warm start",
             "value": res["warm"]["mean_iterations_all"], "unit": "iterations (all instances, "
             "capped at max_iter)", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
@@ -550,7 +552,13 @@ def run_warm_start(args):
                                    f"runs {K}, held-out 8192",
                        "network": "3 layers, width 256, BF16 weights/activations, Adam",
                        "train_steps": args.ws_steps, "batch": 256},
-            "cold": res["cold"], "warm": res["warm"], "training_solutions": int(F.shape[0]),
+            "cold": res["cold"], "warm": res["warm"],
+            "paired": {"instances_converged_both": int(both.sum()),
+                       "mean_iterations_cold": float(per["cold"][1][both].mean()) if both.any() else None,
+                       "mean_iterations_warm": float(per["warm"][1][both].mean()) if both.any() else None,
+                       "converged_warm_only": int((per["warm"][0] & ~per["cold"][0]).sum()),
+                       "converged_cold_only": int((per["cold"][0] & ~per["warm"][0]).sum())},
+            "training_solutions": int(F.shape[0]),
             "training_runs": K, "data_s": t_data, "train_s": t_train,
             "loss_first": losses[0], "loss_last": losses[-1]}
     if not args.no_cpu_baseline:
