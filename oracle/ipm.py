@@ -7,17 +7,17 @@ Point Method" and Section "Applying the regularized IPM to optimal control"):
 
   min f(x)  s.t.  c(x) = 0,  g(x) + s = 0,  s >= 0
   L(x, s, y, z; mu)  = f - mu sum log s + y^T c + z^T (g + s)
-  A(x, s; y, z, mu)  = L + 1/2 (eta ||c||^2 + eta_g ||g + s||^2)     (merit)
+  A(x, s; y, z, mu)  = L + 1/2 (eta ||c||^2 + eta ||g + s||^2)     (merit)
 
 Each iteration solves the Newton-KKT system eq. ipm-3x3-newton-kkt with
-W = S Z^{-1}, Delta_C = eta I, Delta_G = eta_g I, by eliminating
+W = S Z^{-1}, Delta_C = Delta_G = eta I, by eliminating
 Delta z = (W + Delta_G^{-1})^{-1} (G Delta x + r_z) and passing the reduced
 (x, y) system to the dual-regularized LQR solve (delta = 1 / eta); then
 Delta s = -W (Delta z - mu S^{-1} e + z).  The LQR step is the oracle's
 sequential recursion (``oracle.riccati``), whose pivot-PD flags are the
 inertia certificate: when a flag is not PD the Hessian is shifted by rho I
-and the system re-solved (the rho I correction after Theorem
-inertia-al-descent).  With correct inertia the primal direction descends the
+and the system re-solved within the same iteration (the rho I correction
+after Theorem inertia-al-descent).  With correct inertia the primal direction descends the
 merit function (Theorem inertia-al-descent), and a backtracking Armijo line
 search on A with (y, z) fixed accepts the step.
 
