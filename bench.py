@@ -675,6 +675,19 @@ def run_long_horizon(args):
         return e0.elapsed_time(e1) / steps
 
     step, bufs = make(rlqr.RLQR_MIXED, rlqr.RLQR_ALGO_SCAN)
+    chunks = int((N + max(8, (N + 443) // 444) - 1) // max(8, (N + 443) // 444))
+    tune = None
+    if args.autotune:
+        # the scan's tile (chunk count) chosen by timing the candidates; the
+        # default chunking is timed beside it
+        ms_default = timed(step, args.steps, args.warmup)
+        o = rlqr.make_opts(rlqr.RLQR_MIXED, algo=rlqr.RLQR_ALGO_SCAN, tol=TOL, max_refine=3)
+        wst = rlqr.alloc_workspace(rlqr.rlqr_workspace_bytes(N, n, m, o))
+        chunks, tms = rlqr.rlqr_autotune_scan(dp, o, wst, bufs["x"], bufs["u"], bufs["y"],
+                                              bufs["flags"])
+        del wst
+        tune = {"chunks": chunks, "autotune_ms": tms, "default_ms": ms_default,
+                "candidates": list(rlqr.SCAN_CHUNK_CANDIDATES)}
     rlqr.rlqr_instrument(True)
     with ClockSampler(0) as clk:
         ms = timed(step, args.steps, args.warmup)
@@ -691,7 +704,7 @@ def run_long_horizon(args):
             "data": "synthetic",
             "config": {"workload": "one dual-regularized LQR, n_x=32, n_u=8, N=65536, delta=1e-7, "
                                    "rho(A)=0.99, cond(Q)=cond(R)=1e4", "algo": "scan",
-                       "chunks": int((N + max(8, (N + 443) // 444) - 1) // max(8, (N + 443) // 444)),
+                       "chunks": chunks, "autotune": tune,
                        "l2": "inputs 1.4 GB > L2 (no flush needed)"},
             "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in report.items()},
             "accuracy": {"rel_resid": rel, "all_le_tol": rel <= TOL,
@@ -824,6 +837,17 @@ def run_ours(args):
     # the arithmetic pipes' measured rates (roofline denominators of the FP64
     # and FP32 kernels), taken before the timed regions
     pipes = rlqr.rlqr_measure_pipes()
+    # setup, not timed: the autotuner times the batch's residual routes
+    # (warp per instance / grid over all stages) and records the faster one
+    # for this shape, which the timed solves then take
+    tune = {}
+    for prec, name in ((rlqr.RLQR_MIXED, "mixed"), (rlqr.RLQR_FP64, "fp64")):
+        o_t, ws_t, st_t, _, _ = setup(prec)
+        route, tms = rlqr.rlqr_autotune_batched(db, o_t, ws_t, st_t)
+        tune[name] = {"residual_route": {rlqr.RES_ROUTE_WARP: "warp",
+                                         rlqr.RES_ROUTE_GRID: "grid"}[route],
+                      "ms": round(tms, 4)}
+        del ws_t
     with ClockSampler(local) as clk:
         ms_mixed, report, chk_mixed = timed(rlqr.RLQR_MIXED, args.steps, args.warmup, True)
     ms_fp64, report64, chk_fp64 = timed(rlqr.RLQR_FP64, max(3, args.steps // 4), args.warmup, True)
@@ -873,7 +897,8 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64 (FP32 sweep; FP64 certificate, residual, correction)",
         "data": "synthetic", "config": dict(WORKLOAD, parallelism=f"replicas x{world}",
-                                              precision="mixed", max_refine=3, tol=TOL),
+                                              precision="mixed", max_refine=3, tol=TOL,
+                                              autotune=tune),
         "roofline": roofline(report, args.steps, n, m, stages, load_peaks(), pipes["fp64_tflops"]),
         "pipes": {k: round(v, 2) for k, v in pipes.items()},
         "kernels": {k: {"launches": c, "ms_total": round(t, 4)} for k, (c, t) in report.items()},
@@ -906,6 +931,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-instances", type=int, default=0,
                     help="profiling case: the mixed solve on the first K instances only")
+    ap.add_argument("--autotune", action="store_true",
+                    help="with --long-horizon: choose the scan's chunk count by timing first")
     ap.add_argument("--long-horizon", action="store_true",
                     help="the single long-horizon instance (associative scan)")
     ap.add_argument("--cross", type=int, default=0,

@@ -207,6 +207,49 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
                                int32_t *iters, rlqr_stream_t stream);
 
 /* ------------------------------------------------------------------ *
+ * Autotuning: the scan's chunk length and the batched residual route.  *
+ * ------------------------------------------------------------------ */
+
+/* The scan path (RLQR_ALGO_SCAN, or AUTO from N = 4096) folds the horizon in
+ * chunks of L stages, one CTA per chunk; by default about 444 chunks (three
+ * CTAs per SM of a 148-SM part), L >= 8.  rlqr_autotune_scan times
+ * rlqr_factor + rlqr_solve of `prob` (three timed runs after a warm-up,
+ * CUDA events, host-synchronising) for 148, 296, 444, 592 and 888 chunks
+ * and records the fastest for (nx, nu, opts->prec, floor(log2 N)) in a
+ * process-wide table (mutex-protected) that later factorizations of that
+ * shape use; best_chunks / best_ms (host, may be NULL) receive the choice
+ * and its time.  x, u, y, pivot_pd are scratch outputs of the timed solves;
+ * ws as for rlqr_factor (rlqr_workspace_bytes sizes every scan workspace
+ * for the largest candidate count).  RLQR_ERR_ARG if the problem does not
+ * take the scan path.  A factorization and the solves that use it must run
+ * with the same table entry: re-factor after tuning.
+ * rlqr_tune_scan_set records a chunk count explicitly (1..888; 0 removes
+ * the entry) and rlqr_tune_reset clears the table. */
+rlqr_status rlqr_autotune_scan(const rlqr_problem *prob, const rlqr_opts *opts, void *ws,
+                               size_t ws_bytes, double *x, double *u, double *y,
+                               uint8_t *pivot_pd, int32_t *best_chunks, double *best_ms,
+                               rlqr_stream_t stream);
+rlqr_status rlqr_tune_scan_set(int32_t N, int32_t nx, int32_t nu, const rlqr_opts *opts,
+                               int32_t chunks);
+
+/* Residual route of uniform batches of the FP32 warp-sweep sizes ((4,2),
+ * (6,2), (12,4)): 1 = one warp per instance (float-float in mixed mode),
+ * 2 = the stage-parallel grid over all stages of the batch.
+ * rlqr_autotune_batched times rlqr_solve_batched on `batch` with each route
+ * (a warm-up and three timed runs, CUDA events, host-synchronising) and
+ * records the faster one for (nx, nu, opts->prec, floor(log2 max N),
+ * floor(log2 count)) in the process-wide table; status (device [count],
+ * may be NULL) is scratch for the timed solves; best_route / best_ms (host,
+ * may be NULL) receive the choice and its time.  RLQR_ERR_ARG for ragged
+ * batches or other sizes.  rlqr_tune_batched_set records a route explicitly
+ * (0 removes the entry).  rlqr_tune_reset clears both tables. */
+rlqr_status rlqr_autotune_batched(const rlqr_batch *batch, const rlqr_opts *opts, void *ws,
+                                  size_t ws_bytes, int32_t *status, int32_t *best_route,
+                                  double *best_ms, rlqr_stream_t stream);
+rlqr_status rlqr_tune_batched_set(const rlqr_batch *batch, const rlqr_opts *opts, int32_t route);
+rlqr_status rlqr_tune_reset(void);
+
+/* ------------------------------------------------------------------ *
  * General diagonal dual regularization Delta_i = diag(d_i).            *
  * ------------------------------------------------------------------ */
 

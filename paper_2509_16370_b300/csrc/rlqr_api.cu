@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 
 #include "common.cuh"
@@ -69,9 +70,35 @@ static bool warp_sweep32_size(int n, int m) {
   return (n == 4 && m == 2) || (n == 6 && m == 2) || (n == 12 && m == 4);
 }
 
+// Residual route of a uniform launch group of a warp size: 0 = by size (the
+// warp residual), 1 = the warp residual, 2 = the stage-parallel grid
+// residual.  Batches record the autotuner's choice (rlqr_autotune_batched)
+// per (nx, nu, precision, floor(log2 max N), floor(log2 count)).
+static std::mutex g_route_mu;
+static std::map<uint64_t, int> g_res_route;
+
+static int ilog2(int v) {
+  int l = 0;
+  while (l < 30 && (1 << (l + 1)) <= v) ++l;
+  return l;
+}
+
+static uint64_t route_key(int N, int n, int m, int tsize, int count) {
+  return ((uint64_t)n << 40) | ((uint64_t)m << 32) | ((uint64_t)tsize << 24) |
+         ((uint64_t)ilog2(N) << 8) | (uint64_t)ilog2(count);
+}
+
+static int residual_route(int N, int n, int m, int tsize, int count) {
+  std::lock_guard<std::mutex> lock(g_route_mu);
+  const auto it = g_res_route.find(route_key(N, n, m, tsize, count));
+  return it == g_res_route.end() ? 0 : it->second;
+}
+
 static cudaError_t launch_first_residual(const BatchArgs &a, int n, int m, bool mixed, int cert_g,
-                                         const int64_t *spre, int64_t items, cudaStream_t s) {
-  if (!warp_sweep32_size(n, m)) return launch_grid_residual(a, spre, items, mixed, cert_g, s);
+                                         const int64_t *spre, int64_t items, cudaStream_t s,
+                                         int route = 0) {
+  if (!warp_sweep32_size(n, m) || (route == 2 && spre))
+    return launch_grid_residual(a, spre, items, mixed, cert_g, s);
   if (mixed) return launch_residual32<float>(n, m, true, a, cert_g, s);
   return launch_residual(a, 2 * n + m, 0, nullptr, nullptr, 1, 0, s);
 }
@@ -284,10 +311,35 @@ static int use_scan(const rlqr_problem *p, const rlqr_opts *o) {
   return 0;
 }
 
+// ---- scan tiles: the chunk of stages one CTA folds.  Default: about 444
+// chunks (three CTAs per SM on 148 SMs), at least 8 stages.  The autotuner
+// (rlqr_autotune_scan) times chunk counts that are multiples of the SM count
+// and records the fastest per (nx, nu, precision, floor(log2 N)); later
+// factorizations of that shape use it.  Workspaces are sized for the largest
+// candidate count, so every recorded choice fits.
+constexpr int kScanChunkCandidates[] = {148, 296, 444, 592, 888};
+constexpr int kScanChunkMax = 888;
+std::mutex g_tune_mu;
+std::map<uint64_t, int> g_scan_chunks;
+
+static uint64_t tune_key(int N, int n, int m, int tsize) {
+  int lg = 0;
+  while (lg < 30 && (1 << (lg + 1)) <= N) ++lg;
+  return ((uint64_t)n << 40) | ((uint64_t)m << 32) | ((uint64_t)tsize << 24) | (uint64_t)lg;
+}
+
+static int chunk_len_of_count(int N, int chunks) { return std::max(8, (N + chunks - 1) / chunks); }
+
+static int scan_len_for(int N, int n, int m, int tsize) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  const auto it = g_scan_chunks.find(tune_key(N, n, m, tsize));
+  return it == g_scan_chunks.end() ? scan_chunk_len(N) : chunk_len_of_count(N, it->second);
+}
+
 static ScanLayout scan_args(const rlqr_problem *p, const rlqr_opts *o, size_t *sbase) {
   const int tsize = o->prec == RLQR_MIXED ? 4 : 8;
   *sbase = ws_layout(p->N, p->nx, p->nu, tsize).total;
-  return scan_layout(p->N, p->nx, scan_chunk_len(p->N), tsize);
+  return scan_layout(p->N, p->nx, scan_len_for(p->N, p->nx, p->nu, tsize), tsize);
 }
 
 }  // namespace rlqr
@@ -326,7 +378,8 @@ size_t rlqr_workspace_bytes(int32_t N, int32_t nx, int32_t nu, const rlqr_opts *
   if (!valid_dims(N, nx, nu) || !valid_opts(opts)) return 0;
   int tsize = opts->prec == RLQR_MIXED ? 4 : 8;
   size_t tot = ws_layout(N, nx, nu, tsize).total;
-  if (scan_sized(N, nx, nu, opts)) tot += scan_layout(N, nx, scan_chunk_len(N), tsize).total;
+  if (scan_sized(N, nx, nu, opts))
+    tot += scan_layout(N, nx, chunk_len_of_count(N, kScanChunkMax), tsize).total;
   return tot;
 }
 
@@ -578,8 +631,13 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
         static_cast<char *>(ws) + align_up((size_t)B.count * sizeof(int64_t)) +
         align_up((size_t)B.count * sizeof(int32_t)));
     int64_t items = 0;
-    for (int b = 0; b < B.count; ++b) items += (int64_t)B.h_N[b] + 1;
-    e = uniform ? launch_first_residual(a, nmax, mmax, mixed, 1, spre, items, s)
+    int nmaxN = 1;
+    for (int b = 0; b < B.count; ++b) {
+      items += (int64_t)B.h_N[b] + 1;
+      nmaxN = std::max(nmaxN, B.h_N[b]);
+    }
+    const int route = uniform ? residual_route(nmaxN, nmax, mmax, a.tsize, B.count) : 0;
+    e = uniform ? launch_first_residual(a, nmax, mmax, mixed, 1, spre, items, s, route)
                 : launch_grid_residual(a, spre, items, mixed, 1, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
@@ -906,6 +964,164 @@ int rlqr_instrument_report(int max, const char **names, int64_t *launches, doubl
     ms[j] += t;
   }
   return k;
+}
+
+}  // extern "C"
+
+// ---- scan tile autotuning
+extern "C" {
+
+rlqr_status rlqr_tune_scan_set(int32_t N, int32_t nx, int32_t nu, const rlqr_opts *opts,
+                               int32_t chunks) {
+  if (!valid_dims(N, nx, nu) || !valid_opts(opts)) return RLQR_ERR_ARG;
+  if (chunks != 0 && (chunks < 1 || chunks > kScanChunkMax)) return RLQR_ERR_ARG;
+  const int tsize = opts->prec == RLQR_MIXED ? 4 : 8;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (chunks == 0)
+    g_scan_chunks.erase(tune_key(N, nx, nu, tsize));
+  else
+    g_scan_chunks[tune_key(N, nx, nu, tsize)] = chunks;
+  return RLQR_OK;
+}
+
+rlqr_status rlqr_tune_reset(void) {
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_scan_chunks.clear();
+  }
+  std::lock_guard<std::mutex> lock(g_route_mu);
+  g_res_route.clear();
+  return RLQR_OK;
+}
+
+static bool batch_tune_key(const rlqr_batch *batch, const rlqr_opts *opts, uint64_t *key) {
+  if (!batch || batch->count < 1 || !batch->h_N || !batch->h_nx || !batch->h_nu ||
+      !valid_opts(opts))
+    return false;
+  int nmaxN = 1;
+  for (int b = 0; b < batch->count; ++b) {
+    if (batch->h_nx[b] != batch->h_nx[0] || batch->h_nu[b] != batch->h_nu[0]) return false;
+    nmaxN = std::max(nmaxN, batch->h_N[b]);
+  }
+  if (!warp_sweep32_size(batch->h_nx[0], batch->h_nu[0])) return false;
+  *key = route_key(nmaxN, batch->h_nx[0], batch->h_nu[0], opts->prec == RLQR_MIXED ? 4 : 8,
+                   batch->count);
+  return true;
+}
+
+rlqr_status rlqr_tune_batched_set(const rlqr_batch *batch, const rlqr_opts *opts, int32_t route) {
+  uint64_t key;
+  if (!batch_tune_key(batch, opts, &key) || route < 0 || route > 2) return RLQR_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_route_mu);
+  if (route == 0)
+    g_res_route.erase(key);
+  else
+    g_res_route[key] = route;
+  return RLQR_OK;
+}
+
+rlqr_status rlqr_autotune_batched(const rlqr_batch *batch, const rlqr_opts *opts, void *ws,
+                                  size_t ws_bytes, int32_t *status, int32_t *best_route,
+                                  double *best_ms, rlqr_stream_t stream) {
+  uint64_t key;
+  if (!batch_tune_key(batch, opts, &key)) return RLQR_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  rlqr_opts o = *opts;
+  o.flags = 0;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return RLQR_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return RLQR_ERR_CUDA;
+  }
+  rlqr_status err = RLQR_OK;
+  int best = 0;
+  float best_t = 0.0f;
+  const int reps = 3;
+  for (int route = 1; route <= 2 && err == RLQR_OK; ++route) {
+    err = rlqr_tune_batched_set(batch, opts, route);
+    float t = 0.0f;
+    for (int r = 0; r <= reps && err == RLQR_OK; ++r) {  // r = 0: warm-up
+      if (r == 1 && cudaEventRecord(e0, s) != cudaSuccess) err = RLQR_ERR_CUDA;
+      if (err == RLQR_OK)
+        err = rlqr_solve_batched(batch, &o, ws, ws_bytes, status, nullptr, nullptr, stream);
+    }
+    if (err != RLQR_OK) break;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+      err = RLQR_ERR_CUDA;
+      break;
+    }
+    t /= reps;
+    if (best == 0 || t < best_t) {
+      best = route;
+      best_t = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != RLQR_OK) {
+    rlqr_tune_batched_set(batch, opts, 0);
+    return err;
+  }
+  rlqr_tune_batched_set(batch, opts, best);
+  if (best_route) *best_route = best;
+  if (best_ms) *best_ms = best_t;
+  return RLQR_OK;
+}
+
+rlqr_status rlqr_autotune_scan(const rlqr_problem *prob, const rlqr_opts *opts, void *ws,
+                               size_t ws_bytes, double *x, double *u, double *y,
+                               uint8_t *pivot_pd, int32_t *best_chunks, double *best_ms,
+                               rlqr_stream_t stream) {
+  if (!valid_problem(prob) || !valid_opts(opts) || !x || !u || !y || !pivot_pd)
+    return RLQR_ERR_ARG;
+  if (use_scan(prob, opts) != 1) return RLQR_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  rlqr_opts o = *opts;
+  o.flags = 0;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return RLQR_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return RLQR_ERR_CUDA;
+  }
+  rlqr_status err = RLQR_OK;
+  int best = 0;
+  float best_t = 0.0f;
+  const int reps = 3;
+  for (int c : kScanChunkCandidates) {
+    err = rlqr_tune_scan_set(prob->N, prob->nx, prob->nu, opts, c);
+    if (err != RLQR_OK) break;
+    float t = 0.0f;
+    for (int r = 0; r <= reps && err == RLQR_OK; ++r) {  // r = 0: warm-up
+      if (r == 1 && cudaEventRecord(e0, s) != cudaSuccess) err = RLQR_ERR_CUDA;
+      if (err == RLQR_OK) err = rlqr_factor(prob, &o, ws, ws_bytes, pivot_pd, nullptr, stream);
+      if (err == RLQR_OK)
+        err = rlqr_solve(prob, &o, ws, ws_bytes, x, u, y, nullptr, nullptr, nullptr, stream);
+    }
+    if (err != RLQR_OK) break;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+      err = RLQR_ERR_CUDA;
+      break;
+    }
+    t /= reps;
+    if (best == 0 || t < best_t) {
+      best = c;
+      best_t = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != RLQR_OK) {
+    rlqr_tune_scan_set(prob->N, prob->nx, prob->nu, opts, 0);
+    return err;
+  }
+  rlqr_tune_scan_set(prob->N, prob->nx, prob->nu, opts, best);
+  if (best_chunks) *best_chunks = best;
+  if (best_ms) *best_ms = best_t;
+  return RLQR_OK;
 }
 
 }  // extern "C"

@@ -98,6 +98,18 @@ def _load():
     lib.rlqr_solve_cross.restype = st
     lib.rlqr_solve_cross.argtypes = [P(rlqr_problem), P(rlqr_opts), _dp, sz, ctypes.c_int32, _dp,
                                      _dp, _dp, _dp, sz, _dp, _dp, _dp, _dp, _dp, _dp]
+    lib.rlqr_autotune_scan.restype = st
+    lib.rlqr_autotune_scan.argtypes = [P(rlqr_problem), P(rlqr_opts), _dp, sz, _dp, _dp, _dp, _dp,
+                                       P(ctypes.c_int32), P(ctypes.c_double), _dp]
+    lib.rlqr_tune_scan_set.restype = st
+    lib.rlqr_tune_scan_set.argtypes = [ctypes.c_int32] * 3 + [P(rlqr_opts), ctypes.c_int32]
+    lib.rlqr_autotune_batched.restype = st
+    lib.rlqr_autotune_batched.argtypes = [P(rlqr_batch), P(rlqr_opts), _dp, sz, _dp,
+                                          P(ctypes.c_int32), P(ctypes.c_double), _dp]
+    lib.rlqr_tune_batched_set.restype = st
+    lib.rlqr_tune_batched_set.argtypes = [P(rlqr_batch), P(rlqr_opts), ctypes.c_int32]
+    lib.rlqr_tune_reset.restype = st
+    lib.rlqr_tune_reset.argtypes = []
     lib.rlqr_diag_workspace_bytes.restype = sz
     lib.rlqr_diag_workspace_bytes.argtypes = [ctypes.c_int32] * 3 + [P(rlqr_opts)]
     lib.rlqr_solve_diag.restype = st
@@ -438,3 +450,49 @@ def rlqr_solve_diag(prob: "DeviceProblem", delta_diag, opts: rlqr_opts, ws: torc
                                            _ptr(ws), ws.numel(), _ptr(x), _ptr(u), _ptr(y),
                                            _ptr(pivot_pd), _ptr(rel_resid), _ptr(status),
                                            _stream(stream)), "rlqr_solve_diag")
+
+
+SCAN_CHUNK_CANDIDATES = (148, 296, 444, 592, 888)
+
+
+def rlqr_autotune_scan(prob: "DeviceProblem", opts: rlqr_opts, ws: torch.Tensor, x, u, y,
+                       pivot_pd, stream=None):
+    """Time the scan's chunk counts on `prob` and record the fastest for its
+    shape; returns (chunks, ms of one factor + solve)."""
+    ps = prob.c_struct()
+    c = ctypes.c_int32(0)
+    t = ctypes.c_double(0.0)
+    _check(lib.rlqr_autotune_scan(ctypes.byref(ps), ctypes.byref(opts), _ptr(ws), ws.numel(),
+                                  _ptr(x), _ptr(u), _ptr(y), _ptr(pivot_pd), ctypes.byref(c),
+                                  ctypes.byref(t), _stream(stream)), "rlqr_autotune_scan")
+    return int(c.value), float(t.value)
+
+
+def rlqr_tune_scan_set(N: int, nx: int, nu: int, opts: rlqr_opts, chunks: int):
+    _check(lib.rlqr_tune_scan_set(N, nx, nu, ctypes.byref(opts), chunks), "rlqr_tune_scan_set")
+
+
+def rlqr_tune_reset():
+    _check(lib.rlqr_tune_reset(), "rlqr_tune_reset")
+
+
+RES_ROUTE_WARP, RES_ROUTE_GRID = 1, 2
+
+
+def rlqr_autotune_batched(batch: "DeviceBatch", opts: rlqr_opts, ws: torch.Tensor, status=None,
+                          stream=None):
+    """Time the residual routes of a uniform batch and record the faster one
+    for its shape; returns (route, ms of one rlqr_solve_batched)."""
+    bs = batch.c_struct()
+    r = ctypes.c_int32(0)
+    t = ctypes.c_double(0.0)
+    _check(lib.rlqr_autotune_batched(ctypes.byref(bs), ctypes.byref(opts), _ptr(ws), ws.numel(),
+                                     _ptr(status), ctypes.byref(r), ctypes.byref(t),
+                                     _stream(stream)), "rlqr_autotune_batched")
+    return int(r.value), float(t.value)
+
+
+def rlqr_tune_batched_set(batch: "DeviceBatch", opts: rlqr_opts, route: int):
+    bs = batch.c_struct()
+    _check(lib.rlqr_tune_batched_set(ctypes.byref(bs), ctypes.byref(opts), route),
+           "rlqr_tune_batched_set")

@@ -1,0 +1,91 @@
+"""Scan tiles and their autotuner (rlqr_autotune_scan): the associative
+scan gives the oracle's flags and a backward error <= 1e-9 for every
+candidate chunk count (148 .. 888 chunks, the tiles the autotuner chooses
+among), both precisions; the autotuner returns one of them and the solves
+after it stay exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_16370_b300 import inputs, rlqr
+
+pytestmark = pytest.mark.gpu
+
+
+def _bufs(p):
+    f = dict(dtype=torch.float64, device="cuda")
+    return (torch.zeros(p.N + 1, p.n, **f), torch.zeros(p.N, p.m, **f),
+            torch.zeros(p.N + 1, p.n, **f), torch.zeros(p.N + 1, dtype=torch.uint8, device="cuda"))
+
+
+def _check(p, ref, x, u, y, flags):
+    np.testing.assert_array_equal(flags.cpu().numpy(), ref.flags)
+    r = oracle.residual(p, x.cpu().numpy(), u.cpu().numpy(), y.cpu().numpy()).rel
+    assert r <= 1e-9, r
+
+
+@pytest.mark.parametrize("prec", [rlqr.RLQR_FP64, rlqr.RLQR_MIXED])
+def test_every_chunk_count_is_exact(prec):
+    p = inputs.random_instance(91, 6000, 12, 4, 1e-4)
+    ref = oracle.riccati(p)
+    dp = rlqr.DeviceProblem.from_host(p)
+    opts = rlqr.make_opts(prec, algo=rlqr.RLQR_ALGO_SCAN, tol=1e-9, max_refine=4)
+    ws = rlqr.alloc_workspace(rlqr.rlqr_workspace_bytes(p.N, p.n, p.m, opts))
+    x, u, y, flags = _bufs(p)
+    try:
+        for chunks in rlqr.SCAN_CHUNK_CANDIDATES + (37,):
+            rlqr.rlqr_tune_scan_set(p.N, p.n, p.m, opts, chunks)
+            rlqr.rlqr_factor(dp, opts, ws, flags)
+            rlqr.rlqr_solve(dp, opts, ws, x, u, y)
+            torch.cuda.synchronize()
+            _check(p, ref, x, u, y, flags)
+    finally:
+        rlqr.rlqr_tune_reset()
+
+
+def test_autotuner_choice_and_solves_after_it():
+    p = inputs.random_instance(92, 8192, 12, 4, 1e-4)
+    ref = oracle.riccati(p)
+    dp = rlqr.DeviceProblem.from_host(p)
+    opts = rlqr.make_opts(rlqr.RLQR_MIXED, algo=rlqr.RLQR_ALGO_SCAN, tol=1e-9, max_refine=4)
+    ws = rlqr.alloc_workspace(rlqr.rlqr_workspace_bytes(p.N, p.n, p.m, opts))
+    x, u, y, flags = _bufs(p)
+    try:
+        chunks, ms = rlqr.rlqr_autotune_scan(dp, opts, ws, x, u, y, flags)
+        assert chunks in rlqr.SCAN_CHUNK_CANDIDATES and ms > 0
+        x.zero_()
+        rlqr.rlqr_factor(dp, opts, ws, flags)
+        rlqr.rlqr_solve(dp, opts, ws, x, u, y)
+        torch.cuda.synchronize()
+        _check(p, ref, x, u, y, flags)
+        # a shape the scan does not take: rejected before any work
+        q = inputs.random_instance(93, 64, 5, 2, 1e-4)
+        with pytest.raises(rlqr.RlqrError):
+            rlqr.rlqr_autotune_scan(rlqr.DeviceProblem.from_host(q), opts, ws, *_bufs(q))
+    finally:
+        rlqr.rlqr_tune_reset()
+
+
+@pytest.mark.parametrize("prec", [rlqr.RLQR_FP64, rlqr.RLQR_MIXED])
+def test_both_batched_residual_routes_are_exact_and_the_tuner_picks_one(prec):
+    from tests.gpu_helpers import REL_TOL
+    probs = [inputs.random_instance(300 + b, 96 + 8 * (b % 5), 12, 4, 1e-3) for b in range(64)]
+    db = rlqr.DeviceBatch.from_problems(probs)
+    opts = rlqr.make_opts(prec, tol=1e-9, max_refine=4)
+    ws = rlqr.alloc_workspace(rlqr.rlqr_batched_workspace_bytes(db, opts))
+    st = torch.zeros(db.count, dtype=torch.int32, device="cuda")
+    refs = [oracle.riccati(p) for p in probs]
+    try:
+        for route in (rlqr.RES_ROUTE_WARP, rlqr.RES_ROUTE_GRID):
+            rlqr.rlqr_tune_batched_set(db, opts, route)
+            rlqr.rlqr_solve_batched(db, opts, ws, st)
+            torch.cuda.synchronize()
+            for b, p in enumerate(probs):
+                x, u, y, f = db.instance_view(b)
+                np.testing.assert_array_equal(f, refs[b].flags)
+                assert oracle.residual(p, x, u, y).rel <= REL_TOL
+        route, ms = rlqr.rlqr_autotune_batched(db, opts, ws, st)
+        assert route in (rlqr.RES_ROUTE_WARP, rlqr.RES_ROUTE_GRID) and ms > 0
+    finally:
+        rlqr.rlqr_tune_reset()
