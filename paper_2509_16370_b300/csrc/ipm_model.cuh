@@ -139,6 +139,16 @@ inline CdpConst<T> cdp_const(const rlqr_cdp_model &md) {
 // from the caller's numbers (TrigReplay) -- the value path of every forward
 // direction of a stage is the same RK4, so its transcendental evaluations are
 // done once per stage.
+// Plain FP64: sin and cos of th1 - th2 from those of th1 and th2 (angle
+// difference identities; absolute error of a few ulps, which the model only
+// multiplies by O(1) terms), saving a third of the FP64 transcendentals.
+__device__ __forceinline__ void sin_cos3(const double &a, const double &b, double *sc) {
+  sin_cos(a, sc[0], sc[1]);
+  sin_cos(b, sc[2], sc[3]);
+  sc[4] = sc[0] * sc[3] - sc[1] * sc[2];
+  sc[5] = sc[1] * sc[3] + sc[0] * sc[2];
+}
+
 struct TrigCompute {
   template <class Num>
   __device__ __forceinline__ void operator()(const Num &a, const Num &b, const Num &d, Num *sc) {
@@ -146,15 +156,17 @@ struct TrigCompute {
     sin_cos(b, sc[2], sc[3]);
     sin_cos(d, sc[4], sc[5]);
   }
+  __device__ __forceinline__ void operator()(const double &a, const double &b, const double &,
+                                             double *sc) {
+    sin_cos3(a, b, sc);
+  }
 };
 
 struct TrigRecord {
   double *rec;  // 6 values per right-hand side, appended
-  __device__ __forceinline__ void operator()(const double &a, const double &b, const double &d,
+  __device__ __forceinline__ void operator()(const double &a, const double &b, const double &,
                                              double *sc) {
-    sin_cos(a, sc[0], sc[1]);
-    sin_cos(b, sc[2], sc[3]);
-    sin_cos(d, sc[4], sc[5]);
+    sin_cos3(a, b, sc);
 #pragma unroll
     for (int j = 0; j < 6; ++j) rec[j] = sc[j];
     rec += 6;
