@@ -382,6 +382,7 @@ __global__ void __launch_bounds__(kThreads)
     double g[4], Dg[4], rz[4];
     const double u = i < N ? U[i] : 0.0;
     ineq(md, i, N, X[i * 6], u, g);
+    double sprod = 1.0;  // the stage's barrier term as one log of the slack product
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const bool on = i < N || k >= 2;
@@ -390,9 +391,11 @@ __global__ void __launch_bounds__(kThreads)
       rz[k] = on ? g[k] + mun / z : 0.0;
       if (on) {
         const double gs = g[k] + s;
-        macc += -mun * log(s) + z * gs + 0.5 * eta * gs * gs;
+        sprod *= s;
+        macc += z * gs + 0.5 * eta * gs * gs;
       }
     }
+    macc -= mun * log(sprod);
     double cst = 0.0;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
@@ -597,12 +600,15 @@ __global__ void __launch_bounds__(kThreads)
       acc += 0.5 * cst;
       double g[4];
       ineq(md, i, N, xt[0], ut, g);
+      double sprod = 1.0;  // one log of the slack product per stage
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         if (i == N && kk < 2) continue;
         const double st = S[i * 4 + kk] + alpha * dS[i * 4 + kk], gs = g[kk] + st;
-        acc += -mu * log(st) + Z[i * 4 + kk] * gs + 0.5 * eta * gs * gs;
+        sprod *= st;
+        acc += Z[i * 4 + kk] * gs + 0.5 * eta * gs * gs;
       }
+      acc -= mu * log(sprod);
     }
     acc = block_sum(acc, sh);
     if (acc <= A0 + a.op.armijo * alpha * slope + allow) break;
