@@ -232,7 +232,20 @@ def cpu_baseline(bh, min_seconds=10.0):
     stages = bh.count * bh.N * reps
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": stages / dt, "unit": "stage-solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"{reps} x full batch ({bh.count} instances x N={bh.N}), {dt:.1f} s"}
+            "sample": f"{reps} x full batch ({bh.count} instances x N={bh.N}), {dt:.1f} s",
+            "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (/proc/cpuinfo), or "unknown"."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def run_reference(args):
