@@ -87,7 +87,7 @@ def make_ipm_opts(hessian=RLQR_IPM_HESS_EXACT_FP32, lqr_prec=RLQR_MIXED, **kw) -
     d = dict(max_iter=300, tol=1e-6, eta=1e3, mu0=0.1, mu_min=1e-8, kappa_mu=10.0, tau=0.995,
              armijo=1e-4, ls_steps=12, rho_first=1e-4, rho_grow=8.0, rho_shrink=3.0,
              rho_min=1e-8, rho_max=1e8, kappa_sigma=1e10, s_min=1e-2, hessian=hessian,
-             lqr_prec=lqr_prec, lqr_max_refine=4, lqr_tol=1e-9)
+             lqr_prec=lqr_prec, lqr_max_refine=2, lqr_tol=1e-9)
     d.update(kw)
     o = rlqr_ipm_opts()
     for k, v in d.items():
