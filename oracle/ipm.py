@@ -52,10 +52,11 @@ Constants the paper leaves open (this build's choices, the same on the GPU):
   none passes), with an allowance of 10 eps |A| for rounding; y takes the
   primal step, z the smaller of its own fraction-to-boundary step and the
   primal step, then z is kept in [mu / (kappa s), kappa mu / s] with
-  kappa = 1e10; rho (the inertia correction, as in IPOPT): every iteration
-  first factors with rho = 0; on a certificate failure it restarts from a
-  third of the last successful shift (1e-4 if none, at least 1e-8) and grows
-  x8 until every pivot is PD (failure above 1e8); convergence when
+  kappa = 1e10; rho (the inertia correction): every iteration first factors
+  with a third of the last successful shift (0 if that was 0 or the third
+  is below 1e-8); on a certificate failure a zero shift becomes 1e-4 (1e-8
+  after a nonzero last shift) and a nonzero one grows x8, until every pivot
+  is PD (failure above 1e8); convergence when
   max(||grad_x L||_inf, ||c||_inf, ||g + s||_inf, ||s z||_inf) <= 1e-6 (the
   benchmark tolerance of Section "Benchmarks"), at most 300 iterations;
   initial point: the rollout of the given controls (zeros for a cold start)
@@ -477,10 +478,12 @@ def iterate(md: Model, op: Options, st: State) -> State:
     if lin.err_mu <= op.kappa_mu * st.mu:
         st.mu = max(op.mu_min, min(0.2 * st.mu, st.mu ** 1.5))
     st.iters += 1
-    # inertia correction: rho = 0 first; on a certificate failure the shift
-    # restarts from a third of the last successful one (rho_first if none)
-    # and grows x8 until every pivot is PD
-    rho = 0.0
+    # inertia correction: the first try is a third of the last shift that
+    # gave the correct inertia (0 if that was 0 or the third is below
+    # rho_min); on a certificate failure a zero shift becomes rho_first (or
+    # rho_min after a nonzero last shift) and a nonzero one grows x8, until
+    # every pivot is PD
+    rho = st.rho / op.rho_shrink if st.rho / op.rho_shrink > op.rho_min else 0.0
     while True:
         res, prob, dX, dU, dS, dY, dZ, Gdx = newton_lqr(md, op, st, lin, rho)
         st.factorizations += 1
@@ -494,8 +497,7 @@ def iterate(md: Model, op: Options, st: State) -> State:
             st.status = 3
             st.history.append(dict(it=st.iters, mu=st.mu, rho=rho, err0=lin.err0, alpha=0.0))
             return st
-    if rho > 0.0:
-        st.rho = rho
+    st.rho = rho
     rec = dict(it=st.iters, mu=st.mu, rho=rho, err0=lin.err0, alpha=0.0, trials=0)
     st.history.append(rec)
     m = lin.mask

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kThreads)
     k_ipm_lin(Args a, CdpConst<double> kd, CdpConst<HT> kh) {
   __shared__ double sh[kThreads / 32];
   __shared__ int go;
-  __shared__ double mu_s;
+  __shared__ double mu_s, rho_s;
   const int b = blockIdx.x;
   if (a.status[b] != 0) return;
   const int N = a.N;
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(kThreads)
   if (threadIdx.x == 0) {
     const double err0 = fmax(m_base, m_sz), errmu = fmax(m_base, m_szmu);
     a.kkt[b] = err0;
-    double mun = mu;
+    double mun = mu, rho0 = 0.0;
     int g = 0;
     if (err0 <= a.op.tol) {
       a.status[b] = 1;
@@ -366,15 +366,20 @@ __global__ void __launch_bounds__(kThreads)
       if (errmu <= a.op.kappa_mu * mu) mun = fmax(a.op.mu_min, fmin(0.2 * mu, pow(mu, 1.5)));
       a.mu[b] = mun;
       a.iters[b] += 1;
-      a.rho_try[b] = 0.0;
+      // first inertia shift: a third of the last one that gave the correct
+      // inertia, 0 if that was 0 or the third is below rho_min
+      const double r3 = a.rho[b] / a.op.rho_shrink;
+      rho0 = r3 > a.op.rho_min ? r3 : 0.0;
+      a.rho_try[b] = rho0;
       g = 1;
     }
     go = g;
     mu_s = mun;
+    rho_s = rho0;
   }
   __syncthreads();
   if (!go) return;
-  const double mun = mu_s, eta = a.op.eta, ieta = 1.0 / a.op.eta;
+  const double mun = mu_s, eta = a.op.eta, ieta = 1.0 / a.op.eta, rho0 = rho_s;
 
   // barrier terms of the reduced system and the merit at the current point
   double macc = 0.0;
@@ -402,7 +407,7 @@ __global__ void __launch_bounds__(kThreads)
       const double w = i < N ? md.wx[j] : md.wf[j];
       const double d = X[i * 6 + j] - xg[j];
       cst += w * d * d;
-      Q[i * 36 + j * 6 + j] += w;
+      Q[i * 36 + j * 6 + j] += w + rho0;
       const double cj = c[i * 6 + j];
       macc += Y[i * 6 + j] * cj + 0.5 * eta * cj * cj;
     }
@@ -410,7 +415,7 @@ __global__ void __launch_bounds__(kThreads)
     q[i * 6] += Dg[2] * rz[2] - Dg[3] * rz[3];
     if (i < N) {
       cst += md.wu * u * u;
-      R[i * 4] += md.wu + Dg[0] + Dg[1];
+      R[i * 4] += md.wu + rho0 + Dg[0] + Dg[1];
       r[i * kNu] += Dg[0] * rz[0] - Dg[1] * rz[1];
     }
     macc += 0.5 * cst;
@@ -633,7 +638,7 @@ __global__ void __launch_bounds__(kThreads)
   }
   if (threadIdx.x == 0) {
     a.alpha[b] = alpha;
-    if (a.rho_try[b] > 0.0) a.rho[b] = a.rho_try[b];
+    a.rho[b] = a.rho_try[b];  // the shift that gave the correct inertia (may be 0)
   }
 }
 

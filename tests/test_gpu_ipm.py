@@ -141,7 +141,7 @@ def test_iterations_match_the_oracle_one_at_a_time(N):
 def test_whole_solves_match_the_oracle():
     """Instances the oracle solves to the tolerance: the same outcome and
     iteration count, and the oracle's KKT error at the GPU's final point."""
-    bs = [0, 5, 28]
+    bs = [0, 5, 32]
     model, opts, st, ws, dx0, dxg, x0, xg = _setup(bs)
     n_it = G.rlqr_ipm_solve(model, opts, dx0, dxg, st, ws)
     torch.cuda.synchronize()
