@@ -163,6 +163,15 @@ def kernel_models(n, m, stages):
     }
 
 
+def scan_flops_per_stage(n, m):
+    """Algorithmic FLOPs per stage of the scan kernels (the build's counts of
+    the paper's formulas): the chunk fold does one combination per stage
+    (elimination of I + C P, 2n^3/3, two-sided solves 4n^3, five n x n
+    products 10n^3); a finalize pass is one step of the recursion."""
+    comb = 2.0 / 3.0 * n ** 3 + 4.0 * n ** 3 + 10.0 * n ** 3
+    return {"k_scan_reduce": comb, "k_scan_finalize": seq_flops_per_stage(n, m)}
+
+
 def seq_flops_per_stage(n, m):
     """Algorithmic FLOPs of one stage of the sequential recursion with
     symmetry exploited: 16/3 n^3 + 5 n^2 m + 3 n m^2 + 1/3 m^3."""
@@ -233,7 +242,8 @@ def cpu_baseline(bh, min_seconds=10.0):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": stages / dt, "unit": "stage-solves/s", "cores": cores, "kind": "oracle",
             "sample": f"{reps} x full batch ({bh.count} instances x N={bh.N}), {dt:.1f} s",
-            "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+            "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "build": "gcc " + " ".join(oracle.CFLAGS)}
 
 
 def cpu_model() -> str:
@@ -295,12 +305,18 @@ def run_profile_case(args):
 
 
 def run_latency(args):
-    """One JSON line for the small single instance (n=4, m=2, N=64): the
-    latency of rlqr_factor + rlqr_solve per call, launched one call after
-    another and replayed from a CUDA graph of the same calls, FP64 and mixed
-    (with refinement).  The configuration is bound by launch latency, not by
-    a pipe or HBM, so no roofline fraction is given."""
+    print(json.dumps(measure_latency(args)), flush=True)
+
+
+def measure_latency(args):
+    """The small single instance (n=4, m=2, N=64): the latency of
+    rlqr_factor + rlqr_solve per call, launched one call after another and
+    replayed from a CUDA graph of the same calls, FP64 and mixed (with
+    refinement).  The configuration is bound by launch latency, not by a pipe
+    or HBM, so no roofline fraction is given.  CPU baseline: the oracle's
+    recursion on the same instance, one core."""
     import torch
+    import oracle
     from paper_2509_16370_b300 import inputs, rlqr
     p = inputs.workload1()
     dp = rlqr.DeviceProblem.from_host(p)
@@ -351,12 +367,27 @@ def run_latency(args):
         out[name] = {"eager_us_per_call": round(eager_us, 2), "graph_us_per_call": round(graph_us, 2),
                      "rel_resid": float(rel.item())}
     best = min(out, key=lambda k: out[k]["graph_us_per_call"])
+    oracle.riccati(p)
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < 1.0:
+        oracle.riccati(p)
+        reps += 1
+    cpu_s = (time.perf_counter() - t0) / reps
+    mixed_us = min(out["mixed_seq"]["graph_us_per_call"], out["mixed_scan"]["graph_us_per_call"])
     line = {"metric": "latency of one factor + solve (n=4, m=2, N=64)",
             "value": out[best]["graph_us_per_call"], "unit": "us", "higher_is_better": False,
             "n_gpus": 1, "steps": max(args.steps, 20), "warmup": args.warmup, "data": "synthetic",
             "config": {"workload": "single instance n_x=4, n_u=2, N=64, delta=1e-6", "best": best},
+            "stage_solves_per_s": {"mixed": N / (mixed_us * 1e-6),
+                                   "fp64": N / (min(out["fp64_seq"]["graph_us_per_call"],
+                                                    out["fp64_scan"]["graph_us_per_call"]) * 1e-6)},
+            "roofline": None,
+            "roofline_note": "launch-latency bound: 37 KB of data, a chain of 64 stages",
+            "cpu_baseline": {"value": N / cpu_s, "unit": "stage-solves/s", "cores": 1,
+                             "kind": "oracle", "sample": f"{reps} x the instance, 1 s",
+                             "us_per_call": round(cpu_s * 1e6, 2)},
             **out}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_cross(args):
@@ -650,9 +681,15 @@ def run_diag(args):
 
 
 def run_long_horizon(args):
-    """One JSON line for the long-horizon instance (stage-solves/s of factor +
-    solve + refinement; SCAN mixed vs SEQ FP64 on the GPU)."""
+    print(json.dumps(measure_long_horizon(args)), flush=True)
+
+
+def measure_long_horizon(args, fp64_reps=1, fp64_warmup=1):
+    """The long-horizon instance (stage-solves/s of factor + solve +
+    refinement; SCAN mixed vs SEQ FP64 on the GPU).  CPU baseline: the
+    oracle's recursion on the first 4096 stages (one core)."""
     import torch
+    import oracle
     from paper_2509_16370_b300 import inputs, rlqr
     p = inputs.workload3()
     dp = rlqr.DeviceProblem.from_host(p)
@@ -707,9 +744,34 @@ def run_long_horizon(args):
     report = rlqr.rlqr_instrument_report()
     rlqr.rlqr_instrument(False)
     rel = float(bufs["rel"].item())
+    flags_gpu = bufs["flags"].cpu().numpy()
     step64, bufs64 = make(rlqr.RLQR_FP64, rlqr.RLQR_ALGO_SEQ)
-    ms64 = timed(step64, 1, 1)
+    ms64 = timed(step64, fp64_reps, fp64_warmup)
+    rel64 = None
     value = N / (ms / 1e3)
+    # CPU baseline: the oracle on a bounded prefix of the horizon
+    S = 4096
+    sub = inputs.Problem(S, n, m, p.Q[:S + 1], p.M[:S], p.R[:S], p.q[:S + 1], p.r[:S], p.A[:S],
+                         p.B[:S], p.c[:S + 1], p.delta)
+    t0 = time.perf_counter()
+    oracle.riccati(sub)
+    cpu_s = time.perf_counter() - t0
+    # roofline of the dominant kernel against the measured FP32 FMA rate (the
+    # scan's combine and finalize products run on the FP32 pipes)
+    pipes = rlqr.rlqr_measure_pipes()
+    dom = max(report.items(), key=lambda kv: kv[1][1]) if report else None
+    roof = None
+    if dom is not None:
+        name, (cnt, tot) = dom
+        flops = scan_flops_per_stage(n, m).get(name)
+        if flops:
+            achieved = flops * N / (tot / cnt / 1e3) / 1e12
+            roof = {"kernel": name, "bound": "fp32", "achieved": round(achieved, 3),
+                    "peak": round(pipes["fp32x2_tflops"], 2), "unit": "TFLOP/s",
+                    "frac": round(achieved / pipes["fp32x2_tflops"], 4),
+                    "peak_source": "measured FP32 FMA rate (rlqr_measure_pipes)",
+                    "flops_per_stage": flops, "launch_ms": round(tot / cnt, 4),
+                    "share": round(tot / sum(v[1] for v in report.values()), 3), "traffic": None}
     line = {"metric": METRIC, "value": value, "unit": "stage-solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -723,10 +785,14 @@ def run_long_horizon(args):
             "accuracy": {"rel_resid": rel, "all_le_tol": rel <= TOL,
                          "iters": int(bufs["it"].item()), "status": int(bufs["st"].item())},
             "fp64_plain_seq": {"value": N / (ms64 / 1e3), "ms_per_step": ms64,
-                               "rel_resid": None},
+                               "rel_resid": float(bufs64["rel"].item())},
             "speedup_vs_fp64_plain": ms64 / ms,
+            "roofline": roof,
+            "cpu_baseline": {"value": S / cpu_s, "unit": "stage-solves/s", "cores": 1,
+                             "kind": "oracle", "sample": f"the first {S} stages, {cpu_s:.2f} s"},
+            "flags_all_pd": bool((flags_gpu == 3).all()),
             "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def _ragged_instance(arg):
@@ -736,19 +802,34 @@ def _ragged_instance(arg):
 
 
 def run_ragged(args):
-    """One JSON line for the first K instances of the ragged batch (N in
-    32..2048, n in {6, 12, 24, 48}, m = n/3): rlqr_solve_batched mixed vs
-    plain FP64.  Instances are generated by a process pool (spawn)."""
+    print(json.dumps(measure_ragged(args, args.ragged, args.ragged_n)), flush=True)
+
+
+def measure_ragged(args, count, only_n=0):
+    """The first `count` instances of the ragged batch (N in 32..2048, n in
+    {6, 12, 24, 48}, m = n/3): rlqr_solve_batched mixed vs plain FP64.
+    Instances are generated by a process pool (spawn).  CPU baseline: the
+    oracle's recursion on the batch's instances in order, one core, about
+    5 s."""
     import multiprocessing as mp
     import torch
+    import oracle
     from paper_2509_16370_b300 import inputs, rlqr
-    items = list(enumerate(inputs.workload4_dims(4096)[:args.ragged]))
-    if args.ragged_n:  # one size class of that sample
-        items = [(b, d) for b, d in items if d[1] == args.ragged_n]
+    items = list(enumerate(inputs.workload4_dims(4096)[:count]))
+    if only_n:  # one size class of that sample
+        items = [(b, d) for b, d in items if d[1] == only_n]
     dims = [d for _, d in items]
     with mp.get_context("spawn").Pool(min(32, os.cpu_count() or 1)) as pool:
         probs = pool.map(_ragged_instance, items, chunksize=4)
     db = rlqr.DeviceBatch.from_problems(probs)
+    # CPU baseline sample: instances in batch order until ~5 s of oracle time
+    cpu_stages, t0 = 0, time.perf_counter()
+    for pb in probs:
+        oracle.riccati(pb)
+        cpu_stages += pb.N
+        if time.perf_counter() - t0 >= 5.0:
+            break
+    cpu_s = time.perf_counter() - t0
     del probs  # the batch is on the device; at full size the host copy is ~76 GB
     stages = sum(N for N, _, _ in dims)
     data_gb = sum(8 * ((N + 1) * n * n + N * (2 * n * m + m * m + n * n) + (N + 1) * n * 2 + N * m)
@@ -782,22 +863,36 @@ def run_ragged(args):
     with ClockSampler(0) as clk:
         ms, report, acc = timed(rlqr.RLQR_MIXED, args.steps, args.warmup, True)
     ms64, _, acc64 = timed(rlqr.RLQR_FP64, max(1, args.steps // 4), 1)
+    peaks = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    alg_bytes = sum(N * (8 * (2 * n * n + 2 * n * m + m * m + 2 * n + m) + 8 * (2 * n + m) + 1)
+                    for N, n, m in dims)
+    achieved = alg_bytes / (ms / 1e3) / 1e9
     line = {"metric": METRIC, "value": stages / (ms / 1e3), "unit": "stage-solves/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64 (FP32 sweep; FP64 certificate, residual, correction)",
             "data": "synthetic",
-            "config": {"workload": (f"the n={args.ragged_n} instances ({B}) of " if args.ragged_n
+            "config": {"workload": (f"the n={only_n} instances ({B}) of " if only_n
                                     else f"{B} instances: ") +
-                                   f"the first {args.ragged} of the ragged batch of 4096 "
+                                   f"the first {count} of the ragged batch of 4096 "
                                    "(N in 32..2048, n in {6,12,24,48}, m = n/3, barrier-scaled "
                                    "diagonals)", "instances": B, "stages": stages,
                        "data_gb": round(data_gb, 2)},
             "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in report.items()},
+            "roofline": {"kernel": "whole solve (size classes run concurrently)", "bound": "hbm",
+                         "achieved": round(achieved, 2), "peak": hbm,
+                         "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                         "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                         "algorithmic_bytes": alg_bytes},
             "accuracy": acc,
             "fp64_plain": {"value": stages / (ms64 / 1e3), "ms_per_step": ms64, **acc64},
-            "speedup_vs_fp64_plain": ms64 / ms, "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+            "speedup_vs_fp64_plain": ms64 / ms,
+            "cpu_baseline": {"value": cpu_stages / cpu_s, "unit": "stage-solves/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": f"{cpu_stages} stages of the first instances, {cpu_s:.1f} s"},
+            "clocks": clk.summary()}
+    return line
 
 
 def run_ours(args):
@@ -928,6 +1023,23 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(bh, args.cpu_seconds)
+    if world == 1 and not args.no_extras:
+        # the other configurations of the metric, each with its own roofline
+        # and CPU baseline (single GPU; the headline stays the batch above)
+        del db, ws, host
+        torch.cuda.empty_cache()
+        extras = {}
+        few = argparse.Namespace(**{**vars(args), "steps": 5, "warmup": 3})
+        lat = argparse.Namespace(**{**vars(args), "steps": 50, "warmup": 5})
+        for key, fn in (("latency", lambda: measure_latency(lat)),
+                        ("long_horizon", lambda: measure_long_horizon(few, fp64_warmup=0)),
+                        ("ragged", lambda: measure_ragged(few, 512))):
+            try:
+                extras[key] = fn()
+            except Exception as exc:  # reported, never hidden
+                extras[key] = {"error": f"{type(exc).__name__}: {exc}"}
+            torch.cuda.empty_cache()
+        line["configs"] = extras
     print(json.dumps(line), flush=True)
 
 
@@ -942,6 +1054,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other configurations (small instance, long horizon, ragged)")
     ap.add_argument("--profile-instances", type=int, default=0,
                     help="profiling case: the mixed solve on the first K instances only")
     ap.add_argument("--autotune", action="store_true",

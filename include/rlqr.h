@@ -288,13 +288,16 @@ rlqr_status rlqr_solve_diag(const rlqr_problem *prob, const double *delta_diag,
  * every GPU that loads the library holds it until the process exits. */
 #define RLQR_NOALLOC_SCRATCH_BYTES (8u << 20)
 
-/* Factor + solve one instance (the same kernels as rlqr_factor and
- * rlqr_solve, fused) without any workspace argument and without allocating:
- * for callers that cannot call cudaMalloc -- e.g. a control loop with a fixed
- * memory budget that forbids allocation after start-up, or code running
- * inside another runtime that owns the device allocator.  Scratch is the
- * library's static device array (RLQR_NOALLOC_SCRATCH_BYTES); an instance
- * whose rlqr_workspace_bytes(N, nx, nu, opts) exceeds it is rejected with
+/* Factor + solve one instance with the sequential recursion (the kernels
+ * rlqr_factor and rlqr_solve run with algo RLQR_ALGO_SEQ, the solve fused
+ * with the factorization) without any workspace argument and without
+ * allocating: for callers that cannot call cudaMalloc -- e.g. a control loop
+ * with a fixed memory budget that forbids allocation after start-up, or code
+ * running inside another runtime that owns the device allocator.  AUTO runs
+ * the sequential recursion; RLQR_ALGO_SCAN is refused with RLQR_ERR_ARG.
+ * Scratch is the library's static device array (RLQR_NOALLOC_SCRATCH_BYTES);
+ * an instance whose sequential workspace (rlqr_workspace_bytes(N, nx, nu,
+ * opts) with opts->algo = RLQR_ALGO_SEQ) exceeds it is rejected with
  * RLQR_ERR_WORKSPACE before anything runs.  The caller passes inputs (prob)
  * and device outputs x, u, y, pivot_pd (N+1 bytes) and optional device
  * rel_resid / status (1 element each), exactly as for rlqr_solve.
@@ -439,13 +442,22 @@ rlqr_status rlqr_instrument(int enable);
  * (entries beyond max are dropped), or -1 on a CUDA error. */
 int rlqr_instrument_report(int max, const char **names, int64_t *launches, double *ms);
 
+/* Device bytes of the sink buffer rlqr_measure_pipes needs on the current
+ * device (one double per thread of 4 CTAs of 256 threads per SM; 0 on a
+ * CUDA error). */
+size_t rlqr_measure_pipes_bytes(void);
+
 /* Microbenchmarks of the arithmetic pipes on the current device, for the
  * roofline denominators: FP64 FMA, FP32 FMA and packed f32x2 FMA rates in
  * TFLOP/s (2 flops per FMA lane-operation; independent chains over 4 CTAs
- * of 256 threads per SM; best of 5 CUDA-event-timed launches).  Synchronous;
- * allocates and frees a small device buffer (unlike the solver calls).
- * RLQR_ERR_CUDA on any CUDA error. */
-rlqr_status rlqr_measure_pipes(double *fp64_tflops, double *fp32_tflops, double *fp32x2_tflops);
+ * of 256 threads per SM; best of 5 CUDA-event-timed launches).  scratch
+ * (device, >= rlqr_measure_pipes_bytes(), caller-owned, 8-byte aligned)
+ * receives the chains' results so that they are not optimised away; like the
+ * solver calls, this call allocates nothing.  Synchronous on the default
+ * stream.  RLQR_ERR_WORKSPACE for a missing or small buffer, RLQR_ERR_CUDA
+ * on any CUDA error. */
+rlqr_status rlqr_measure_pipes(void *scratch, size_t scratch_bytes, double *fp64_tflops,
+                               double *fp32_tflops, double *fp32x2_tflops);
 
 #ifdef __cplusplus
 }

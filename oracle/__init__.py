@@ -48,19 +48,39 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rlqr_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
-_LIB_PATH = os.path.join(_BUILD, "librlqr_oracle.so")
 
 OK, NOT_PD, ERR_ARG, SINGULAR = 0, 1, 2, 3
 
+# -O3 -march=native for the timed CPU baseline; -ffp-contract=off keeps every
+# operation a separately rounded FP64 operation in the source's order (no
+# fused multiply-adds, no reassociation), as in a plain evaluation.
+CFLAGS = ["-O3", "-march=native", "-ffp-contract=off", "-std=c99", "-fPIC", "-shared",
+          "-fopenmp"]
+
+
+def _cpu_tag() -> str:
+    """A tag of the host CPU (model and feature flags): -march=native code is
+    built per CPU, so a library built on another machine is never loaded."""
+    import hashlib
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = [ln for ln in f if ln.startswith(("model name", "flags"))][:2]
+    except OSError:
+        info = []
+    return hashlib.sha1("".join(info).encode()).hexdigest()[:12]
+
+
+_LIB_PATH = os.path.join(_BUILD, f"librlqr_oracle.{_cpu_tag()}.so")
+
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle with gcc (plain -O2, OpenMP over instances)."""
+    """Compile the C oracle with gcc (CFLAGS, OpenMP over instances)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc"] + CFLAGS + ["-o", tmp, _SRC, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

@@ -86,6 +86,29 @@ def loss_and_grad(p, x, t, n_out, width, rounding=True):
     return loss, pack(g, n_out, width)
 
 
+def abs_scales(p, x, t, n_out, width):
+    """Per-element magnitudes for element-wise comparisons: for the output and
+    every gradient entry, the sum of the absolute values of the terms that
+    form it (the same chain rule as loss_and_grad with |.| on every factor,
+    no rounding).  An FP32-accumulated value agrees with its FP64 oracle to a
+    few units of roundoff times this scale; BF16 storage of an intermediate
+    adds about 2^-8 times it."""
+    y, c = forward(p, x, n_out, width, rounding=False)
+    P = {k: np.abs(v) for k, v in c["P"].items()}
+    a0, h1, h2 = np.abs(c["a0"]), np.abs(c["h1"]), np.abs(c["h2"])
+    rows = x.shape[0]
+    ys = h2 @ P["W3"].T + P["b3"]
+    npad = c["y"].shape[1]
+    dy = np.zeros((rows, npad))
+    dy[:, :n_out] = 2.0 * (np.abs(y) + np.abs(t)) / (rows * n_out)
+    g = {"W3": dy.T @ h2, "b3": dy.sum(axis=0)}
+    dz2 = (dy @ P["W3"]) * (c["h2"] > 0)
+    g["W2"], g["b2"] = dz2.T @ h1, dz2.sum(axis=0)
+    dz1 = (dz2 @ P["W2"]) * (c["h1"] > 0)
+    g["W1"], g["b1"] = dz1.T @ a0, dz1.sum(axis=0)
+    return ys[:, :n_out], pack(g, n_out, width)
+
+
 def adam(p, m, v, g, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     """One bias-corrected Adam step (Kingma and Ba, 2015); returns new p, m, v."""
     m = b1 * m + (1 - b1) * g

@@ -29,6 +29,11 @@ struct InstState {
   int32_t iters;         // refinement passes done
   int32_t converged;     // rel <= tol
   int32_t r_singular;    // scan path: some R_i had a zero or non-finite pivot
+  int32_t escalated;     // mixed path: a pivot decision lacked its margin, so the
+                         // flags were (or are to be) re-decided by the FP64 recursion
+  double upd;      // mixed path: bound on the rounding errors that the residual
+                   // updates of the refinement passes left in res (absolute)
+  double dzmax;    // scan path: max |dz| of the current refinement pass
 };
 
 // Byte offsets of the arrays of one instance's workspace.  `tsize` is the
@@ -49,8 +54,8 @@ struct WsLayout {
   size_t Qf;     // N n n (as given; readers take the upper triangle)
   size_t Mf;     // N n m
   size_t Rf;     // N m m (as given; readers take the upper triangle)
-  // mixed path, compile-time CTA sweep: state pivots whose FP32 Gershgorin
-  // proof failed are certified afterwards in FP64 from the stored FP32 P_i
+  // mixed path, compile-time CTA and tableau sweeps: state pivots whose FP32
+  // Gershgorin proof failed are certified afterwards from the stored FP32 P_i
   size_t Pc;     // (N+1) n n FP32 P_i of the pending stages
   size_t pend;   // (N+1) bytes: 1 = bit0 of flags[i] still to decide
   size_t total;
@@ -60,6 +65,18 @@ struct WsLayout {
 __host__ __device__ constexpr bool seqx_size(int n, int m) {
   return (n == 24 && m == 8) || (n == 32 && m == 8) || (n == 48 && m == 16);
 }
+
+// (n, m) of the FP32 tableau warp sweep (tab32.cuh)
+__host__ __device__ constexpr bool tab_size(int n, int m) {
+  return ((n == 4 || n == 6) && (m == 1 || m == 2)) || (n == 12 && (m == 3 || m == 4));
+}
+
+// Margin of the mixed path's pivot certificate: a decision taken from an
+// FP32-computed pivot matrix X is kept only when X - tau D (PD claims) or
+// X + tau D (indefinite claims) provably has the same inertia, D = |diag X|
+// (relative to the Jacobi-scaled matrix); otherwise the FP64 recursion
+// decides.  2^-15 ~ 3.1e-5, about 500 times the FP32 unit roundoff.
+constexpr float kMarginTau = 0x1p-15f;
 
 __host__ __device__ inline WsLayout ws_layout(int N, int n, int m, int tsize) {
   WsLayout L;
@@ -91,7 +108,7 @@ __host__ __device__ inline WsLayout ws_layout(int N, int n, int m, int tsize) {
   o = align_up(o + (size_t)N * n * m * ts);
   L.Rf = o;
   o = align_up(o + (size_t)N * m * m * ts);
-  const bool cta_sizes = ts != 0 && seqx_size(n, m);
+  const bool cta_sizes = ts != 0 && (seqx_size(n, m) || tab_size(n, m));
   L.Pc = o;
   o = align_up(o + (cta_sizes ? (size_t)(N + 1) * n * n * 4 : 0));
   L.pend = o;
@@ -125,6 +142,12 @@ struct BatchArgs {
   int32_t *iters;
   double tol;
   int max_refine;
+  // residual launches: recompute the residual only for the instances that
+  // have not converged (after a refinement pass whose rounding bound could
+  // not certify convergence)
+  int recheck;
+  // refinement launches: index of the pass (0 = first)
+  int rpass;
 };
 
 // Instance of a launch slot: the identity, or the group's entry of perm.
@@ -302,6 +325,42 @@ __device__ __forceinline__ bool gershgorin_row_pd(float p_ii, float off_ru, floa
   return d >= 0.0f || __fmul_ru(delta_up, -d) < 1.0f;
 }
 
+// Robust Gershgorin row test for S = I + delta P (P in FP32, delta the FP64
+// regularization): with d = P_ii - sum_{j != i} |P_ij| (the sum rounded up),
+// the row's disc of S - tau diag(S) lies in (0, inf) when
+//   (1 + delta d) - tau (1 + delta P_ii) > 0,
+// evaluated with every rounding against the claim (delta_dn <= delta <=
+// delta_up, both FP32).  All rows true proves lambda_min(D^-1/2 S D^-1/2) >
+// tau, D = diag(S).  NaN gives false.
+__device__ __forceinline__ bool gershgorin_row_margin(float p_ii, float off_ru, float delta_dn,
+                                                      float delta_up, float tau) {
+  const float d = __fsub_rd(p_ii, off_ru);
+  const float g = d >= 0.f ? __fadd_rd(1.f, __fmul_rd(delta_dn, d))
+                           : __fsub_rd(1.f, __fmul_ru(delta_up, -d));
+  const float sd = p_ii >= 0.f ? __fadd_ru(1.f, __fmul_ru(delta_up, p_ii))
+                               : __fsub_ru(1.f, __fmul_rd(delta_dn, -p_ii));
+  return __fsub_rd(g, __fmul_ru(tau, sd)) > 0.f;
+}
+
+// Asynchronous global -> shared copies (cp.async): each thread copies its
+// own elements, commits them as a group and later waits until at most N of
+// its groups are still in flight.  A hardware wait, no polling.  The copied
+// bytes are visible to the copying thread after the wait; other threads see
+// them after a barrier that follows that wait.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Working-precision conversion used by the staging helpers.
 template <typename T, typename S>
 __device__ __forceinline__ T to_work(S v) {
@@ -460,12 +519,59 @@ __device__ __forceinline__ float abs_f32_trunc(double v) {
 
 __device__ __forceinline__ bool finite_nonzero(double d) { return isfinite(d) && d != 0.0; }
 
-// Proof in FP32, by one warp, that I + delta P is positive definite (delta >
-// 0; P symmetric FP32, row-major NX x NX, NX <= 64).  Method: the
+// Certificate decision with margin for a symmetric m x m pivot matrix X
+// computed in FP32 (row-major; the entries X[c][i], c <= i, are read), by one
+// thread: unpivoted LDL^T in FP64 of X - tau D and, when that is not PD, of
+// X + tau D, with D = diag(max(|X_jj|, 2^-24 max_j |X_jj|)).
+//   kPdYes: every pivot of X - tau D is positive, so the Jacobi-scaled X has
+//           lambda_min > tau: X and every X + E with E below tau (scaled) are PD;
+//   kPdNo:  a pivot of X + tau D is <= 0, so lambda_min < -tau: robustly not PD;
+//   kPdAmbiguous: neither (the decision is left to the FP64 recursion), also
+//           for non-finite entries.
+enum { kPdNo = 0, kPdYes = 1, kPdAmbiguous = 2 };
+template <int MAXM>
+__device__ __forceinline__ int pd_margin_f32(const float *X, int m, double tau) {
+  double L[MAXM * (MAXM + 1) / 2];
+  double dmax = 0.0;
+  for (int j = 0; j < m; ++j) dmax = fmax(dmax, fabs(widen(__ldcg(X + j * m + j))));
+  const double floor_d = 0x1p-24 * dmax;
+  for (int pass = 0; pass < 2; ++pass) {
+    const double sg = pass == 0 ? -tau : tau;
+    for (int i = 0; i < m; ++i)
+      for (int c = 0; c <= i; ++c) {
+        double v = widen(__ldcg(X + c * m + i));
+        if (c == i) v += sg * fmax(fabs(v), floor_d);
+        L[i * (i + 1) / 2 + c] = v;
+      }
+    bool pos = true;
+    for (int j = 0; j < m; ++j) {
+      const double d = L[j * (j + 1) / 2 + j];
+      if (!isfinite(d)) return kPdAmbiguous;
+      if (!(d > 0.0)) {
+        pos = false;
+        break;
+      }
+      const double rd = 1.0 / d;
+      for (int i = j + 1; i < m; ++i) {
+        const double lij = L[i * (i + 1) / 2 + j] * rd;
+        for (int c = j + 1; c <= i; ++c) L[i * (i + 1) / 2 + c] -= lij * L[c * (c + 1) / 2 + j];
+      }
+    }
+    if (pass == 0 && pos) return kPdYes;
+    if (pass == 1 && !pos) return kPdNo;
+  }
+  return kPdAmbiguous;
+}
+
+// Proof in FP32, by one warp, that I + delta P - tau D is positive definite
+// (D = diag(I + delta P); delta > 0; P symmetric FP32, row-major NX x NX,
+// NX <= 64; tau >= 0 the certificate's margin).  Method: the
 // verification of positive definiteness of S. M. Rump (BIT 46, 2006) applied
 // to A = P + I/delta, which is PD exactly when I + delta P is.  A is scaled
 // as D A D with D the powers of two nearest diag(A)^(-1/2) (exact), its
-// diagonal is lowered by c and the result S is Cholesky-factored (S = R^T R,
+// diagonal entries d_i are lowered by c + tau d_i (the margin: A - tau
+// diag(A) is a positive multiple of I + delta P - tau D) and the result S is
+// Cholesky-factored (S = R^T R,
 // R upper) in FP32 with correctly rounded square roots and divisions.  If
 // that run completes (every pivot finite and positive), the backward error
 // of Cholesky (Demmel; Higham, "Accuracy and Stability of Numerical
@@ -477,7 +583,7 @@ __device__ __forceinline__ bool finite_nonzero(double d) { return isfinite(d) &&
 // triangle's columns l and l + 32; row j of R reaches the other lanes by
 // shuffles.
 template <int NX>
-__device__ __noinline__ int warp_pd_proof_f32(const float *P, double delta) {
+__device__ __noinline__ int warp_pd_proof_f32(const float *P, double delta, float tau) {
   static_assert(NX >= 1 && NX <= 64, "one warp, two columns per lane");
   constexpr int R0 = NX < 32 ? NX : 32;  // rows held for column lane (<= lane)
   constexpr int R1 = NX > 32 ? NX : 1;   // rows held for column lane + 32
@@ -510,7 +616,10 @@ __device__ __noinline__ int warp_pd_proof_f32(const float *P, double delta) {
     const float si = __shfl_sync(FULL, s0, i);
     float v = 0.f;
     if (h0 && i < c0) v = (si * __ldcg(P + i * NX + c0)) * s0;
-    if (h0 && i == c0) v = __fsub_rd(a0 * s0 * s0, c);
+    if (h0 && i == c0) {
+      const float dg = a0 * s0 * s0;  // exact: scaling by powers of two
+      v = __fsub_rd(__fsub_rd(dg, c), __fmul_ru(tau, dg));
+    }
     x0[i] = v;
     bad |= !(fabsf(v) <= 3.0e38f);
   }
@@ -520,7 +629,10 @@ __device__ __noinline__ int warp_pd_proof_f32(const float *P, double delta) {
       const float si = __shfl_sync(FULL, i < 32 ? s0 : s1, i & 31);
       float v = 0.f;
       if (h1 && i < c1) v = (si * __ldcg(P + i * NX + c1)) * s1;
-      if (h1 && i == c1) v = __fsub_rd(a1 * s1 * s1, c);
+      if (h1 && i == c1) {
+        const float dg = a1 * s1 * s1;
+        v = __fsub_rd(__fsub_rd(dg, c), __fmul_ru(tau, dg));
+      }
       x1[i] = v;
       bad |= !(fabsf(v) <= 3.0e38f);
     }

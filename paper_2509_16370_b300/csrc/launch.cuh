@@ -56,6 +56,16 @@ inline cudaError_t set_smem(F *kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Same, and the largest shared-memory carveout of the unified L1 / shared
+// storage, for kernels whose occupancy is set by their shared memory.
+template <typename F>
+inline cudaError_t set_smem_carveout(F *kernel, size_t bytes) {
+  cudaError_t e = set_smem(kernel, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
+}
+
 // Defined in launch_fp32.cu / launch_fp64.cu (explicit instantiations).
 template <typename T, bool SOLVE>
 cudaError_t launch_seq(int n, int m, bool uniform, const BatchArgs &a, cudaStream_t s);

@@ -2,6 +2,8 @@
 // launch_fp64.cu (one translation unit per precision).
 #pragma once
 
+#include <algorithm>
+
 #include "launch.cuh"
 #include "refine.cuh"
 #include "seq.cuh"
@@ -10,6 +12,8 @@
 #include "refine32.cuh"
 #include "residual32.cuh"
 #include "seqx.cuh"
+#include "tab32.cuh"
+#include "refine_tab.cuh"
 
 namespace rlqr {
 
@@ -50,63 +54,6 @@ static cudaError_t launch_solve_impl(const BatchArgs &a, cudaStream_t s) {
   X(32, 8, 256)             \
   X(48, 16, 256)
 
-// One warp per instance for the small sizes (2 n <= 32, 2 m + n + 1 <= 32);
-// the FP32 sweep of even sizes runs the block-pivot kernel of sweep32.cuh.
-template <typename T, int NX, int NU, bool SOLVE>
-static cudaError_t launch_seq_warp(const BatchArgs &a, cudaStream_t s) {
-  const char *name = sizeof(T) == 4 ? (SOLVE ? "k_seq_fp32_solve" : "k_seq_fp32_factor")
-                                    : (SOLVE ? "k_seq_fp64_solve" : "k_seq_fp64_factor");
-  if constexpr (sizeof(T) == 4 && sweep32_fits<NX, NU>()) {
-    auto kern = k_sweep32<NX, NU, SOLVE>;
-    const size_t bytes = sizeof(Sw32<NX, NU>);
-    cudaError_t e = set_smem(kern, bytes);
-    if (e != cudaSuccess) return e;
-    LaunchScope ls(name, s);
-    kern<<<a.count, 32, bytes, s>>>(a);
-    return cudaGetLastError();
-  } else {
-    constexpr int WPC = 1;  // one instance per CTA: spreads the warps evenly over the SMs
-    auto kern = k_seq_warp<T, NX, NU, WPC, SOLVE>;
-    const size_t bytes = sizeof(WarpSmem<T, NX, NU>) * WPC;
-    cudaError_t e = set_smem(kern, bytes);
-    if (e != cudaSuccess) return e;
-    LaunchScope ls(name, s);
-    kern<<<(a.count + WPC - 1) / WPC, 32 * WPC, bytes, s>>>(a);
-    return cudaGetLastError();
-  }
-}
-
-template <typename T, int NX, int NU, bool FROM_RES>
-static cudaError_t launch_solve_warp(const BatchArgs &a, cudaStream_t s) {
-  const char *name =
-      FROM_RES ? "k_solve_refine" : (sizeof(T) == 4 ? "k_solve_fp32" : "k_solve_fp64");
-  if constexpr (sizeof(T) == 4 && FROM_RES && sweep32_fits<NX, NU>()) {
-    // the factor and the FP32 data copies come from k_sweep32
-    auto kern = k_refine32<NX, NU>;
-    const size_t bytes = sizeof(Rf32<NX, NU>);
-    cudaError_t e = set_smem(kern, bytes);
-    if (e != cudaSuccess) return e;
-    LaunchScope ls(name, s);
-    kern<<<a.count, 32, bytes, s>>>(a);
-    return cudaGetLastError();
-  } else {
-    constexpr int WPC = 1;  // one instance per CTA: spreads the warps evenly over the SMs
-    auto kern = k_solve_warp<T, NX, NU, WPC, FROM_RES>;
-    const size_t bytes = sizeof(WarpSmem<T, NX, NU>) * WPC;
-    cudaError_t e = set_smem(kern, bytes);
-    if (e != cudaSuccess) return e;
-    LaunchScope ls(name, s);
-    kern<<<(a.count + WPC - 1) / WPC, 32 * WPC, bytes, s>>>(a);
-    return cudaGetLastError();
-  }
-}
-
-#define RLQR_WARP_SIZES(X) \
-  X(4, 2)                  \
-  X(6, 1)                  \
-  X(6, 2)                  \
-  X(12, 4)
-
 // Certificate of the state pivots the FP32 CTA sweep left undecided: the
 // FP32 proof, then the FP64 decision for what it did not prove.  4 warps per
 // block, about 32 warps per SM over the grid and at least 16 warps per
@@ -123,6 +70,84 @@ cudaError_t launch_seqx_cert(const BatchArgs &a, cudaStream_t s) {
   k64<<<dim3(a.count, gy), 128, bytes, s>>>(a);
   return cudaGetLastError();
 }
+
+// One warp per instance for the small sizes (2 n <= 32, 2 m + n + 1 <= 32);
+// the FP32 sweep of even n and m runs the block-pivot kernel of sweep32.cuh,
+// that of even n and odd m the tableau kernel of tab32.cuh.
+template <typename T, int NX, int NU, bool SOLVE>
+static cudaError_t launch_seq_warp(const BatchArgs &a, cudaStream_t s) {
+  const char *name = sizeof(T) == 4 ? (SOLVE ? "k_seq_fp32_solve" : "k_seq_fp32_factor")
+                                    : (SOLVE ? "k_seq_fp64_solve" : "k_seq_fp64_factor");
+  if constexpr (sizeof(T) == 4 && sweep32_fits<NX, NU>()) {
+    // even n and m: the block-pivot warp sweep of sweep32.cuh (its certificate
+    // is decided in the kernel, with the margin; escalation marks the rest)
+    auto kern = k_sweep32<NX, NU, SOLVE>;
+    const size_t bytes = sizeof(Sw32<NX, NU>);
+    cudaError_t e = set_smem(kern, bytes);
+    if (e != cudaSuccess) return e;
+    LaunchScope ls(name, s);
+    kern<<<a.count, 32, bytes, s>>>(a);
+    return cudaGetLastError();
+  } else if constexpr (sizeof(T) == 4 && tab32_fits<NX, NU>()) {
+    // even n, odd m: tableau sweep (two warps per instance), then the
+    // deferred certificate of the state pivots its Gershgorin test left open
+    auto kern = k_tab32<NX, NU, SOLVE>;
+    const size_t bytes = sizeof(Tb32<NX, NU>);
+    cudaError_t e = set_smem_carveout(kern, bytes);  // 7 CTAs of ~21 KB per SM
+    if (e != cudaSuccess) return e;
+    {
+      LaunchScope ls(name, s);
+      kern<<<a.count, 64, bytes, s>>>(a);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
+    return launch_seqx_cert<NX>(a, s);
+  } else {
+    constexpr int WPC = 1;  // one instance per CTA: spreads the warps evenly over the SMs
+    auto kern = k_seq_warp<T, NX, NU, WPC, SOLVE>;
+    const size_t bytes = sizeof(WarpSmem<T, NX, NU>) * WPC;
+    cudaError_t e = set_smem(kern, bytes);
+    if (e != cudaSuccess) return e;
+    LaunchScope ls(name, s);
+    kern<<<(a.count + WPC - 1) / WPC, 32 * WPC, bytes, s>>>(a);
+    return cudaGetLastError();
+  }
+}
+
+template <typename T, int NX, int NU, bool FROM_RES>
+static cudaError_t launch_solve_warp(const BatchArgs &a, cudaStream_t s) {
+  const char *name =
+      FROM_RES ? "k_solve_refine" : (sizeof(T) == 4 ? "k_solve_fp32" : "k_solve_fp64");
+  if constexpr (sizeof(T) == 4 && FROM_RES && tab32_fits<NX, NU>()) {
+    // the factor and the FP32 data copies come from k_sweep32 or k_tab32
+    auto kern = k_refine_tab<NX, NU>;
+    const size_t bytes = sizeof(Rt32<NX, NU>);
+    cudaError_t e = set_smem_carveout(kern, bytes);
+    if (e != cudaSuccess) return e;
+    LaunchScope ls(name, s);
+    // later passes find most instances converged: fewer, striding blocks
+    const int grid = a.rpass == 0 ? a.count : std::min(a.count, 148 * 4);
+    kern<<<grid, 32, bytes, s>>>(a);
+    return cudaGetLastError();
+  } else {
+    constexpr int WPC = 1;  // one instance per CTA: spreads the warps evenly over the SMs
+    auto kern = k_solve_warp<T, NX, NU, WPC, FROM_RES>;
+    const size_t bytes = sizeof(WarpSmem<T, NX, NU>) * WPC;
+    cudaError_t e = set_smem(kern, bytes);
+    if (e != cudaSuccess) return e;
+    LaunchScope ls(name, s);
+    kern<<<(a.count + WPC - 1) / WPC, 32 * WPC, bytes, s>>>(a);
+    return cudaGetLastError();
+  }
+}
+
+#define RLQR_WARP_SIZES(X) \
+  X(4, 1)                  \
+  X(4, 2)                  \
+  X(6, 1)                  \
+  X(6, 2)                  \
+  X(12, 3)                 \
+  X(12, 4)
 
 template <typename T, bool SOLVE>
 cudaError_t launch_seq(int n, int m, bool uniform, const BatchArgs &a, cudaStream_t s) {
@@ -202,7 +227,8 @@ cudaError_t launch_residual32(int n, int m, bool uniform, const BatchArgs &a, in
         cudaError_t e = set_smem(kern, bytes);                               \
         if (e != cudaSuccess) return e;                                      \
         LaunchScope ls("k_residual_ff", s);                                  \
-        kern<<<a.count, 32 * kResWarps, bytes, s>>>(a, 1, cert_g);           \
+        const int grid = a.recheck ? std::min(a.count, 148 * 4) : a.count;  \
+        kern<<<grid, 32 * kResWarps, bytes, s>>>(a, 1, cert_g);             \
         return cudaGetLastError();                                           \
       }                                                                      \
     }

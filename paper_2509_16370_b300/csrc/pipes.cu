@@ -4,6 +4,7 @@
 // independent FMA chains (enough to cover the pipe latency) over a grid of
 // several CTAs per SM; rate = 2 flops per FMA lane-operation / CUDA-event time.
 #include <cuda_runtime.h>
+#include <cstdint>
 
 #include "common.cuh"
 
@@ -72,17 +73,27 @@ float time_best(F launch, int reps) {
 
 using namespace rlqr;
 
-extern "C" rlqr_status rlqr_measure_pipes(double *fp64_tflops, double *fp32_tflops,
-                                          double *fp32x2_tflops) {
-  if (!fp64_tflops || !fp32_tflops || !fp32x2_tflops) return RLQR_ERR_ARG;
+static int pipe_blocks() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return RLQR_ERR_CUDA;
-  const int threads = 256, blocks = sms * 4;
-  void *buf = nullptr;
-  if (cudaMalloc(&buf, (size_t)blocks * threads * sizeof(double)) != cudaSuccess)
-    return RLQR_ERR_CUDA;
+    return 0;
+  return sms * 4;
+}
+
+extern "C" size_t rlqr_measure_pipes_bytes(void) {
+  return (size_t)pipe_blocks() * 256 * sizeof(double);
+}
+
+extern "C" rlqr_status rlqr_measure_pipes(void *scratch, size_t scratch_bytes, double *fp64_tflops,
+                                          double *fp32_tflops, double *fp32x2_tflops) {
+  if (!fp64_tflops || !fp32_tflops || !fp32x2_tflops) return RLQR_ERR_ARG;
+  const int threads = 256, blocks = pipe_blocks();
+  if (blocks <= 0) return RLQR_ERR_CUDA;
+  void *buf = scratch;
+  if (!buf || scratch_bytes < (size_t)blocks * threads * sizeof(double) ||
+      (reinterpret_cast<uintptr_t>(buf) % sizeof(double)) != 0)
+    return RLQR_ERR_WORKSPACE;
   const double lanes = (double)blocks * threads * kChains;
   const int it64 = 2048, it32 = 32768;
   const float ms64 = time_best([&] {
@@ -94,7 +105,6 @@ extern "C" rlqr_status rlqr_measure_pipes(double *fp64_tflops, double *fp32_tflo
   const float ms2 = time_best([&] {
     k_pipe_fma2<<<blocks, threads>>>((float *)buf, it32, 1.0000001f, 1e-9f);
   }, 5);
-  cudaFree(buf);
   if (ms64 <= 0.f || ms32 <= 0.f || ms2 <= 0.f) return RLQR_ERR_CUDA;
   *fp64_tflops = 2.0 * lanes * it64 / (ms64 * 1e-3) / 1e12;
   *fp32_tflops = 2.0 * lanes * it32 / (ms32 * 1e-3) / 1e12;

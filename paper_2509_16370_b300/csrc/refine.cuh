@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(THREADS) k_solve(BatchArgs a) {
   // ---------------- forward rollout (+ z update and residual update)
   // The FP64 iterate and residual rows of the next stage are prefetched with
   // the stage data, so their read-modify-writes never wait on HBM.
-  unsigned long long rbits = 0, zbits = 0;  // max |.| as order-preserving bit patterns
+  unsigned long long rbits = 0, zbits = 0, dzbits = 0;  // max |.| as order-preserving bit patterns
   double *dsm = reinterpret_cast<double *>(smem_raw + align_up(sizeof(T) * S::kT, 16));
   double *zx = dsm, *zy = dsm + NM, *zq = dsm + 2 * NM, *zc = dsm + 3 * NM;
   double *zu = dsm + 4 * NM, *zr = zu + MM;
@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(THREADS) k_solve(BatchArgs a) {
       I.x[i] = xv;
       I.y[i] = yv;
       zbits = max(zbits, max(abs_bits(xv), abs_bits(yv)));
+      dzbits = max(dzbits, max(abs_bits(widen(dxv)), abs_bits(widen(dyv))));
       double r0 = __ldcg(rc + i) - widen(dxv) - delta64 * widen(dyv);  // (K dz) rows of y_0
       rc[i] = r0;
       rbits = max(rbits, abs_bits(r0));
@@ -295,6 +296,7 @@ __global__ void __launch_bounds__(THREADS) k_solve(BatchArgs a) {
         const double uv = zu[i] + widen(s);
         I.u[(size_t)k * m + i] = uv;
         zbits = max(zbits, abs_bits(uv));
+        dzbits = max(dzbits, abs_bits(widen(s)));
       } else {
         I.u[(size_t)k * m + i] = widen(s);
       }
@@ -327,6 +329,7 @@ __global__ void __launch_bounds__(THREADS) k_solve(BatchArgs a) {
         I.x[o] = xv;
         I.y[o] = yv;
         zbits = max(zbits, max(abs_bits(xv), abs_bits(yv)));
+        dzbits = max(dzbits, max(abs_bits(widen(dxv)), abs_bits(widen(dyv))));
       } else {
         I.x[o] = widen(dxv);
         I.y[o] = widen(dyv);
@@ -400,9 +403,15 @@ __global__ void __launch_bounds__(THREADS) k_solve(BatchArgs a) {
   }
   const double rmax = block_max<THREADS>(bits_to_double(rbits), s_red);
   const double zmax = block_max<THREADS>(bits_to_double(zbits), s_red);
+  const double dzmax = block_max<THREADS>(bits_to_double(dzbits), s_red);
   if (tid == 0) {
+    // the working-precision products of this pass's residual update err by
+    // at most 2 gamma_L ||K||_inf max|dz| per entry (L = 2n + m); the bound
+    // accumulates over passes and is part of the reported backward error
+    const double uw = sizeof(T) == 4 ? 0x1p-24 : 0x1p-53;
+    stp->upd += 2.0 * (2 * n + m) * uw * stp->kmax * dzmax;
     double den = stp->kmax * zmax + stp->bmax;
-    double rel = den > 0.0 ? rmax / den : rmax;
+    double rel = den > 0.0 ? (rmax + stp->upd) / den : rmax + stp->upd;
     stp->rmax = rmax;
     stp->zmax = zmax;
     stp->rel = rel;

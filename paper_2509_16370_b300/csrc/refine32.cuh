@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(32) k_refine32(BatchArgs a) {
   }
 
   // ---------------- forward rollout, FP64 update of z and of the residual
-  unsigned long long rbits = 0, zbits = 0;
+  unsigned long long rbits = 0, zbits = 0, dzbits = 0;
   // per-lane row segments of K dz (lane r < RS); see the header comment
   const float *seg1 = s.zero, *seg2 = s.zero, *seg3 = s.zero;
   double *zp = nullptr, *resp = nullptr;  // this lane's FP64 z and res element at stage 0
@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(32) k_refine32(BatchArgs a) {
     I.x[lane] = xv;
     I.y[lane] = yv;
     zbits = max(zbits, max(abs_bits(xv), abs_bits(yv)));
+    dzbits = max(dzbits, max(abs_bits(widen(dxv)), abs_bits(widen(dyv))));
     const double r0 = __ldcg(rc + lane) - widen(dxv) - delta64 * widen(dyv);
     rc[lane] = r0;
     rbits = max(rbits, abs_bits(r0));
@@ -369,6 +370,7 @@ __global__ void __launch_bounds__(32) k_refine32(BatchArgs a) {
       zp[(size_t)k * zstride] = zv;
       resp[(size_t)k * rstride] = rv;
       zbits = max(zbits, abs_bits(zv));
+      dzbits = max(dzbits, abs_bits(widen(dz)));
       rbits = max(rbits, abs_bits(rv));
     }
     float *t1 = dx; dx = dxn; dxn = t1;
@@ -398,11 +400,15 @@ __global__ void __launch_bounds__(32) k_refine32(BatchArgs a) {
   for (int o = 16; o > 0; o >>= 1) {
     rbits = max(rbits, __shfl_xor_sync(0xffffffffu, rbits, o));
     zbits = max(zbits, __shfl_xor_sync(0xffffffffu, zbits, o));
+    dzbits = max(dzbits, __shfl_xor_sync(0xffffffffu, dzbits, o));
   }
   if (lane == 0) {
     const double rmax = bits_to_double(rbits), zmax = bits_to_double(zbits);
+    // rounding bound of this pass's FP32 residual update, accumulated over
+    // passes and included in the reported backward error
+    stp->upd += 2.0 * RS * 0x1p-24 * stp->kmax * bits_to_double(dzbits);
     const double den = stp->kmax * zmax + stp->bmax;
-    const double rel = den > 0.0 ? rmax / den : rmax;
+    const double rel = den > 0.0 ? (rmax + stp->upd) / den : rmax + stp->upd;
     stp->rmax = rmax;
     stp->zmax = zmax;
     stp->rel = rel;

@@ -55,49 +55,25 @@ __global__ void k_residual(BatchArgs a, int store, double *res_out, double *norm
   unsigned long long rbits = 0, zbits = 0, bbits = 0;
 
   if (cert_g) {
-    // Control-pivot certificate (mixed path): FP64 LDL^T of every stored
-    // G_s, one stage per thread so that the FP64 instructions are lane-packed.
-    // Each thread's lower triangle lives in shared memory, interleaved by
-    // thread.  bit1 of flags[s] is set when G_s is PD.
-    const int tri = m * (m + 1) / 2;
-    const int cap = (int)((residual_warp_bytes(rs_max) * nwarps) / (sizeof(double) * tri));
-    const int ct = min((int)blockDim.x, cap);
-    double *L = reinterpret_cast<double *>(smem_raw);
+    // Control-pivot certificate with margin (mixed path), one stage per
+    // thread (pd_margin_f32): bit1 of flags[s]; a decision without its
+    // margin escalates the instance to the FP64 recursion.
     const float *gG = reinterpret_cast<const float *>(I.ws + I.L.G);
-    int bad = 0, sing = 0;
-    if ((int)threadIdx.x < ct) {
-      for (int s = threadIdx.x; s < N; s += ct) {
-        const float *Gs = gG + (size_t)s * m * m;
-        for (int i = 0; i < m; ++i)
-          for (int c = 0; c <= i; ++c) L[(i * (i + 1) / 2 + c) * ct + threadIdx.x] = (double)Gs[c * m + i];
-        int neg = 0, zs = 0;
-        for (int j = 0; j < m; ++j) {
-          const double d = L[(j * (j + 1) / 2 + j) * ct + threadIdx.x];
-          if (!finite_nonzero(d)) { zs = 1; break; }
-          if (d < 0.0) ++neg;
-          // FP32 reciprocal refined by one Newton step (error ~1e-14 relative)
-          const float df = (float)d;
-          double rd = (double)(1.0f / df);
-          rd = (isfinite(rd) && rd != 0.0) ? rd * (2.0 - d * rd) : 1.0 / d;
-          for (int i = j + 1; i < m; ++i) {
-            const double lij = L[(i * (i + 1) / 2 + j) * ct + threadIdx.x] * rd;
-            for (int c = j + 1; c <= i; ++c)
-              L[(i * (i + 1) / 2 + c) * ct + threadIdx.x] -= lij * L[(c * (c + 1) / 2 + j) * ct + threadIdx.x];
-          }
-        }
-        const uint8_t old = I.flags[s];
-        I.flags[s] = (uint8_t)((old & 1) | ((neg == 0 && !zs) ? 2 : 0));
-        bad |= (neg != 0) | zs;
-        sing |= zs;
-      }
+    int bad = 0, esc = 0;
+    for (int s = threadIdx.x; s < N; s += blockDim.x) {
+      const int dec = pd_margin_f32<16>(gG + (size_t)s * m * m, m, (double)kMarginTau);
+      const uint8_t old = I.flags[s];
+      I.flags[s] = (uint8_t)((old & 1) | (dec == kPdYes ? 2 : 0));
+      bad |= dec == kPdNo;
+      esc |= dec == kPdAmbiguous;
     }
     const int any_bad = __syncthreads_or(bad);
-    const int any_sing = __syncthreads_or(sing);
+    const int any_esc = __syncthreads_or(esc);
     if (threadIdx.x == 0 && !standalone) {
       int32_t ps = I.st->pivot_status;
-      if (any_sing) ps = RLQR_ERR_SINGULAR;
-      else if (any_bad && ps == RLQR_OK) ps = RLQR_NOT_PD;
+      if (any_bad && ps == RLQR_OK) ps = RLQR_NOT_PD;
       I.st->pivot_status = ps;
+      if (any_esc) I.st->escalated = 1;
       if (!do_residual && a.status) a.status[b] = ps;
     }
     __syncthreads();
@@ -235,6 +211,7 @@ __global__ void k_residual(BatchArgs a, int store, double *res_out, double *norm
     st->rmax = rmax;
     st->zmax = zmax;
     st->rel = rel;
+    st->upd = 0.0;  // a residual computed from scratch
     const int32_t conv = (rel <= a.tol) ? 1 : 0;
     st->converged = conv;
     if (a.rel) a.rel[b] = rel;

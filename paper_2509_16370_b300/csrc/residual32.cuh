@@ -119,64 +119,55 @@ __device__ __forceinline__ float2 abs_sum2(const float2 (&r)[L / 2], float2 acc)
 // store: write res into the workspace for the refinement; cert_g: FP64
 // certificate of the stored control pivots (bit1 of the flags).
 template <int NX, int NU>
+__device__ __forceinline__ void res32_instance(const BatchArgs &a, int slot, int store, int cert_g,
+                                               unsigned char *smem_raw);
+
+template <int NX, int NU>
 __global__ void __launch_bounds__(32 * kResWarps) k_res32(BatchArgs a, int store, int cert_g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // one instance per block; recheck launches use fewer blocks than
+  // instances and stride over the slots
+  for (int slot = blockIdx.x; slot < a.count; slot += gridDim.x)
+    res32_instance<NX, NU>(a, slot, store, cert_g, smem_raw);
+}
+
+template <int NX, int NU>
+__device__ __forceinline__ void res32_instance(const BatchArgs &a, int slot, int store, int cert_g,
+                                               unsigned char *smem_raw) {
   constexpr int n = NX, m = NU, nn = n * n, nm = n * m, mmm = m * m;
   constexpr int H2 = n / 2, M2 = m / 2, RS = 2 * n + m;
   using SW = Rs32Warp<NX, NU>;
   constexpr int N4 = SW::N4, M4 = SW::M4;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double s_red[32];
-  const int slot = blockIdx.x;
-  if (slot >= a.count) return;
-  const int b = inst_of(a, slot);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   SW &s = reinterpret_cast<SW *>(smem_raw)[warp];
+  const int b = inst_of(a, slot);
   const Inst I = get_inst(a, b);
+  if (a.recheck && (I.st->converged || I.st->pivot_status == RLQR_ERR_SINGULAR)) return;
   const int N = I.N;
   const double delta = I.delta;
   double *rq = reinterpret_cast<double *>(I.ws + I.L.res);
   double *rr = rq + (size_t)(N + 1) * n;
   double *rc = rr + (size_t)N * m;
 
-  // ---- FP64 certificate of the control pivots, one stage per thread
+  // ---- FP64 certificate of the control pivots with margin, one stage per
+  // thread (pd_margin_f32); a decision without its margin escalates the
+  // instance to the FP64 recursion
   if (cert_g) {
     const float *gG = reinterpret_cast<const float *>(I.ws + I.L.G);
-    int bad = 0, sing = 0;
+    int bad = 0, esc = 0;
     for (int st = threadIdx.x; st < N; st += blockDim.x) {
-      double L[m][m];
-#pragma unroll
-      for (int i = 0; i < m; ++i)
-#pragma unroll
-        for (int c = 0; c <= i; ++c) L[i][c] = widen(__ldcg(gG + (size_t)st * mmm + c * m + i));
-      int neg = 0, zs = 0;
-#pragma unroll
-      for (int j = 0; j < m; ++j) {
-        const double d = L[j][j];
-        if (!finite_nonzero(d)) zs = 1;
-        if (d < 0.0) ++neg;
-        // FP32-seeded reciprocal, one Newton step in FP64 (IEEE quotient
-        // when the seed is out of range)
-        double rd = widen(recip_pivot(f64_to_f32_rz(d)));
-        rd = (isfinite(rd) && rd != 0.0) ? rd * (2.0 - d * rd) : 1.0 / d;
-#pragma unroll
-        for (int i = j + 1; i < m; ++i) {
-          const double lij = L[i][j] * rd;
-#pragma unroll
-          for (int c = j + 1; c <= i; ++c) L[i][c] -= lij * L[c][j];
-        }
-      }
+      const int dec = pd_margin_f32<m>(gG + (size_t)st * mmm, m, (double)kMarginTau);
       const uint8_t old = I.flags[st];
-      I.flags[st] = (uint8_t)((old & 1) | ((neg == 0 && !zs) ? 2 : 0));
-      bad |= (neg != 0) | zs;
-      sing |= zs;
+      I.flags[st] = (uint8_t)((old & 1) | (dec == kPdYes ? 2 : 0));
+      bad |= dec == kPdNo;
+      esc |= dec == kPdAmbiguous;
     }
     const int any_bad = __syncthreads_or(bad);
-    const int any_sing = __syncthreads_or(sing);
+    const int any_esc = __syncthreads_or(esc);
     if (threadIdx.x == 0) {
-      int32_t ps = I.st->pivot_status;
-      if (any_sing) ps = RLQR_ERR_SINGULAR;
-      else if (any_bad && ps == RLQR_OK) ps = RLQR_NOT_PD;
-      I.st->pivot_status = ps;
+      if (any_bad && I.st->pivot_status == RLQR_OK) I.st->pivot_status = RLQR_NOT_PD;
+      if (any_esc) I.st->escalated = 1;
     }
   }
 
@@ -354,6 +345,7 @@ __global__ void __launch_bounds__(32 * kResWarps) k_res32(BatchArgs a, int store
     stp->rmax = rmax;
     stp->zmax = zmax;
     stp->rel = rel;
+    stp->upd = 0.0;  // a residual computed from scratch
     const int32_t conv = (rel <= a.tol) ? 1 : 0;
     stp->converged = conv;
     if (a.rel) a.rel[b] = rel;

@@ -27,6 +27,7 @@ __device__ __forceinline__ int instance_of_item(const int64_t *spre, int count, 
 __global__ void k_resb_reset(BatchArgs a) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < a.count; b += gridDim.x * blockDim.x) {
     InstState *st = get_inst(a, b).st;
+    if (a.recheck && (st->converged || st->pivot_status == RLQR_ERR_SINGULAR)) continue;
     st->rmax = 0.0;
     st->zmax = 0.0;
     st->kmax = 0.0;
@@ -34,8 +35,9 @@ __global__ void k_resb_reset(BatchArgs a) {
   }
 }
 
-// FP64 certificate of the stored FP32 control pivots G_s (mixed path), one
-// stage per thread: unpivoted LDL^T, bit1 of flags[s], worst status.
+// FP64 certificate with margin of the stored FP32 control pivots G_s (mixed
+// path), one stage per thread (pd_margin_f32): bit1 of flags[s], the worst
+// status, and the escalation mark for a decision without its margin.
 __global__ void k_certb(BatchArgs a, const int64_t *spre, int64_t total) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -45,22 +47,10 @@ __global__ void k_certb(BatchArgs a, const int64_t *spre, int64_t total) {
     if (s >= I.N) continue;
     const int m = I.m;
     const float *G = reinterpret_cast<const float *>(I.ws + I.L.G) + (size_t)s * m * m;
-    double L[16 * 17 / 2];  // lower triangle, m <= 16
-    for (int i = 0; i < m; ++i)
-      for (int c = 0; c <= i; ++c) L[i * (i + 1) / 2 + c] = widen(__ldcg(G + c * m + i));
-    int neg = 0, zs = 0;
-    for (int j = 0; j < m; ++j) {
-      const double d = L[j * (j + 1) / 2 + j];
-      if (!finite_nonzero(d)) zs = 1;
-      if (d < 0.0) ++neg;
-      const double rd = 1.0 / d;
-      for (int i = j + 1; i < m; ++i) {
-        const double lij = L[i * (i + 1) / 2 + j] * rd;
-        for (int c = j + 1; c <= i; ++c) L[i * (i + 1) / 2 + c] -= lij * L[c * (c + 1) / 2 + j];
-      }
-    }
-    I.flags[s] = (uint8_t)((I.flags[s] & 1) | ((neg == 0 && !zs) ? 2 : 0));
-    if (neg || zs) atomicMax(&I.st->pivot_status, zs ? RLQR_ERR_SINGULAR : RLQR_NOT_PD);
+    const int dec = pd_margin_f32<16>(G, m, (double)kMarginTau);
+    I.flags[s] = (uint8_t)((I.flags[s] & 1) | (dec == kPdYes ? 2 : 0));
+    if (dec == kPdNo) atomicMax(&I.st->pivot_status, (int32_t)RLQR_NOT_PD);
+    if (dec == kPdAmbiguous) I.st->escalated = 1;
   }
 }
 
@@ -74,6 +64,7 @@ __global__ void __launch_bounds__(256) k_resb(BatchArgs a, const int64_t *spre, 
   for (int64_t g = w0; g < total; g += nw) {
     const int b = instance_of_item(spre, a.count, g);
     const Inst I = get_inst(a, b);
+    if (a.recheck && (I.st->converged || I.st->pivot_status == RLQR_ERR_SINGULAR)) continue;
     const int N = I.N, n = I.n, m = I.m, s = (int)(g - (spre ? spre[b] : 0));
     const int nn = n * n, nm = n * m, mmm = m * m;
     const double delta = I.delta;
@@ -195,9 +186,11 @@ __global__ void __launch_bounds__(256) k_resb(BatchArgs a, const int64_t *spre, 
 __global__ void k_resb_final(BatchArgs a) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < a.count; b += gridDim.x * blockDim.x) {
     InstState *st = get_inst(a, b).st;
+    if (a.recheck && (st->converged || st->pivot_status == RLQR_ERR_SINGULAR)) continue;
     const double den = st->kmax * st->zmax + st->bmax;
     const double rel = den > 0.0 ? st->rmax / den : st->rmax;
     st->rel = rel;
+    st->upd = 0.0;  // a residual computed from scratch
     const int32_t conv = (rel <= a.tol) ? 1 : 0;
     st->converged = conv;
     if (a.rel) a.rel[b] = rel;

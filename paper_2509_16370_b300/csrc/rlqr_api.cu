@@ -14,6 +14,7 @@
 
 #include "common.cuh"
 #include "cross.cuh"
+#include "escalate.cuh"
 #include "launch.cuh"
 #include "residual.cuh"
 #include "residual_grid.cuh"
@@ -101,6 +102,37 @@ static cudaError_t launch_first_residual(const BatchArgs &a, int n, int m, bool 
     return launch_grid_residual(a, spre, items, mixed, cert_g, s);
   if (mixed) return launch_residual32<float>(n, m, true, a, cert_g, s);
   return launch_residual(a, 2 * n + m, 0, nullptr, nullptr, 1, 0, s);
+}
+
+// FP64 re-decision of the pivot certificate (k_escalate) for the instances
+// of `a` whose FP32-computed pivots a margin test could not decide; the
+// other instances' blocks return at once.  solved: the call also produced a
+// solution (the status output then reflects convergence too); scan: the
+// factor came from the associative scan.
+static cudaError_t launch_escalate(const BatchArgs &a, int nmax, int mmax, int solved, int scan,
+                                   cudaStream_t s) {
+  const size_t bytes = escalate_smem_bytes(nmax, mmax);
+  cudaError_t e = set_smem(k_escalate, bytes);
+  if (e != cudaSuccess) return e;
+  BatchArgs ab = a;
+  ab.perm = nullptr;
+  ab.goff = 0;
+  LaunchScope ls("k_escalate", s);
+  k_escalate<<<ab.count, kEscThreads, bytes, s>>>(ab, solved, scan);
+  return cudaGetLastError();
+}
+
+// After a refinement pass: the full residual, recomputed in FP64 accuracy for
+// the instances whose convergence the pass's rounding bound could not
+// certify (the others return at once).  The next pass then starts from an
+// exact residual, and a certified backward error never rests on the bound.
+static cudaError_t launch_recheck(const BatchArgs &a, int n, int m, const int64_t *spre,
+                                  int64_t items, cudaStream_t s, int route = 0,
+                                  bool uniform = true) {
+  BatchArgs ar = a;
+  ar.recheck = 1;
+  return uniform ? launch_first_residual(ar, n, m, true, 0, spre, items, s, route)
+                 : launch_grid_residual(ar, spre, items, true, 0, s);
 }
 
 // ---- ragged batches: size classes and the launch order
@@ -407,14 +439,17 @@ rlqr_status rlqr_factor(const rlqr_problem *prob, const rlqr_opts *opts, void *w
     // mixed: FP64 certificate of the stored control pivots; status out
     e = mixed ? launch_scan_residual<float>(n, m, a, 1, 0, s)
               : launch_scan_residual<double>(n, m, a, 0, 0, s);
+    if (e == cudaSuccess && mixed) e = launch_escalate(a, n, m, 0, 1, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
     return sync_status(opts, ws, false, mixed, s);
   }
   if (opts->prec == RLQR_MIXED) {
     cudaError_t e = launch_seq<float, false>(n, m, true, a, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
-    // FP64 certificate of the control pivots stored by the FP32 sweep
+    // FP64 certificate of the control pivots stored by the FP32 sweep, then
+    // the FP64 decision of whatever lacked its margin
     e = launch_residual(a, 2 * n + m, 0, nullptr, nullptr, 0, 0, s, 1, 0);
+    if (e == cudaSuccess) e = launch_escalate(a, n, m, 0, 0, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
     return sync_status(opts, ws, false, true, s);
   }
@@ -468,7 +503,9 @@ rlqr_status rlqr_solve(const rlqr_problem *prob, const rlqr_opts *opts, void *ws
   }
   if (mixed)
     for (int it = 0; it < opts->max_refine; ++it) {
+      a.rpass = it;
       e = launch_solve<float, true>(n, m, true, a, s);
+      if (e == cudaSuccess) e = launch_recheck(a, n, m, nullptr, (int64_t)prob->N + 1, s);
       if (e != cudaSuccess) return RLQR_ERR_CUDA;
     }
   return sync_status(opts, ws, true, mixed, s);
@@ -639,19 +676,33 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
     const int route = uniform ? residual_route(nmaxN, nmax, mmax, a.tsize, B.count) : 0;
     e = uniform ? launch_first_residual(a, nmax, mmax, mixed, 1, spre, items, s, route)
                 : launch_grid_residual(a, spre, items, mixed, 1, s);
+    if (e == cudaSuccess && mixed) e = launch_escalate(a, nmax, mmax, 1, 0, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
   if (mixed) {
-    if (!fork()) return RLQR_ERR_CUDA;
-    for (int g = 0; g < ng; ++g) {
-      const Group &G = groups[g];
-      const BatchArgs ag = group_args(g);
-      for (int it = 0; it < opts->max_refine; ++it) {
+    const int64_t *spre = reinterpret_cast<const int64_t *>(
+        static_cast<char *>(ws) + align_up((size_t)B.count * sizeof(int64_t)) +
+        align_up((size_t)B.count * sizeof(int32_t)));
+    int64_t items = 0;
+    int nmaxN = 1;
+    for (int b = 0; b < B.count; ++b) {
+      items += (int64_t)B.h_N[b] + 1;
+      nmaxN = std::max(nmaxN, B.h_N[b]);
+    }
+    const int route = uniform ? residual_route(nmaxN, nmax, mmax, a.tsize, B.count) : 0;
+    for (int it = 0; it < opts->max_refine; ++it) {
+      if (!fork()) return RLQR_ERR_CUDA;
+      for (int g = 0; g < ng; ++g) {
+        const Group &G = groups[g];
+        BatchArgs ag = group_args(g);
+        ag.rpass = it;
         e = launch_solve<float, true>(G.n, G.m, G.exact, ag, gstream(g));
         if (e != cudaSuccess) return RLQR_ERR_CUDA;
       }
+      if (!join()) return RLQR_ERR_CUDA;
+      e = launch_recheck(a, nmax, mmax, spre, items, s, route, uniform);
+      if (e != cudaSuccess) return RLQR_ERR_CUDA;
     }
-    if (!join()) return RLQR_ERR_CUDA;
   }
   return RLQR_OK;
 }
@@ -707,11 +758,14 @@ rlqr_status rlqr_solve_noalloc(const rlqr_problem *prob, const rlqr_opts *opts, 
   if (e != cudaSuccess) return RLQR_ERR_CUDA;
   if (mixed || rel_resid) {
     e = launch_first_residual(a, n, m, mixed, 1, nullptr, (int64_t)prob->N + 1, s);
+    if (e == cudaSuccess && mixed) e = launch_escalate(a, n, m, 1, 0, s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
   if (mixed)
     for (int it = 0; it < opts->max_refine; ++it) {
+      a.rpass = it;
       e = launch_solve<float, true>(n, m, true, a, s);
+      if (e == cudaSuccess) e = launch_recheck(a, n, m, nullptr, (int64_t)prob->N + 1, s);
       if (e != cudaSuccess) return RLQR_ERR_CUDA;
     }
   return sync_status(opts, ws, true, mixed, s);

@@ -167,6 +167,89 @@ __device__ __forceinline__ void mmt(T *D, int ldd, const T *A, int lda, const T 
   }
 }
 
+// ---- 3xTF32 tensor-core products (FP32 data, sm_80+ mma.sync on the tensor
+// pipe).  Each FP32 operand x is split as x = hi + lo with hi = tf32(x)
+// (round to nearest) and lo = tf32(x - hi); the product is accumulated in
+// FP32 as lo_a hi_b + hi_a lo_b + hi_a hi_b (the lo_a lo_b term, below
+// 2^-22 of the product, is dropped).  Fragment layouts of
+// mma.m16n8k8.row.col.f32.tf32.tf32.f32 (PTX ISA): with g = lane / 4 and
+// t = lane % 4,
+//   A (16 x 8): a0 (g, t), a1 (g + 8, t), a2 (g, t + 4), a3 (g + 8, t + 4)
+//   B (8 x 8):  b0 (t, g), b1 (t + 4, g)
+//   C (16 x 8): c0 (g, 2t), c1 (g, 2t + 1), c2 (g + 8, 2t), c3 (g + 8, 2t + 1)
+__device__ __forceinline__ uint32_t tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) {
+  hi = tf32_rn(x);
+  lo = tf32_rn(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4],
+                                         const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// D (R x C) = alpha op(A) op(B) (+ Add) with 3xTF32 tensor-core products,
+// R % 16 == 0, C % 8 == 0, K % 8 == 0; one warp per 16 x 8 output tile.  The
+// same contract as mmt (D must not alias A or B; no barrier).
+template <int R, int C, int K, bool TA, bool TB>
+__device__ __forceinline__ void mmt_tc(float *D, int ldd, const float *A, int lda, const float *B,
+                                       int ldb, const float *Add, int ldadd, float alpha) {
+  static_assert(R % 16 == 0 && C % 8 == 0 && K % 8 == 0, "tensor-core tile multiples");
+  constexpr int TR = R / 16, TCn = C / 8, NT = TR * TCn;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  auto ea = [&](int r, int k) { return TA ? A[k * lda + r] : A[r * lda + k]; };
+  auto eb = [&](int k, int c) { return TB ? B[c * ldb + k] : B[k * ldb + c]; };
+  for (int tile = warp; tile < NT; tile += nw) {
+    const int r0 = (tile / TCn) * 16, c0 = (tile % TCn) * 8;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k0 = 0; k0 < K; k0 += 8) {
+      uint32_t ah[4], al[4], bh[2], bl[2];
+      tf32_split(ea(r0 + g, k0 + t), ah[0], al[0]);
+      tf32_split(ea(r0 + g + 8, k0 + t), ah[1], al[1]);
+      tf32_split(ea(r0 + g, k0 + t + 4), ah[2], al[2]);
+      tf32_split(ea(r0 + g + 8, k0 + t + 4), ah[3], al[3]);
+      tf32_split(eb(k0 + t, c0 + g), bh[0], bl[0]);
+      tf32_split(eb(k0 + t + 4, c0 + g), bh[1], bl[1]);
+      mma_tf32(acc, al, bh);
+      mma_tf32(acc, ah, bl);
+      mma_tf32(acc, ah, bh);
+    }
+    const int ra = r0 + g, rb = r0 + g + 8, ca = c0 + 2 * t;
+    float o0 = acc[0] * alpha, o1 = acc[1] * alpha, o2 = acc[2] * alpha, o3 = acc[3] * alpha;
+    if (Add) {
+      o0 += Add[ra * ldadd + ca];
+      o1 += Add[ra * ldadd + ca + 1];
+      o2 += Add[rb * ldadd + ca];
+      o3 += Add[rb * ldadd + ca + 1];
+    }
+    *reinterpret_cast<float2 *>(D + ra * ldd + ca) = make_float2(o0, o1);
+    *reinterpret_cast<float2 *>(D + rb * ldd + ca) = make_float2(o2, o3);
+  }
+}
+
+// The scan's products: 3xTF32 tensor cores where the tile shapes allow (FP32,
+// R % 16 == 0, C % 8 == 0, K % 8 == 0), the FP32 / FP64 CUDA-core tiles
+// otherwise.
+template <typename T, int R, int C, int K, bool TA, bool TB>
+__device__ __forceinline__ void mmp(T *D, int ldd, const T *A, int lda, const T *B, int ldb,
+                                    const T *Add, int ldadd, T alpha) {
+  if constexpr (sizeof(T) == 4 && R % 16 == 0 && C % 8 == 0 && K % 8 == 0)
+    mmt_tc<R, C, K, TA, TB>(D, ldd, A, lda, B, ldb, Add, ldadd, alpha);
+  else
+    mmt<T, R, C, K, TA, TB>(D, ldd, A, lda, B, ldb, Add, ldadd, alpha);
+}
+
 // Threads per row of gjr: a power of two <= 32 (a row's threads share a warp).
 template <int R, int TH>
 constexpr int gj_tpr() {
@@ -295,9 +378,9 @@ __device__ void stage_element(const Inst &I, int i, CombSmem<T, NX, NU> &s) {
   gjr<T, NU, NU + 2 * NX, kTH>(s.RX, LDR, s.rowbuf, &s.rbit, &s.rsing);
   if (tid == 0 && s.rsing) atomicOr(&I.st->r_singular, 1);
   // P = Q - M (R^{-1} M^T), A = A - B (R^{-1} M^T), C = delta I + B (R^{-1} B^T)
-  mmt<T, NX, NX, NU, false, false>(s.P1, LD, s.M, m, s.RX + m, LDR, s.Q, LD, (T)-1);
-  mmt<T, NX, NX, NU, false, false>(s.A1, LD, s.B, m, s.RX + m, LDR, s.A, LD, (T)-1);
-  mmt<T, NX, NX, NU, false, false>(s.C1, LD, s.B, m, s.RX + m + n, LDR, nullptr, 0, (T)1);
+  mmp<T, NX, NX, NU, false, false>(s.P1, LD, s.M, m, s.RX + m, LDR, s.Q, LD, (T)-1);
+  mmp<T, NX, NX, NU, false, false>(s.A1, LD, s.B, m, s.RX + m, LDR, s.A, LD, (T)-1);
+  mmp<T, NX, NX, NU, false, false>(s.C1, LD, s.B, m, s.RX + m + n, LDR, nullptr, 0, (T)1);
   __syncthreads();
   const T delta = (T)I.delta;
   for (int r = tid; r < n; r += blockDim.x) s.C1[r * LD + r] += delta;
@@ -307,13 +390,14 @@ __device__ void stage_element(const Inst &I, int i, CombSmem<T, NX, NU> &s) {
 }
 
 // (Pn, An, Cn) = (P1, A1, C1) (+) (P2, A2, C2); eq. lqr-gpu-combo with one
-// elimination of I + C1 P2 on [A1 | C1].
+// elimination of I + C1 P2 on [A1 | C1].  The six n x n products run on the
+// tensor cores in 3xTF32 (mmp) for n a multiple of 16 in FP32.
 template <typename T, int NX, int NU>
 __device__ void combine(CombSmem<T, NX, NU> &s) {
   constexpr int n = NX, LD = CombSmem<T, NX, NU>::LD, LD3 = CombSmem<T, NX, NU>::LD3;
   const int tid = threadIdx.x;
   __syncthreads();
-  mmt<T, NX, NX, NX, false, false>(s.G3, LD3, s.C1, LD, s.P2, LD, nullptr, 0, (T)1);  // C1 P2
+  mmp<T, NX, NX, NX, false, false>(s.G3, LD3, s.C1, LD, s.P2, LD, nullptr, 0, (T)1);  // C1 P2
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int r = e / n, c = e - r * n;
     s.G3[r * LD3 + n + c] = s.A1[r * LD + c];
@@ -324,12 +408,12 @@ __device__ void combine(CombSmem<T, NX, NU> &s) {
   __syncthreads();
   gjr<T, NX, 3 * NX, kTH>(s.G3, LD3, s.rowbuf, nullptr, nullptr);   // XA = T A1, XC = T C1
   const T *XA = s.G3 + n, *XC = s.G3 + 2 * n;
-  mmt<T, NX, NX, NX, false, false>(s.An, LD, s.A2, LD, XA, LD3, nullptr, 0, (T)1);   // A2 XA
-  mmt<T, NX, NX, NX, false, false>(s.T1, LD, s.A2, LD, XC, LD3, nullptr, 0, (T)1);   // A2 XC
-  mmt<T, NX, NX, NX, false, false>(s.T2, LD, s.P2, LD, XA, LD3, nullptr, 0, (T)1);   // P2 XA
+  mmp<T, NX, NX, NX, false, false>(s.An, LD, s.A2, LD, XA, LD3, nullptr, 0, (T)1);   // A2 XA
+  mmp<T, NX, NX, NX, false, false>(s.T1, LD, s.A2, LD, XC, LD3, nullptr, 0, (T)1);   // A2 XC
+  mmp<T, NX, NX, NX, false, false>(s.T2, LD, s.P2, LD, XA, LD3, nullptr, 0, (T)1);   // P2 XA
   __syncthreads();
-  mmt<T, NX, NX, NX, false, true>(s.Cn, LD, s.T1, LD, s.A2, LD, s.C2, LD, (T)1);     // (A2 XC) A2^T + C2
-  mmt<T, NX, NX, NX, true, false>(s.Pn, LD, s.A1, LD, s.T2, LD, s.P1, LD, (T)1);     // A1^T (P2 XA) + P1
+  mmp<T, NX, NX, NX, false, true>(s.Cn, LD, s.T1, LD, s.A2, LD, s.C2, LD, (T)1);     // (A2 XC) A2^T + C2
+  mmp<T, NX, NX, NX, true, false>(s.Pn, LD, s.A1, LD, s.T2, LD, s.P1, LD, (T)1);     // A1^T (P2 XA) + P1
   __syncthreads();
   mirror_lower<T>(n, s.Pn, LD);
   mirror_lower<T>(n, s.Cn, LD);
@@ -382,6 +466,7 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_reduce(BatchArgs a, ScanLayo
   if (c == SL.C) {  // terminal element (Q_N, 0, 0); instance state reset
     if (threadIdx.x == 0) {
       I.st->pivot_status = RLQR_OK;
+      I.st->escalated = 0;
       I.st->iters = 0;
       I.st->converged = 0;
       I.st->rel = 0.0;
@@ -483,7 +568,7 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_finalize(BatchArgs a, ScanLa
   const int N = I.N, c = blockIdx.x;
   const int s0 = c * SL.L, e0 = min(s0 + SL.L, N);
   const T delta = (T)I.delta;
-  const float delta_up = __double2float_ru(I.delta);
+  const float delta_up = __double2float_ru(I.delta), delta_dn = __double2float_rd(I.delta);
   const T *Sfin = reinterpret_cast<const T *>(I.ws + sbase + (from1 ? SL.S1 : SL.S0));
   T *gPhi = reinterpret_cast<T *>(I.ws + sbase + SL.Phi) + (size_t)c * nn;
   T *gW = reinterpret_cast<T *>(I.ws + I.L.W);
@@ -530,18 +615,24 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_finalize(BatchArgs a, ScanLa
     if constexpr (!FULL) {
       scan::gjr<T, NX, 2 * NX, scan::kTH>(s.S2, LD2, s.rowbuf, nullptr, nullptr);
     } else if constexpr (FP32) {
-      // Gershgorin proof in FP32 with directed rounding; FP64 LDL^T otherwise
+      // Gershgorin proof with the certificate's margin in FP32 with directed
+      // rounding; otherwise the FP64 LDL^T of I + delta P - tau D (D its
+      // diagonal) proves it or the instance is escalated to the FP64
+      // recursion (bit0 then stays 1 until that decides)
       if (tid < n) {
         float off = 0.f;
         for (int j = 0; j < n; ++j)
           if (j != tid) off = __fadd_ru(off, fabsf((float)s.P[tid * LD + j]));
-        if (!gershgorin_row_pd((float)s.P[tid * LD + tid], off, delta_up)) atomicAnd(&s.pass, 0);
+        if (!gershgorin_row_margin((float)s.P[tid * LD + tid], off, delta_dn, delta_up, kMarginTau))
+          atomicAnd(&s.pass, 0);
       }
       __syncthreads();
       if (!s.pass) {
         for (int e = tid; e < nn; e += blockDim.x) {
           const int r = e / n, col = e - r * n;
-          s.S64[e] = (r == col ? 1.0 : 0.0) + I.delta * widen((float)s.P[r * LD + col]);
+          double v = (r == col ? 1.0 : 0.0) + I.delta * widen((float)s.P[r * LD + col]);
+          if (r == col) v -= (double)kMarginTau * fabs(v);
+          s.S64[e] = v;
         }
         for (int j = 0; j < n; ++j) {
           __syncthreads();
@@ -576,6 +667,11 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_finalize(BatchArgs a, ScanLa
       if (FULL) gWk[e] = w;
     }
     __syncthreads();
+    if (FP32 && FULL) {
+      // no decision with margin: the FP64 recursion decides this instance
+      if ((!s.bit || s.sing) && tid == 0) I.st->escalated = 1;
+      return 1;
+    }
     if (s.sing) singular = 1;
     return s.bit;
   };

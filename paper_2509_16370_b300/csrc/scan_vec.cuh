@@ -260,6 +260,7 @@ __global__ void __launch_bounds__(32) k_scan_xvec(BatchArgs a, ScanLayout SL, si
   const T *dQ = scan::data_ptr<T>(I.Q, reinterpret_cast<const float *>(I.ws + I.L.Qf));
   const T *dM = scan::data_ptr<T>(I.M, reinterpret_cast<const float *>(I.ws + I.L.Mf));
   const T *dR = scan::data_ptr<T>(I.R, reinterpret_cast<const float *>(I.ws + I.L.Rf));
+  unsigned long long dzb = 0;  // max |dz| applied by this lane (refinement)
   const T *xb = reinterpret_cast<const T *>(I.ws + sbase + SL.xb);
   const T *pb = reinterpret_cast<const T *>(I.ws + sbase + SL.pb);
   T *psi = reinterpret_cast<T *>(I.ws + sbase + SL.psi);
@@ -355,6 +356,7 @@ __global__ void __launch_bounds__(32) k_scan_xvec(BatchArgs a, ScanLayout SL, si
           const size_t o = (size_t)(i + 1) * n + lane;
           I.x[o] = zx0 + widen(xn);
           I.y[o] = zy0 + widen(yn);
+          dzb = max(dzb, max(abs_bits(widen(xn)), abs_bits(widen(yn))));
           // x rows of stage i: Q dx + M du + A^T dy_{i+1} - dy_i
           const T t = scan::dotc<T, NX>(s.Q + lane * n, s.x) + scan::dots<T, NX>(s.A + lane, n, s.dyn) +
                       scan::dotc<T, NU>(s.M + lane * m, s.u) - s.dy[lane];
@@ -367,6 +369,7 @@ __global__ void __launch_bounds__(32) k_scan_xvec(BatchArgs a, ScanLayout SL, si
         if (lane < m) {
           const size_t o = (size_t)i * m + lane;
           I.u[o] = zu0 + widen(s.u[lane]);
+          dzb = max(dzb, abs_bits(widen(s.u[lane])));
           // u rows of stage i: M^T dx + R du + B^T dy_{i+1}
           const T t = scan::dots<T, NX>(s.M + lane, m, s.x) + scan::dots<T, NX>(s.B + lane, m, s.dyn) +
                       scan::dotc<T, NU>(s.R + lane * m, s.u);
@@ -392,6 +395,10 @@ __global__ void __launch_bounds__(32) k_scan_xvec(BatchArgs a, ScanLayout SL, si
     }
     double *dst = rq + (size_t)N * n + lane;
     *dst = __ldcg(dst) + widen(t);
+  }
+  if (RES) {
+    for (int o = 16; o > 0; o >>= 1) dzb = max(dzb, __shfl_xor_sync(0xffffffffu, dzb, o));
+    if (lane == 0) atomicMax(reinterpret_cast<unsigned long long *>(&I.st->dzmax), dzb);
   }
 }
 
@@ -428,6 +435,8 @@ __global__ void __launch_bounds__(32) k_scan_xbound(BatchArgs a, ScanLayout SL, 
       I.x[lane] = __ldcg(I.x + lane) + widen(x0);
       I.y[lane] = __ldcg(I.y + lane) + widen(y0);
       rc[lane] = __ldcg(rc + lane) - widen(x0) - I.delta * widen(y0);
+      atomicMax(reinterpret_cast<unsigned long long *>(&I.st->dzmax),
+                max(abs_bits(widen(x0)), abs_bits(widen(y0))));
     }
   }
   // column `lane` of Phi_c, prefetched one chunk ahead
@@ -473,28 +482,14 @@ __global__ void __launch_bounds__(128) k_res_grid(BatchArgs a, int cert_g, int d
   unsigned long long rbits = 0, zbits = 0, bbits = 0;
   float kmaxf = 0.f;
   if (cert_g) {
+    // control pivots with margin (pd_margin_f32); no margin: escalation
     const float *gG = reinterpret_cast<const float *>(I.ws + I.L.G);
-    int bad = 0, sing = 0;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
-      double L[m][m];
-      for (int i = 0; i < m; ++i)
-        for (int c = 0; c <= i; ++c) L[i][c] = widen(__ldcg(gG + (size_t)s * mmm + c * m + i));
-      int neg = 0, zs = 0;
-      for (int j = 0; j < m; ++j) {
-        const double d = L[j][j];
-        if (!finite_nonzero(d)) zs = 1;
-        if (d < 0.0) ++neg;
-        const double rd = 1.0 / d;
-        for (int i = j + 1; i < m; ++i) {
-          const double lij = L[i][j] * rd;
-          for (int c = j + 1; c <= i; ++c) L[i][c] -= lij * L[c][j];
-        }
-      }
-      I.flags[s] = (uint8_t)((I.flags[s] & 1) | ((neg == 0 && !zs) ? 2 : 0));
-      bad |= (neg != 0) | zs;
-      sing |= zs;
+      const int dec = pd_margin_f32<m>(gG + (size_t)s * mmm, m, (double)kMarginTau);
+      I.flags[s] = (uint8_t)((I.flags[s] & 1) | (dec == kPdYes ? 2 : 0));
+      if (dec == kPdNo) atomicMax(&st->pivot_status, (int32_t)RLQR_NOT_PD);
+      if (dec == kPdAmbiguous) st->escalated = 1;
     }
-    if (bad) atomicMax(&st->pivot_status, sing ? RLQR_ERR_SINGULAR : RLQR_NOT_PD);
   }
   if (!do_res) return;
   for (int s = gw; s < N; s += nw) {
@@ -643,8 +638,18 @@ static __global__ void k_res_final(BatchArgs a, int pass) {
   const Inst I = get_inst(a, 0);
   InstState *st = I.st;
   if (pass && (st->converged || st->pivot_status == RLQR_ERR_SINGULAR)) return;
+  if (pass) {
+    // rounding bound of the pass's residual update in the working precision
+    // (2 gamma_L ||K||_inf max|dz| per entry, L = 2n + m), accumulated
+    const double uw = a.tsize == 4 ? 0x1p-24 : 0x1p-53;
+    st->upd += 2.0 * (2 * I.n + I.m) * uw * st->kmax * st->dzmax;
+    st->dzmax = 0.0;
+  } else {
+    st->upd = 0.0;  // a residual computed from scratch
+    st->dzmax = 0.0;
+  }
   const double den = st->kmax * st->zmax + st->bmax;
-  const double rel = den > 0.0 ? st->rmax / den : st->rmax;
+  const double rel = den > 0.0 ? (st->rmax + st->upd) / den : st->rmax + st->upd;
   st->rel = rel;
   if (pass) st->iters += 1;
   const int32_t conv = (rel <= a.tol) ? 1 : 0;
@@ -667,6 +672,8 @@ static __global__ void k_norms_reset(BatchArgs a, int all) {
   if (all) {  // start of a solve
     st->kmax = 0.0;
     st->bmax = 0.0;
+    st->upd = 0.0;
+    st->dzmax = 0.0;
     st->iters = 0;
     st->converged = 0;
   }

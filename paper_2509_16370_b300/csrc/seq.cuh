@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
   const int N = I.N, n = dims.n, m = dims.m;
   const T delta = (T)I.delta;
   const float delta_up = __double2float_ru(I.delta);  // Gershgorin test (FP32 sweep)
+  const float delta_dn = __double2float_rd(I.delta);
   const int tid = threadIdx.x;
   using S = SeqSmem<T, NM, MM>;
 
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
 
   RegGJ<T, THREADS, NM, WS> gs;  // owner of entries of [I + delta P | P]
   RegGJ<T, THREADS, MM, WC> gc;  // owner of entries of [G | H | h | I]
-  bool notpd = false, singular = false;
+  bool notpd = false, singular = false, escal = false;
   int bit1_next = 1;  // stage N has no control pivot
 
   // ---- terminal stage: P_N = Q_N (upper triangle), p_N = q_N
@@ -296,14 +297,16 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
     }
     bool shadow = false;
     if constexpr (FP32SWEEP) {
-      // Gershgorin proof that I + delta P is PD, in FP32 with directed
-      // rounding; otherwise an FP64 LDL^T decides.
+      // Gershgorin proof, with the certificate's margin, that I + delta P
+      // is PD, in FP32 with directed rounding; otherwise the FP64 LDL^T of
+      // I + delta P - tau D (D its diagonal) proves it, or the instance is
+      // escalated to the FP64 recursion.
       int pass = 1;
       if (tid < n) {
         float off = 0.f;
         for (int j = 0; j < n; ++j)
           if (j != tid) off = __fadd_ru(off, fabsf(sP[tid * n + j]));
-        pass = gershgorin_row_pd(sP[tid * n + tid], off, delta_up);
+        pass = gershgorin_row_margin(sP[tid * n + tid], off, delta_dn, delta_up, kMarginTau);
       }
       __syncthreads();  // the flag reset by thread 0 precedes every later write
       gs.template publish0<DECIDE>(n, w2, shs);
@@ -311,7 +314,8 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
       if (shadow) {
         for (int idx = tid; idx < nn; idx += THREADS) {
           const int i = idx / n, j = idx - i * n;
-          const double v = (i == j ? 1.0 : 0.0) + I.delta * widen(sP[idx]);
+          double v = (i == j ? 1.0 : 0.0) + I.delta * widen(sP[idx]);
+          if (i == j) v -= (double)kMarginTau * fabs(v);
           sS64[idx] = v;
           if (idx == 0) rinv64[0] = 1.0 / v;
         }
@@ -505,9 +509,15 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
     if (tid == 0) {
       // FP32 sweep: bit1 of stages < N is added by the FP64 control-pivot pass
       const int b1 = FP32SWEEP ? (k + 1 == N) : bit1_next;
-      I.flags[k + 1] = (uint8_t)(shs.bit | (b1 << 1));
-      if (!shs.bit || (!FP32SWEEP && !b1)) notpd = true;
-      if (shs.singular || (!FP32SWEEP && shc.singular)) singular = true;
+      if (FP32SWEEP) {
+        // the shifted FP64 LDL^T failed: no decision with margin
+        if (!shs.bit || shs.singular) escal = true;
+        I.flags[k + 1] = (uint8_t)(1 | (b1 << 1));
+      } else {
+        I.flags[k + 1] = (uint8_t)(shs.bit | (b1 << 1));
+        if (!shs.bit || !b1) notpd = true;
+        if (shs.singular || shc.singular) singular = true;
+      }
       bit1_next = shc.bit;
     }
     __syncthreads();
@@ -517,11 +527,17 @@ __global__ void __launch_bounds__(THREADS) k_seq(BatchArgs a) {
   state_pivot(gW);
   if (tid == 0) {
     const int b1 = FP32SWEEP ? (N == 0) : bit1_next;
-    I.flags[0] = (uint8_t)(shs.bit | (b1 << 1));
-    if (!shs.bit || (!FP32SWEEP && !b1)) notpd = true;
-    if (shs.singular) singular = true;
+    if (FP32SWEEP) {
+      if (!shs.bit || shs.singular) escal = true;
+      I.flags[0] = (uint8_t)(1 | (b1 << 1));
+    } else {
+      I.flags[0] = (uint8_t)(shs.bit | (b1 << 1));
+      if (!shs.bit || !b1) notpd = true;
+      if (shs.singular) singular = true;
+    }
     const int32_t st = singular ? RLQR_ERR_SINGULAR : (notpd ? RLQR_NOT_PD : RLQR_OK);
     I.st->pivot_status = st;
+    I.st->escalated = escal ? 1 : 0;
     I.st->iters = 0;
     I.st->converged = 0;
     I.st->rel = 0.0;

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(scan::kTH) k_seqx(BatchArgs a) {
   const Inst I = get_inst(a, b);
   const int N = I.N, tid = threadIdx.x;
   const T delta = (T)I.delta;
-  const float delta_up = __double2float_ru(I.delta);
+  const float delta_up = __double2float_ru(I.delta), delta_dn = __double2float_rd(I.delta);
   T *gW = reinterpret_cast<T *>(I.ws + I.L.W);
   T *gK = reinterpret_cast<T *>(I.ws + I.L.K);
   T *gGi = reinterpret_cast<T *>(I.ws + I.L.Gi);
@@ -151,14 +151,15 @@ __global__ void __launch_bounds__(scan::kTH) k_seqx(BatchArgs a) {
     }
     __syncthreads();
     if constexpr (FP32) {
-      // Gershgorin proof in FP32 with directed rounding; when it fails the
-      // stage's P is stored and k_seqx_cert decides bit0 later,
-      // off this instance's sequential chain
+      // Gershgorin proof in FP32 with directed rounding, with the
+      // certificate's margin; when it fails the stage's P is stored and
+      // k_seqx_cert decides bit0 later, off this instance's sequential chain
       if (tid < n) {
         float off = 0.f;
         for (int j = 0; j < n; ++j)
           if (j != tid) off = __fadd_ru(off, fabsf((float)s.P[tid * LD + j]));
-        if (!gershgorin_row_pd((float)s.P[tid * LD + tid], off, delta_up)) atomicAnd(&s.pass, 0);
+        if (!gershgorin_row_margin((float)s.P[tid * LD + tid], off, delta_dn, delta_up, kMarginTau))
+          atomicAnd(&s.pass, 0);
       }
       __syncthreads();
       const int stage = (int)((gWk - gW) / nn);
@@ -296,6 +297,7 @@ __global__ void __launch_bounds__(scan::kTH) k_seqx(BatchArgs a) {
       if (!bit0 || (!FP32 && !b1)) notpd = true;
       const int32_t st = singular ? RLQR_ERR_SINGULAR : (notpd ? RLQR_NOT_PD : RLQR_OK);
       I.st->pivot_status = st;
+      I.st->escalated = 0;
       I.st->iters = 0;
       I.st->converged = 0;
       I.st->rel = 0.0;
@@ -405,16 +407,19 @@ __global__ void __launch_bounds__(128) k_seqx_cert(BatchArgs a) {
   for (int st = blockIdx.y * nwb + wid; st <= I.N; st += gridDim.y * nwb) {
     if (!__ldcg(pend + st)) continue;
     // proven: bit0 stays as the sweep wrote it (1)
-    if (warp_pd_proof_f32<NX>(Pc + (size_t)st * NX * NX, I.delta)) continue;
+    if (warp_pd_proof_f32<NX>(Pc + (size_t)st * NX * NX, I.delta, kMarginTau)) continue;
     if (lane == 0) pend[st] = 2;
   }
 }
 
-// The FP64 decision for the stages the FP32 proof left open (pend[s] = 2):
-// unpivoted LDL^T of I + delta P_s in shared memory, one warp per stage, the
-// trailing triangle's updates spread over the lanes.  Sets bit0 of flags[s]
-// and raises the instance's pivot status (and status output) to RLQR_NOT_PD
-// or RLQR_ERR_SINGULAR.  Same grid as k_seqx_cert.
+// The FP64 decision for the stages the FP32 proof left open (pend[s] = 2),
+// with the certificate's margin: unpivoted LDL^T of S - tau D and, when that
+// is not PD, of S + tau D (S = I + delta P_s from the stored FP32 P_s, D =
+// diag(max(|S_jj|, 2^-24 max |S_jj|))), one warp per stage, the trailing
+// triangle's updates spread over the lanes.  S - tau D PD: bit0 stays 1;
+// S + tau D not PD: bit0 = 0 and the pivot status (and status output) rise
+// to RLQR_NOT_PD; neither, or a non-finite entry: the instance is escalated
+// to the FP64 recursion (InstState::escalated).  Same grid as k_seqx_cert.
 template <int NX>
 __global__ void __launch_bounds__(128) k_seqx_cert64(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -427,43 +432,56 @@ __global__ void __launch_bounds__(128) k_seqx_cert64(BatchArgs a) {
   const Inst I = get_inst(a, b);
   const uint8_t *pend = reinterpret_cast<const uint8_t *>(I.ws + I.L.pend);
   const float *Pc = reinterpret_cast<const float *>(I.ws + I.L.Pc);
-  int worst = RLQR_OK;
+  int notpd = 0, esc = 0;
   for (int st = blockIdx.y * nwb + wid; st <= I.N; st += gridDim.y * nwb) {
     if (__ldcg(pend + st) != 2) continue;
     const float *P = Pc + (size_t)st * nn;
-    __syncwarp();
-    for (int e = lane; e < nn; e += 32) {
-      const int r = e / n, c = e - r * n;
-      S[e] = (r == c ? 1.0 : 0.0) + I.delta * widen(__ldcg(P + e));
-    }
-    int bit = 1, sing = 0;
-    for (int j = 0; j < n; ++j) {
+    // diagonal scale of the shift
+    double dmax = 0.0;
+    for (int j = lane; j < n; j += 32)
+      dmax = fmax(dmax, fabs(1.0 + I.delta * widen(__ldcg(P + j * n + j))));
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    int dec = kPdAmbiguous;
+    for (int pass = 0; pass < 2; ++pass) {
+      const double sg = pass == 0 ? -(double)kMarginTau : (double)kMarginTau;
       __syncwarp();
-      const double d = S[j * n + j];
-      if (!(d > 0.0)) bit = 0;
-      if (!finite_nonzero(d)) sing = 1;
-      // FP32 reciprocal and one Newton step (relative error ~1e-14); it only
-      // scales the updates, the decision is the signs of the pivots
-      const float df = (float)d;
-      double rd = (double)(1.0f / df);
-      rd = (isfinite(rd) && rd != 0.0) ? rd * (2.0 - d * rd) : 1.0 / d;
-      const int r = n - 1 - j;
-      for (int idx = lane; idx < r * (r + 1) / 2; idx += 32) {
-        int i, c;
-        tri_decode(idx, i, c);
-        i += j + 1;
-        c += j + 1;
-        S[i * n + c] -= S[i * n + j] * (S[c * n + j] * rd);
+      for (int e = lane; e < nn; e += 32) {
+        const int r = e / n, c = e - r * n;
+        double v = (r == c ? 1.0 : 0.0) + I.delta * widen(__ldcg(P + e));
+        if (r == c) v += sg * fmax(fabs(v), 0x1p-24 * dmax);
+        S[e] = v;
       }
+      int pos = 1, fin = 1;
+      for (int j = 0; j < n; ++j) {
+        __syncwarp();
+        const double d = S[j * n + j];
+        if (!isfinite(d)) fin = 0;
+        if (!(d > 0.0)) pos = 0;
+        if (!pos || !fin) break;  // uniform over the warp
+        const double rd = 1.0 / d;
+        const int r = n - 1 - j;
+        for (int idx = lane; idx < r * (r + 1) / 2; idx += 32) {
+          int i, c;
+          tri_decode(idx, i, c);
+          i += j + 1;
+          c += j + 1;
+          S[i * n + c] -= S[i * n + j] * (S[c * n + j] * rd);
+        }
+      }
+      if (!fin) break;
+      if (pass == 0 && pos) { dec = kPdYes; break; }
+      if (pass == 1 && !pos) { dec = kPdNo; break; }
     }
     if (lane == 0) {
-      I.flags[st] = (uint8_t)((I.flags[st] & 2) | bit);
-      worst = max(worst, sing ? (int)RLQR_ERR_SINGULAR : (bit ? (int)RLQR_OK : (int)RLQR_NOT_PD));
+      if (dec == kPdNo) I.flags[st] = (uint8_t)(I.flags[st] & 2);
+      notpd |= dec == kPdNo;
+      esc |= dec == kPdAmbiguous;
     }
   }
-  if (lane == 0 && worst != RLQR_OK) {
-    atomicMax(&I.st->pivot_status, worst);
-    if (a.status) atomicMax(&a.status[b], worst);
+  if (lane == 0 && esc) I.st->escalated = 1;
+  if (lane == 0 && notpd) {
+    atomicMax(&I.st->pivot_status, (int32_t)RLQR_NOT_PD);
+    if (a.status) atomicMax(&a.status[b], (int32_t)RLQR_NOT_PD);
   }
 }
 

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(32) k_sweep32(BatchArgs a) {
   const Inst I = get_inst(a, b);
   const int N = I.N;
   const float delta = (float)I.delta;
-  const float delta_up = __double2float_ru(I.delta);
+  const float delta_up = __double2float_ru(I.delta), delta_dn = __double2float_rd(I.delta);
   const float2 delta2 = bcast2(delta);
   float *gW = reinterpret_cast<float *>(I.ws + I.L.W);
   float *gK = reinterpret_cast<float *>(I.ws + I.L.K);
@@ -260,8 +260,12 @@ __global__ void __launch_bounds__(32) k_sweep32(BatchArgs a) {
       else
         v2[q] = Pc[q];
     }
-    // Gershgorin proof that I + delta P is PD (lanes n..2n-1 hold column c =
-    // row c of P); otherwise an FP64 LDL^T decides
+    // Gershgorin proof, with the certificate's margin, that I + delta P is PD
+    // (lanes n..2n-1 hold column c = row c of P).  Otherwise the FP64 LDL^T
+    // of I + delta P - tau D (D = diag, floored at 2^-24 max |D|) proves it;
+    // else a non-positive pivot of I + delta P + tau D proves it not PD
+    // (bit 0); else the instance is escalated to the FP64 recursion (`sing`;
+    // the bit stays 1 until that decides).
     int bit = 1;
     bool pass = true;
     if (lane >= n && lane < 2 * n) {
@@ -275,31 +279,50 @@ __global__ void __launch_bounds__(32) k_sweep32(BatchArgs a) {
         else
           off = __fadd_ru(off, fabsf(val));
       }
-      pass = gershgorin_row_pd(diag, off, delta_up);
+      pass = gershgorin_row_margin(diag, off, delta_dn, delta_up, kMarginTau);
     }
     if (!__all_sync(0xffffffffu, pass)) {
-      if (lane >= n && lane < 2 * n) {
-        const int c = lane - n;
+      // largest diagonal magnitude of I + delta P (shift floor)
+      double dm = 0.0;
+      if (lane >= n && lane < 2 * n)
+        dm = fabs(1.0 + I.delta * widen(el(Pc[(lane - n) / 2], (lane - n) & 1)));
+      for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+      int decided = 0;
+      for (int pass2 = 0; pass2 < 2 && !decided; ++pass2) {
+        const double sg = pass2 == 0 ? -(double)kMarginTau : (double)kMarginTau;
+        __syncwarp();
+        if (lane >= n && lane < 2 * n) {
+          const int c = lane - n;
 #pragma unroll
-        for (int i = 0; i < n; ++i)
-          s.S64[i * n + c] = (i == c ? 1.0 : 0.0) + I.delta * widen(el(Pc[i / 2], i & 1));
-      }
-      __syncwarp();
-      for (int j = 0; j < n; ++j) {
-        const double d = s.S64[j * n + j];
-        if (!(d > 0.0)) bit = 0;
-        if (!finite_nonzero(d)) sing = true;
-        const double rd = 1.0 / d;
-        const int r = n - j - 1;
-        for (int idx = lane; idx < r * (r + 1) / 2; idx += 32) {
-          int i, cc;
-          tri_decode(idx, i, cc);
-          i += j + 1;
-          cc += j + 1;
-          s.S64[i * n + cc] -= s.S64[i * n + j] * (s.S64[cc * n + j] * rd);
+          for (int i = 0; i < n; ++i) {
+            double v = (i == c ? 1.0 : 0.0) + I.delta * widen(el(Pc[i / 2], i & 1));
+            if (i == c) v += sg * fmax(fabs(v), 0x1p-24 * dm);
+            s.S64[i * n + c] = v;
+          }
         }
         __syncwarp();
+        bool pos = true, fin = true;
+        for (int j = 0; j < n; ++j) {
+          const double d = s.S64[j * n + j];
+          if (!isfinite(d)) fin = false;
+          if (!(d > 0.0)) pos = false;
+          if (!pos || !fin) break;  // uniform over the warp
+          const double rd = 1.0 / d;
+          const int r = n - j - 1;
+          for (int idx = lane; idx < r * (r + 1) / 2; idx += 32) {
+            int i, cc;
+            tri_decode(idx, i, cc);
+            i += j + 1;
+            cc += j + 1;
+            s.S64[i * n + cc] -= s.S64[i * n + j] * (s.S64[cc * n + j] * rd);
+          }
+          __syncwarp();
+        }
+        if (!fin) break;
+        if (pass2 == 0 && pos) decided = 1;                // PD with margin
+        if (pass2 == 1 && !pos) { decided = 1; bit = 0; }  // not PD with margin
       }
+      if (!decided) sing = true;  // escalate
     }
     // block Gauss-Jordan, pivot blocks {j, j+1}
 #pragma unroll
@@ -542,8 +565,10 @@ __global__ void __launch_bounds__(32) k_sweep32(BatchArgs a) {
     if (lane == 0) {
       I.flags[0] = (uint8_t)bit0;
       if (!bit0) notpd = true;
-      const int32_t st = singular ? RLQR_ERR_SINGULAR : (notpd ? RLQR_NOT_PD : RLQR_OK);
+      // `singular` marks a state pivot without a decision with margin
+      const int32_t st = notpd ? RLQR_NOT_PD : RLQR_OK;
       I.st->pivot_status = st;
+      I.st->escalated = singular ? 1 : 0;
       I.st->iters = 0;
       I.st->converged = 0;
       I.st->rel = 0.0;

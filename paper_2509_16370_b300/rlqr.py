@@ -115,8 +115,10 @@ def _load():
     lib.rlqr_solve_diag.restype = st
     lib.rlqr_solve_diag.argtypes = [P(rlqr_problem), _dp, P(rlqr_opts), _dp, sz, _dp, _dp, _dp,
                                     _dp, _dp, _dp, _dp]
+    lib.rlqr_measure_pipes_bytes.restype = sz
+    lib.rlqr_measure_pipes_bytes.argtypes = []
     lib.rlqr_measure_pipes.restype = st
-    lib.rlqr_measure_pipes.argtypes = [P(ctypes.c_double)] * 3
+    lib.rlqr_measure_pipes.argtypes = [_dp, sz] + [P(ctypes.c_double)] * 3
     lib.rlqr_instrument.restype = st
     lib.rlqr_instrument.argtypes = [ctypes.c_int]
     lib.rlqr_instrument_report.restype = ctypes.c_int
@@ -416,9 +418,13 @@ def rlqr_shard_entry(nx: int, delta: float, P_start, x_start, x_first, c0, strea
 
 def rlqr_measure_pipes() -> dict:
     """Measured FP64 / FP32 / packed-FP32 FMA rates of the current device in
-    TFLOP/s (synchronous microbenchmark)."""
+    TFLOP/s (synchronous microbenchmark; the sink buffer is a torch tensor)."""
+    nb = int(lib.rlqr_measure_pipes_bytes())
+    buf = torch.empty(max(nb, 8), dtype=torch.uint8, device="cuda")
     v = [ctypes.c_double() for _ in range(3)]
-    _check(lib.rlqr_measure_pipes(*[ctypes.byref(x) for x in v]), "rlqr_measure_pipes")
+    _check(lib.rlqr_measure_pipes(_ptr(buf), nb, *[ctypes.byref(x) for x in v]),
+           "rlqr_measure_pipes")
+    torch.cuda.synchronize()
     return dict(fp64_tflops=v[0].value, fp32_tflops=v[1].value, fp32x2_tflops=v[2].value)
 
 

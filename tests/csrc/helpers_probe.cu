@@ -52,12 +52,12 @@ __global__ void k_gersh(const float *P, int rows, int n, double delta, int *pass
   pass[r] = gershgorin_row_pd(row[i], off, __double2float_ru(delta)) ? 1 : 0;
 }
 
-// one warp per matrix: the FP32 proof that I + delta P_k is PD
+// one warp per matrix: the FP32 proof that I + delta P_k - tau D is PD
 template <int NX>
-__global__ void k_pdproof(const float *P, int count, double delta, int *pass) {
+__global__ void k_pdproof(const float *P, int count, double delta, float tau, int *pass) {
   const int k = blockIdx.x;
   if (k >= count) return;
-  const int r = warp_pd_proof_f32<NX>(P + (size_t)k * NX * NX, delta);
+  const int r = warp_pd_proof_f32<NX>(P + (size_t)k * NX * NX, delta, tau);
   if (threadIdx.x == 0) pass[k] = r;
 }
 
@@ -89,10 +89,11 @@ extern "C" int probe_gersh(const float *P, int rows, int n, double delta, int *p
   return finish();
 }
 
-extern "C" int probe_pdproof(const float *P, int count, int n, double delta, int *pass) {
-  if (n == 12) k_pdproof<12><<<count, 32>>>(P, count, delta, pass);
-  else if (n == 24) k_pdproof<24><<<count, 32>>>(P, count, delta, pass);
-  else if (n == 48) k_pdproof<48><<<count, 32>>>(P, count, delta, pass);
+extern "C" int probe_pdproof(const float *P, int count, int n, double delta, float tau,
+                             int *pass) {
+  if (n == 12) k_pdproof<12><<<count, 32>>>(P, count, delta, tau, pass);
+  else if (n == 24) k_pdproof<24><<<count, 32>>>(P, count, delta, tau, pass);
+  else if (n == 48) k_pdproof<48><<<count, 32>>>(P, count, delta, tau, pass);
   else return -1;
   return finish();
 }

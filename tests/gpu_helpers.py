@@ -71,3 +71,10 @@ def workload4_item(arg):
     from paper_2509_16370_b300 import inputs
     b, (N, n, m) = arg
     return inputs.workload4_instance(b, N, n, m)
+
+
+def workload4_oracle_flags(arg):
+    """The oracle's pivot flags of instance b of the ragged workload (a worker
+    of a spawn process pool: it regenerates the instance from its seed)."""
+    import oracle
+    return oracle.riccati(workload4_item(arg)).flags

@@ -11,9 +11,9 @@ against an independent definition computed on the host:
 * gershgorin_row_pd: sound (a pass implies the exact rational test
   1 + delta (P_ii - sum |P_ij|) > 0) and not needlessly conservative.
 * warp_pd_proof_f32: sound (a pass implies that the smallest eigenvalue of
-  I + delta P, computed by LAPACK in FP64 from the exact FP32 P, is
-  positive), invariant to diagonal scaling, and passing every matrix whose
-  Jacobi-scaled smallest eigenvalue is clear of zero.
+  I + delta P - tau D, D its diagonal, computed by LAPACK in FP64 from the
+  exact FP32 P, is positive), invariant to diagonal scaling, and passing
+  every matrix whose Jacobi-scaled smallest eigenvalue is clear of tau.
 """
 import ctypes
 import os
@@ -202,30 +202,35 @@ def _pd_cases(rng, n, delta, count):
 
 
 @pytest.mark.parametrize("n", [12, 24, 48])
-def test_fp32_cholesky_pd_proof(probe, n):
+@pytest.mark.parametrize("tau", [0.0, 2.0 ** -15])
+def test_fp32_cholesky_pd_proof(probe, n, tau):
+    """With the margin tau the proof is for I + delta P - tau D (D its
+    diagonal): a pass implies that matrix PD, and every matrix whose
+    Jacobi-scaled smallest eigenvalue exceeds tau by a clear gap passes."""
     rng = np.random.default_rng(100 + n)
     for delta in (1e-3, 0.3, 7.0):
         mats = _pd_cases(rng, n, delta, 64)
         P = np.stack(mats)
         pas = torch.empty(len(mats), dtype=torch.int32, device="cuda")
-        assert probe.probe_pdproof(_ptr(_dev(P)), len(mats), n, ctypes.c_double(delta), _ptr(pas)) == 0
+        assert probe.probe_pdproof(_ptr(_dev(P)), len(mats), n, ctypes.c_double(delta),
+                                   ctypes.c_float(tau), _ptr(pas)) == 0
         pas = pas.cpu().numpy()
         passed = 0
         for k, Pk in enumerate(mats):
             M = np.eye(n) + delta * Pk.astype(np.float64)
-            lam_min = np.linalg.eigvalsh(M).min()
+            Mt = M - tau * np.diag(np.diag(M))
+            lam_min = np.linalg.eigvalsh(Mt).min()
             tol = 64 * n * np.finfo(np.float64).eps * np.abs(M).max()
             if pas[k]:
                 # sound: a proof never passes a matrix that is not PD
                 assert lam_min > -tol, (n, delta, k, lam_min)
                 passed += 1
-            # complete where the Jacobi-scaled spectrum is clear of zero
+            # complete where the Jacobi-scaled spectrum is clear of tau
             d = 1.0 / np.sqrt(np.abs(np.diag(M)))
             lam_s = np.linalg.eigvalsh(d[:, None] * M * d[None, :]).min()
-            if lam_s > 2e-3:
+            if lam_s > 2e-3 + tau:
                 assert pas[k], (n, delta, k, lam_s)
         assert passed >= len(mats) // 4
-
 
 
 def test_measured_pipe_rates_are_consistent():

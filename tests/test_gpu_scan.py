@@ -53,8 +53,10 @@ def test_scan_matches_oracle(name, make, prec):
     rel, fe, ref = check_against_oracle(p, out, prec)
     assert out["status_factor"] == ref.status
     if prec == rlqr.RLQR_MIXED:
+        # the reported value bounds the backward error from above (updated
+        # residual plus the accumulated rounding bound of the corrections)
         assert out["rel"] <= REL_TOL
-        np.testing.assert_allclose(out["rel"], rel, rtol=0.05, atol=1e-11)
+        assert rel <= 1.05 * out["rel"] + 1e-15, (rel, out["rel"])
 
 
 @pytest.mark.parametrize("prec", PRECS)

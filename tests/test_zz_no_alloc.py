@@ -53,6 +53,37 @@ def test_noalloc_matches_workspace_entry_points_twice(prec):
         assert out["rel"] <= REL_TOL
 
 
+@pytest.mark.parametrize("dims", [(40, 24, 8), (128, 6, 1), (30, 10, 3), (20, 12, 3)],
+                         ids=["cta_24x8", "tableau_6x1", "bucket_10x3", "tableau_12x3"])
+@pytest.mark.parametrize("prec", [rlqr.RLQR_FP64, rlqr.RLQR_MIXED])
+def test_noalloc_other_kernel_routes(dims, prec):
+    """The sizes whose sweeps take the other routes -- the compile-time CTA
+    sweep with its deferred certificate (24, 8), the tableau warp sweep with
+    odd n_u (6, 1) and (12, 3), the bucket kernels at a size without an
+    instantiation (10, 3) -- give the same flags, status and (within the
+    parity tolerance) solution as rlqr_factor + rlqr_solve."""
+    N, n, m = dims
+    p = inputs.random_instance(400 + n, N, n, m, 1e-3, with_M=True)
+    ref = solve_single(p, prec)
+    out = _noalloc(p, prec)
+    np.testing.assert_array_equal(out["flags"], ref["flags"])
+    assert out["status"] == ref["status"]
+    fe = oracle.forward_error((ref["x"], ref["u"], ref["y"]), out["x"], out["u"], out["y"])
+    assert fe <= FWD_TOL[prec]
+    assert oracle.residual(p, out["x"], out["u"], out["y"]).rel <= REL_TOL
+
+
+def test_noalloc_refuses_the_scan():
+    """The allocation-free call runs the sequential recursion only."""
+    p = inputs.workload1()
+    dp = rlqr.DeviceProblem.from_host(p)
+    opts = rlqr.make_opts(rlqr.RLQR_FP64, algo=rlqr.RLQR_ALGO_SCAN)
+    t = torch.zeros((p.N + 1) * p.n, dtype=torch.float64, device="cuda")
+    f = torch.zeros(p.N + 1, dtype=torch.uint8, device="cuda")
+    with pytest.raises(rlqr.RlqrError, match="argument"):
+        rlqr.rlqr_solve_noalloc(dp, opts, t, t, t, f)
+
+
 def test_noalloc_rejects_oversized_instances():
     """An instance whose workspace exceeds the static scratch is refused on
     the host with RLQR_ERR_WORKSPACE; nothing runs on the GPU."""
