@@ -691,7 +691,7 @@ def measure_long_horizon(args, fp64_reps=1, fp64_warmup=1):
     import torch
     import oracle
     from paper_2509_16370_b300 import inputs, rlqr
-    p = inputs.workload3()
+    p = inputs.workload3(N=getattr(args, "lh_stages", 65536))
     dp = rlqr.DeviceProblem.from_host(p)
     N, n, m = p.N, p.n, p.m
 
@@ -777,10 +777,11 @@ def measure_long_horizon(args, fp64_reps=1, fp64_warmup=1):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64 (FP32 scan; FP64 certificate, residual, correction)",
             "data": "synthetic",
-            "config": {"workload": "one dual-regularized LQR, n_x=32, n_u=8, N=65536, delta=1e-7, "
+            "config": {"workload": f"one dual-regularized LQR, n_x=32, n_u=8, N={N}, delta=1e-7, "
                                    "rho(A)=0.99, cond(Q)=cond(R)=1e4", "algo": "scan",
                        "chunks": chunks, "autotune": tune,
-                       "l2": "inputs 1.4 GB > L2 (no flush needed)"},
+                       "l2": f"inputs {21.5e3 * N / 1e9:.2f} GB" + (
+                           " > L2 (no flush needed)" if N >= 8192 else "")},
             "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in report.items()},
             "accuracy": {"rel_resid": rel, "all_le_tol": rel <= TOL,
                          "iters": int(bufs["it"].item()), "status": int(bufs["st"].item())},
@@ -793,6 +794,17 @@ def measure_long_horizon(args, fp64_reps=1, fp64_warmup=1):
             "flags_all_pd": bool((flags_gpu == 3).all()),
             "clocks": clk.summary()}
     return line
+
+
+def escalated_instances(ws, count):
+    """Per instance of a batched solve: 1 if the FP64 recursion decided its
+    pivot certificate (the escalated field, int32 at byte 56 of the
+    instance's state; the instance offsets are the int64 array at the head
+    of the batched workspace)."""
+    import torch
+    offs = ws[:8 * count].view(torch.int64)
+    idx = offs.unsqueeze(1) + 56 + torch.arange(4, device=ws.device)
+    return ws[idx].contiguous().view(torch.int32).reshape(count).cpu().numpy()
 
 
 def _ragged_instance(arg):
@@ -856,9 +868,15 @@ def measure_ragged(args, count, only_n=0):
         report = rlqr.rlqr_instrument_report() if instrument else {}
         rlqr.rlqr_instrument(False)
         relv, stv = rel.cpu().numpy(), st.cpu().numpy()
-        return e0.elapsed_time(e1) / steps, report, dict(
-            max_rel=float(relv.max()), all_le_tol=bool(np.all(relv <= TOL)),
-            max_iters=int(it.max().item()), statuses=sorted(set(stv.tolist())))
+        acc = dict(max_rel=float(relv.max()), all_le_tol=bool(np.all(relv <= TOL)),
+                   max_iters=int(it.max().item()), statuses=sorted(set(stv.tolist())))
+        if prec == rlqr.RLQR_MIXED:
+            esc = escalated_instances(ws, B)
+            acc["escalated"] = {f"n={nn}": int(sum(int(e) for e, (_, n_, _) in zip(esc, dims)
+                                                   if n_ == nn))
+                                for nn in sorted({d[1] for d in dims})}
+            acc["escalated_stages"] = int(sum(N_ for e, (N_, _, _) in zip(esc, dims) if e))
+        return e0.elapsed_time(e1) / steps, report, acc
 
     with ClockSampler(0) as clk:
         ms, report, acc = timed(rlqr.RLQR_MIXED, args.steps, args.warmup, True)
@@ -939,8 +957,9 @@ def run_ours(args):
         stv = st.cpu().numpy()
         relv = rel.cpu().numpy()
         ok = bool(np.all(relv <= TOL) and np.all((stv == 0) | (stv == 1)))
+        esc = int(escalated_instances(ws, B).sum()) if prec == rlqr.RLQR_MIXED else 0
         return ms, report, dict(max_rel=float(relv.max()), ok=ok, iters=int(it.max().item()),
-                                not_pd=int((stv == 1).sum()))
+                                not_pd=int((stv == 1).sum()), escalated=esc)
 
     # the arithmetic pipes' measured rates (roofline denominators of the FP64
     # and FP32 kernels), taken before the timed regions
@@ -1012,7 +1031,8 @@ def run_ours(args):
         "kernels": {k: {"launches": c, "ms_total": round(t, 4)} for k, (c, t) in report.items()},
         "gpu_launches": launches,
         "accuracy": {"max_rel_resid": chk_mixed["max_rel"], "all_le_tol": chk_mixed["ok"],
-                     "max_refine_iters": chk_mixed["iters"], "not_pd_instances": chk_mixed["not_pd"]},
+                     "max_refine_iters": chk_mixed["iters"], "not_pd_instances": chk_mixed["not_pd"],
+                     "escalated_instances": chk_mixed["escalated"]},
         "fp64_plain": {"value": fp64_value, "ms_per_step": ms_fp64,
                        "max_rel_resid": chk_fp64["max_rel"], "all_le_tol": chk_fp64["ok"],
                        "roofline": fp64_sweep_roofline(report64, n, m, stages, pipes)},
@@ -1062,6 +1082,8 @@ def main():
                     help="with --long-horizon: choose the scan's chunk count by timing first")
     ap.add_argument("--long-horizon", action="store_true",
                     help="the single long-horizon instance (associative scan)")
+    ap.add_argument("--lh-stages", type=int, default=65536,
+                    help="with --long-horizon: the horizon N (smaller for profiling)")
     ap.add_argument("--cross", type=int, default=0,
                     help="cross-stage variables: time rlqr_solve_cross with p = CROSS")
     ap.add_argument("--ipm", type=int, default=0,

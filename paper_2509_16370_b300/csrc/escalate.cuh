@@ -90,8 +90,10 @@ __device__ void esc_symmetrize(double *X, int k) {
   __syncthreads();
 }
 
-// solved: the call produced a solution (the status output then also
-// reflects convergence); otherwise the status is the pivot status.  scan:
+// solved: 1 = the call produced a solution (the status output then also
+// reflects convergence); 0 = the status is the pivot status; 2 = the flags
+// and the pivot status only (the call's refinement runs concurrently on
+// another stream, and k_escalate_status writes the status afterwards).  scan:
 // the factor came from the associative scan, whose singular-R marker
 // (InstState::r_singular) is then valid; the sequential paths never write
 // that field, so it is not read for them.
@@ -189,13 +191,27 @@ __global__ void __launch_bounds__(kEscThreads) k_escalate(BatchArgs a, int solve
   if (scan && I.st->r_singular) status = RLQR_ERR_SINGULAR;
   if (tid == 0) {
     I.st->pivot_status = status;
-    if (a.status) {
+    if (a.status && solved != 2) {
       const int conv = I.st->converged;
       a.status[b] = !solved ? status
                             : (status == RLQR_ERR_SINGULAR ? RLQR_ERR_SINGULAR
                                                            : (conv ? status : RLQR_ERR_NOT_CONVERGED));
     }
   }
+}
+
+// The status output of the escalated instances after a concurrent
+// escalation (k_escalate with solved = 2) and refinement have both finished:
+// the FP64 pivot status, or RLQR_ERR_NOT_CONVERGED if the refinement did not
+// converge.  One thread per instance.
+__global__ void k_escalate_status(BatchArgs a) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.count || !a.status) return;
+  const Inst I = get_inst(a, b);
+  if (!I.st->escalated) return;
+  const int32_t ps = I.st->pivot_status;
+  a.status[b] = ps == RLQR_ERR_SINGULAR ? RLQR_ERR_SINGULAR
+                                        : (I.st->converged ? ps : RLQR_ERR_NOT_CONVERGED);
 }
 
 }  // namespace rlqr

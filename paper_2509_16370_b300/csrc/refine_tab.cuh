@@ -256,7 +256,9 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
   __syncwarp();
 
   // ---------------- forward rollout, FP64 update of z and of the residual
-  unsigned long long rbits = 0, zbits = 0, dzbits = 0;
+  // sbits: max over the updated rows of sum |coefficient| |dz term| (FP32),
+  // which bounds the rounding of this pass's FP32 residual update
+  unsigned long long rbits = 0, zbits = 0, sbits = 0;
   // this lane's row of K dz: coefficient rows (offsets into a slot) of dx_k,
   // du_k, dy_{k+1}, and its FP64 iterate / residual entries
   const bool xr_ = lane < n, ur_ = lane >= n && lane < n + m, cr_ = lane >= n + m && lane < RS;
@@ -338,7 +340,6 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
     I.x[lane] = xv;
     I.y[lane] = yv;
     zbits = max(zbits, max(abs_bits(xv), abs_bits(yv)));
-    dzbits = max(dzbits, max(abs_bits(widen(dxv)), abs_bits(widen(dyv))));
     const double r0 = __ldcg(rc + lane) - widen(dxv) - delta64 * widen(dyv);
     rc[lane] = r0;
     rbits = max(rbits, abs_bits(r0));
@@ -405,22 +406,33 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
       ld_seg<U2, 0, U2>(c2, a2);
       ld_seg<H2, 0, H2>(c3, a3);
       ld_seg<H2, 0, H2>(dyn, y3);
-      float2 acc = mul2(a1[0], xr[0]);
+      float2 acc = mul2(a1[0], xr[0]), sab = mul2(abs2(a1[0]), abs2(xr[0]));
 #pragma unroll
-      for (int q = 1; q < H2; ++q) acc = fma2(a1[q], xr[q], acc);
+      for (int q = 1; q < H2; ++q) {
+        acc = fma2(a1[q], xr[q], acc);
+        sab = fma2(abs2(a1[q]), abs2(xr[q]), sab);
+      }
 #pragma unroll
-      for (int q = 0; q < U2; ++q) acc = fma2(a2[q], ur[q], acc);
+      for (int q = 0; q < U2; ++q) {
+        acc = fma2(a2[q], ur[q], acc);
+        sab = fma2(abs2(a2[q]), abs2(ur[q]), sab);
+      }
 #pragma unroll
-      for (int q = 0; q < H2; ++q) acc = fma2(a3[q], y3[q], acc);
-      float t = acc.x + acc.y, dz;
+      for (int q = 0; q < H2; ++q) {
+        acc = fma2(a3[q], y3[q], acc);
+        sab = fma2(abs2(a3[q]), abs2(y3[q]), sab);
+      }
+      float t = acc.x + acc.y, sa = sab.x + sab.y, dz;
       if (xr_) {
         t -= dy[lane];
+        sa += fabsf(dy[lane]);
         dz = dxn[lane];
       } else if (ur_) {
         dz = s.du[lane - n];
       } else {
         const int i = lane - n - m;
         t -= fmaf(delta, dyn[i], dxn[i]);
+        sa += fmaf(delta, fabsf(dyn[i]), fabsf(dxn[i]));
         dz = dyn[i];
       }
       const double zv = f.z[lane] + widen(dz), rv = f.res[lane] + widen(t);
@@ -428,7 +440,7 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
       resp[(size_t)k * rs] = rv;
       zbits = max(zbits, abs_bits(zv));
       rbits = max(rbits, abs_bits(rv));
-      dzbits = max(dzbits, abs_bits(widen(dz)));
+      sbits = max(sbits, abs_bits(widen(sa)));
     }
     float *t1 = dx; dx = dxn; dxn = t1;
     float *t2 = dy; dy = dyn; dyn = t2;
@@ -437,28 +449,36 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
   cp_async_wait<0>();
   // terminal rows x_N: res += Q_N dx_N - dy_N (Q_N upper triangle, FP64 data)
   if (lane < n) {
-    float t = -dy[lane];
+    float t = -dy[lane], sa = fabsf(dy[lane]);
     const double *QN = I.Q + (size_t)N * nn;
 #pragma unroll 4
-    for (int j = 0; j < n; ++j)
-      t = fmaf(f64_to_f32_rz(__ldg(QN + min(lane, j) * n + max(lane, j))), dx[j], t);
+    for (int j = 0; j < n; ++j) {
+      const float qv = f64_to_f32_rz(__ldg(QN + min(lane, j) * n + max(lane, j)));
+      t = fmaf(qv, dx[j], t);
+      sa = fmaf(fabsf(qv), fabsf(dx[j]), sa);
+    }
     double *dst = rq + (size_t)N * n + lane;
     const double nv = __ldcg(dst) + widen(t);
     *dst = nv;
     rbits = max(rbits, abs_bits(nv));
+    sbits = max(sbits, abs_bits(widen(sa)));
   }
   for (int o = 16; o > 0; o >>= 1) {
     rbits = max(rbits, __shfl_xor_sync(0xffffffffu, rbits, o));
     zbits = max(zbits, __shfl_xor_sync(0xffffffffu, zbits, o));
-    dzbits = max(dzbits, __shfl_xor_sync(0xffffffffu, dzbits, o));
+    sbits = max(sbits, __shfl_xor_sync(0xffffffffu, sbits, o));
   }
   if (lane == 0) {
     const double rmax = bits_to_double(rbits), zmax = bits_to_double(zbits);
-    // the FP32 products of this pass's residual update (and the FP32 copies
-    // of the data) err by at most 2 gamma_RS ||K||_inf max|dz| per entry,
-    // gamma_RS = RS u_32; the bound accumulates over passes, and the
-    // backward error reported (and tested against tol) includes it
-    stp->upd += 2.0 * RS * 0x1p-24 * stp->kmax * bits_to_double(dzbits);
+    // Rounding of this pass's FP32 residual update, row by row: at most
+    // RS + 3 rounded operations and coefficients truncated to FP32 (relative
+    // error below 2 u_32) give |error| <= (RS + 6) u_32 S_row (1 + O(u_32)),
+    // S_row = sum |coefficient| |dz term|; S_row itself is computed in FP32
+    // (relative error below (RS + 3) u_32).  (RS + 8) u_32 (1 + 2^-16)
+    // max_row S_row therefore bounds the update's error in every entry.  The
+    // bound accumulates over passes, and the backward error reported (and
+    // tested against tol) includes it.
+    stp->upd += (double)(RS + 8) * 0x1p-24 * (1.0 + 0x1p-16) * bits_to_double(sbits);
     const double den = stp->kmax * zmax + stp->bmax;
     const double rel = den > 0.0 ? (rmax + stp->upd) / den : rmax + stp->upd;
     stp->rmax = rmax;

@@ -197,6 +197,10 @@ struct ClassStreams {
   bool ok = false;
   cudaStream_t st[kNumClasses];
   cudaEvent_t fork, join[kNumClasses];
+  // the FP64 re-decision of escalated certificates, concurrent with the
+  // refinement passes
+  cudaStream_t esc;
+  cudaEvent_t esc_fork, esc_join;
 };
 constexpr int kMaxClassDevices = 64;
 static ClassStreams g_class_streams[kMaxClassDevices];
@@ -212,7 +216,11 @@ static ClassStreams *class_streams_locked() {
           cudaEventCreateWithFlags(&cs.join[c], cudaEventDisableTiming) != cudaSuccess)
         return nullptr;
     }
-    if (cudaEventCreateWithFlags(&cs.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&cs.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cs.esc, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&cs.esc_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&cs.esc_join, cudaEventDisableTiming) != cudaSuccess)
+      return nullptr;
     cs.ok = true;
   }
   return &cs;
@@ -637,6 +645,7 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
     cs = class_streams_locked();
   }
   auto gstream = [&](int g) { return cs ? cs->st[g] : s; };
+  bool esc_pending = false;  // k_escalate running on cs->esc
   auto fork = [&]() -> bool {
     if (!cs) return true;
     if (cudaEventRecord(cs->fork, s) != cudaSuccess) return false;
@@ -676,7 +685,23 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
     const int route = uniform ? residual_route(nmaxN, nmax, mmax, a.tsize, B.count) : 0;
     e = uniform ? launch_first_residual(a, nmax, mmax, mixed, 1, spre, items, s, route)
                 : launch_grid_residual(a, spre, items, mixed, 1, s);
-    if (e == cudaSuccess && mixed) e = launch_escalate(a, nmax, mmax, 1, 0, s);
+    if (e == cudaSuccess && mixed) {
+      if (cs && opts->max_refine > 0) {
+        // the FP64 re-decision changes only flags and pivot status, which
+        // the refinement does not read: it runs beside the refinement
+        // passes on its own stream (joined, with the status of the
+        // escalated instances, after the last pass)
+        if (cudaEventRecord(cs->esc_fork, s) != cudaSuccess ||
+            cudaStreamWaitEvent(cs->esc, cs->esc_fork, 0) != cudaSuccess)
+          return RLQR_ERR_CUDA;
+        e = launch_escalate(a, nmax, mmax, 2, 0, cs->esc);
+        if (e == cudaSuccess && cudaEventRecord(cs->esc_join, cs->esc) != cudaSuccess)
+          e = cudaErrorUnknown;
+        esc_pending = true;
+      } else {
+        e = launch_escalate(a, nmax, mmax, 1, 0, s);
+      }
+    }
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
   }
   if (mixed) {
@@ -703,6 +728,12 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
       e = launch_recheck(a, nmax, mmax, spre, items, s, route, uniform);
       if (e != cudaSuccess) return RLQR_ERR_CUDA;
     }
+  }
+  if (esc_pending) {
+    if (cudaStreamWaitEvent(s, cs->esc_join, 0) != cudaSuccess) return RLQR_ERR_CUDA;
+    LaunchScope ls("k_escalate", s);
+    k_escalate_status<<<(B.count + 255) / 256, 256, 0, s>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return RLQR_ERR_CUDA;
   }
   return RLQR_OK;
 }
