@@ -530,6 +530,104 @@ def run_ipm(args):
     print(json.dumps(line), flush=True)
 
 
+def wilson(k, n, z=1.96):
+    """Wilson score interval of a binomial proportion k / n (95 %)."""
+    if n == 0:
+        return None
+    p = k / n
+    d = 1.0 + z * z / n
+    c = (p + z * z / (2 * n)) / d
+    h = z * np.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / d
+    return [round(float(c - h), 4), round(float(c + h), 4)]
+
+
+def run_ipm_study(args):
+    """Why cold IPM solves stop short: one JSON line for the first K
+    cart-double-pendulum instances (cold start, the default options, 300
+    iterations).  Reports the converged share with its 95 % Wilson interval,
+    the iteration quantiles of the converged instances, the final KKT error,
+    dynamics defect (max |c| of the last Newton system, the linearization's
+    own residual) and bound violation of the rest, whether the zero-force
+    rollout of the initial point stays inside the bounds (then the problem
+    has a feasible point and a stop is not infeasibility), and the share of
+    the non-converged instances that converge when the same start is given
+    1000 iterations, a doubled force bound, a doubled cart bound or a
+    doubled horizon."""
+    import torch
+    from paper_2509_16370_b300 import inputs, ipm
+    count = args.ipm_study
+    x0, xg = inputs.workload5(count)
+    base = dict(inputs.CDP_MODEL)
+
+    def solve(idx, max_iter=300, **mk):
+        model = ipm.make_model(**mk)
+        opts = ipm.make_ipm_opts(max_iter=max_iter)
+        st = ipm.IpmState(len(idx), model.N)
+        ws = ipm.alloc_ipm_workspace(len(idx), model, opts)
+        dx0 = torch.from_numpy(x0[idx]).cuda().contiguous()
+        dxg = torch.from_numpy(xg[idx]).cuda().contiguous()
+        ipm.rlqr_ipm_init(model, opts, dx0, st)
+        X_init = st.X.clone()
+        t0 = time.perf_counter()
+        ipm.rlqr_ipm_solve(model, opts, dx0, dxg, st, ws)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        v = ipm.rlqr_ipm_lqr_view(model, opts, st, ws)
+        return dict(model=model, st=st, X_init=X_init.cpu().numpy(),
+                    status=st.status.cpu().numpy(), iters=st.iters.cpu().numpy(),
+                    kkt=st.kkt.cpu().numpy(), defect=v["c"].abs().amax(dim=(1, 2)).cpu().numpy(),
+                    X=st.X.cpu().numpy(), U=st.U.cpu().numpy(), seconds=el)
+
+    idx = np.arange(count)
+    r = solve(idx)
+    conv = r["status"] == ipm.CONVERGED
+    nc = np.flatnonzero(~conv)
+    pmax, umax = base["p_max"], base["u_max"]
+    bound_viol = np.maximum(np.maximum(np.abs(r["U"]).max(1) - umax,
+                                       np.abs(r["X"][:, :, 0]).max(1) - pmax), 0.0)
+    init_inside = np.abs(r["X_init"][:, :, 0]).max(1) <= pmax
+
+    def q(v):
+        v = np.asarray(v, dtype=float)
+        if v.size == 0:
+            return None
+        return {k: float(np.quantile(v, p)) for k, p in
+                (("min", 0.0), ("q10", 0.1), ("median", 0.5), ("q90", 0.9), ("max", 1.0))}
+
+    relaxed = {}
+    if nc.size:
+        for name, kw in (("iterations_1000", dict(max_iter=1000)),
+                         ("u_max_x2", dict(u_max=2 * umax)),
+                         ("p_max_x2", dict(p_max=2 * pmax)),
+                         ("horizon_x2", dict(N=2 * base["N"]))):
+            mi = kw.pop("max_iter", 300)
+            rr = solve(nc, max_iter=mi, **kw)
+            k = int((rr["status"] == ipm.CONVERGED).sum())
+            relaxed[name] = {"converged": k, "of": int(nc.size),
+                             "fraction": round(k / nc.size, 4), "ci95": wilson(k, nc.size),
+                             "mean_iterations_converged":
+                                 float(rr["iters"][rr["status"] == ipm.CONVERGED].mean())
+                                 if k else None}
+    line = {"metric": "IPM cold-start convergence study (cart-double-pendulum)",
+            "config": {"workload": f"the first {count} cart-double-pendulum instances, N=128, "
+                                   "n_x=6, n_u=1, RK4 dt=0.02, |u|<=20, |p|<=2, angles U[-pi,pi]",
+                       "max_iter": 300, "tol": 1e-6},
+            "converged": int(conv.sum()), "instances": count,
+            "converged_fraction": round(float(conv.mean()), 4),
+            "converged_ci95": wilson(int(conv.sum()), count),
+            "status_counts": {k: int((r["status"] == v).sum()) for k, v in
+                              (("converged", ipm.CONVERGED), ("iteration_limit", ipm.ITERATION_LIMIT),
+                               ("rho_limit", ipm.RHO_LIMIT))},
+            "iterations_converged": q(r["iters"][conv]),
+            "not_converged": {"final_kkt": q(r["kkt"][nc]), "dynamics_defect": q(r["defect"][nc]),
+                              "bound_violation": q(bound_viol[nc])},
+            "zero_force_rollout_inside_bounds": {"all": int(init_inside.sum()),
+                                                 "not_converged": int(init_inside[nc].sum())},
+            "relaxed_from_the_same_start": relaxed,
+            "seconds_cold_solve": round(r["seconds"], 3)}
+    print(json.dumps(line), flush=True)
+
+
 def run_warm_start(args):
     """One JSON line for the learned warm start of the IPM: cold-start solves
     of the first K cart-double-pendulum instances give the training set (the
@@ -1088,6 +1186,8 @@ def main():
                     help="cross-stage variables: time rlqr_solve_cross with p = CROSS")
     ap.add_argument("--ipm", type=int, default=0,
                     help="the regularized IPM on the first IPM cart-double-pendulum instances")
+    ap.add_argument("--ipm-study", type=int, default=0,
+                    help="why cold IPM solves stop short, on the first K instances")
     ap.add_argument("--diag", action="store_true",
                     help="general diagonal Delta_i: rlqr_solve_diag beside the scalar-delta solve")
     ap.add_argument("--warm-start", type=int, default=0,
@@ -1125,6 +1225,8 @@ def main():
         run_cross(args)
     elif args.ipm:
         run_ipm(args)
+    elif args.ipm_study:
+        run_ipm_study(args)
     elif args.warm_start:
         run_warm_start(args)
     elif args.diag:

@@ -100,12 +100,7 @@ typedef struct {
 
 /* Device pointers into the workspace: the LQR data and solution of the last
  * Newton system (same layouts as rlqr_problem, instance-major with stride
- * of one instance, nx = 6), for inspection.  The LQR has nu = 2: the force
- * and a decoupled dummy control (zero columns of B and M, R = diag(R_uu, 1),
- * r = 0; its solution component is 0 and the control pivot is
- * diag(G_11, 1), so the Newton step and the certificate are those of the
- * one-control system), which lets the batched solve take the FP32
- * block-pivot warp sweep. */
+ * of one instance, nx = 6, nu = 1), for inspection. */
 typedef struct {
   double *Q, *M, *R, *q, *r, *A, *B, *c, *dx, *du, *dy;
   uint8_t *pivot_pd;

@@ -19,12 +19,9 @@ namespace rlqr {
 namespace ipm {
 
 constexpr int kThreads = 128;  // CTA size of the per-instance kernels
-// Control dimension of the LQR data: the force plus a decoupled dummy control
-// (zero columns of B and M, R = diag(R_uu, 1), r = 0, so its component of
-// every solution is 0 and the control pivot is diag(G_11, 1): the same
-// Newton step and certificate), which routes the batched solve to the FP32
-// block-pivot warp sweep (it needs an even control dimension).
-constexpr int kNu = 2;
+// Control dimension of the LQR data: the cart force (the batched solve takes
+// the FP32 tableau sweep and the float-float warp residual at (6, 1)).
+constexpr int kNu = 1;
 constexpr int kMaxN = 4096;
 constexpr size_t kAlignB = 256;
 
@@ -268,12 +265,8 @@ __global__ void __launch_bounds__(kThreads)
         q[i * 6 + j] = md.wx[j] * (X[i * 6 + j] - xg[j]) + gj - Y[i * 6 + j];
       } else {
 #pragma unroll
-        for (int l = 0; l < 6; ++l) {
-          B[(i * 6 + l) * kNu] = o[l].d;
-          B[(i * 6 + l) * kNu + 1] = 0.0;
-        }
+        for (int l = 0; l < 6; ++l) B[(i * 6 + l) * kNu] = o[l].d;
         r[i * kNu] = md.wu * U[i] + gj + Z[i * 4 + 0] - Z[i * 4 + 1];
-        r[i * kNu + 1] = 0.0;
       }
     }
     __syncthreads();
@@ -322,13 +315,6 @@ __global__ void __launch_bounds__(kThreads)
     for (int e = threadIdx.x; e < 36 * N; e += kThreads) Q[e] = 0.0;
     for (int e = threadIdx.x; e < 6 * N; e += kThreads) Mx[e * kNu] = 0.0;
     for (int e = threadIdx.x; e < N; e += kThreads) R[e * kNu * kNu] = 0.0;
-  }
-  // the dummy control: zero column of M, R row / column (0, 1)
-  for (int e = threadIdx.x; e < 6 * N; e += kThreads) Mx[e * kNu + 1] = 0.0;
-  for (int i = threadIdx.x; i < N; i += kThreads) {
-    R[i * 4 + 1] = 0.0;
-    R[i * 4 + 2] = 0.0;
-    R[i * 4 + 3] = 1.0;
   }
   __syncthreads();
 
@@ -415,7 +401,7 @@ __global__ void __launch_bounds__(kThreads)
     q[i * 6] += Dg[2] * rz[2] - Dg[3] * rz[3];
     if (i < N) {
       cst += md.wu * u * u;
-      R[i * 4] += md.wu + rho0 + Dg[0] + Dg[1];
+      R[i * kNu * kNu] += md.wu + rho0 + Dg[0] + Dg[1];
       r[i * kNu] += Dg[0] * rz[0] - Dg[1] * rz[1];
     }
     macc += 0.5 * cst;

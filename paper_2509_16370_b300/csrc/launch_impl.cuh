@@ -9,7 +9,6 @@
 #include "seq.cuh"
 #include "seq_warp.cuh"
 #include "sweep32.cuh"
-#include "refine32.cuh"
 #include "residual32.cuh"
 #include "seqx.cuh"
 #include "tab32.cuh"
@@ -220,7 +219,7 @@ cudaError_t launch_residual32(int n, int m, bool uniform, const BatchArgs &a, in
                               cudaStream_t s) {
   if (uniform) {
 #define RLQR_RES32(NX, NU)                                                   \
-    if constexpr (sweep32_fits<NX, NU>()) {                                  \
+    if constexpr (res32_fits<NX, NU>()) {                                    \
       if (n == NX && m == NU) {                                              \
         auto kern = k_res32<NX, NU>;                                         \
         const size_t bytes = sizeof(Rs32Warp<NX, NU>) * kResWarps;           \

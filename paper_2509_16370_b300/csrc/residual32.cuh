@@ -3,6 +3,10 @@
 // float-float arithmetic on the FP32 pipes, plus the FP64 certificate of the
 // control pivots G_i stored by the FP32 sweep.
 //
+// Sizes: n even, 2n + m <= 32 (one lane per row of a stage), m <= 8; an odd m
+// runs its control segments padded to m + 1 with zero coefficients and zero
+// z entries (the pad stays zero in shared memory).
+//
 // One CTA of RW warps per instance; warp w takes stages w, w + RW, ... and
 // loads stage s + RW into registers while it computes stage s.  The rows of
 // K z + b of stage s (same layout as k_residual in residual.cuh):
@@ -54,6 +58,11 @@ struct Rs32Warp {
 };
 
 constexpr int kResWarps = 4;
+
+template <int NX, int NU>
+constexpr bool res32_fits() {
+  return NX % 2 == 0 && NX >= 2 && NU >= 1 && NU <= 8 && 2 * NX + NU <= 32;
+}
 
 // Packed float-float accumulation of two terms: (sh, sl) += (ah + al)(zh + zl)
 // elementwise, zhn = -zh.  The product's rounding error comes from an FMA
@@ -134,8 +143,10 @@ __global__ void __launch_bounds__(32 * kResWarps) k_res32(BatchArgs a, int store
 template <int NX, int NU>
 __device__ __forceinline__ void res32_instance(const BatchArgs &a, int slot, int store, int cert_g,
                                                unsigned char *smem_raw) {
+  static_assert(res32_fits<NX, NU>(), "dimensions outside the warp residual");
   constexpr int n = NX, m = NU, nn = n * n, nm = n * m, mmm = m * m;
-  constexpr int H2 = n / 2, M2 = m / 2, RS = 2 * n + m;
+  constexpr int ME = m + (m & 1);  // control segments padded to an even length
+  constexpr int H2 = n / 2, M2 = ME / 2, RS = 2 * n + m;
   using SW = Rs32Warp<NX, NU>;
   constexpr int N4 = SW::N4, M4 = SW::M4;
   __shared__ double s_red[32];
@@ -144,6 +155,11 @@ __device__ __forceinline__ void res32_instance(const BatchArgs &a, int slot, int
   const int b = inst_of(a, slot);
   const Inst I = get_inst(a, b);
   if (a.recheck && (I.st->converged || I.st->pivot_status == RLQR_ERR_SINGULAR)) return;
+  if constexpr (ME != m) {
+    // the pad column of the control segments reads zeros
+    float4 *z4 = reinterpret_cast<float4 *>(&s);
+    for (int e = lane; e < (int)(sizeof(SW) / 16); e += 32) z4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   const int N = I.N;
   const double delta = I.delta;
   double *rq = reinterpret_cast<double *>(I.ws + I.L.res);
@@ -271,14 +287,14 @@ __device__ __forceinline__ void res32_instance(const BatchArgs &a, int slot, int
       }
       {
         float2 ch[M2], cl[M2], zh[M2], zl[M2];
-        lds_row2<m>(s2h, ch);
-        lds_row2<m>(s2l, cl);
-        lds_row2<m>(s.uh, zh);
-        lds_row2<m>(s.ul, zl);
+        lds_row2<ME>(s2h, ch);
+        lds_row2<ME>(s2l, cl);
+        lds_row2<ME>(s.uh, zh);
+        lds_row2<ME>(s.ul, zl);
 #pragma unroll
         for (int q = 0; q < M2; ++q)
           ff2_fma(sh, sl, ch[q], cl[q], zh[q], make_float2(-zh[q].x, -zh[q].y), zl[q]);
-        ka = abs_sum2<m>(ch, ka);
+        ka = abs_sum2<ME>(ch, ka);
       }
       {
         float2 ch[H2], cl[H2], zh[H2], zl[H2];

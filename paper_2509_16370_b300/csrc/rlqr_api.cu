@@ -64,11 +64,11 @@ static cudaError_t launch_grid_residual(const BatchArgs &a, const int64_t *spre,
 
 // First residual of a uniform launch group (or one instance): stored for the
 // refinement and certifying the control pivots when cert_g (mixed), or the
-// FP64 backward error only.  The sizes of the FP32 warp sweep take the
+// FP64 backward error only.  The sizes of the FP32 warp sweeps take the
 // float-float warp residual (mixed) or the generic FP64 one; the rest take
 // the stage-parallel grid residual.
-static bool warp_sweep32_size(int n, int m) {
-  return (n == 4 && m == 2) || (n == 6 && m == 2) || (n == 12 && m == 4);
+static bool warp_res32_size(int n, int m) {
+  return ((n == 4 || n == 6) && (m == 1 || m == 2)) || (n == 12 && (m == 3 || m == 4));
 }
 
 // Residual route of a uniform launch group of a warp size: 0 = by size (the
@@ -98,7 +98,7 @@ static int residual_route(int N, int n, int m, int tsize, int count) {
 static cudaError_t launch_first_residual(const BatchArgs &a, int n, int m, bool mixed, int cert_g,
                                          const int64_t *spre, int64_t items, cudaStream_t s,
                                          int route = 0) {
-  if (!warp_sweep32_size(n, m) || (route == 2 && spre))
+  if (!warp_res32_size(n, m) || (route == 2 && spre))
     return launch_grid_residual(a, spre, items, mixed, cert_g, s);
   if (mixed) return launch_residual32<float>(n, m, true, a, cert_g, s);
   return launch_residual(a, 2 * n + m, 0, nullptr, nullptr, 1, 0, s);
@@ -1088,7 +1088,7 @@ static bool batch_tune_key(const rlqr_batch *batch, const rlqr_opts *opts, uint6
     if (batch->h_nx[b] != batch->h_nx[0] || batch->h_nu[b] != batch->h_nu[0]) return false;
     nmaxN = std::max(nmaxN, batch->h_N[b]);
   }
-  if (!warp_sweep32_size(batch->h_nx[0], batch->h_nu[0])) return false;
+  if (!warp_res32_size(batch->h_nx[0], batch->h_nu[0])) return false;
   *key = route_key(nmaxN, batch->h_nx[0], batch->h_nu[0], opts->prec == RLQR_MIXED ? 4 : 8,
                    batch->count);
   return true;

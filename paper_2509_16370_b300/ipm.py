@@ -172,16 +172,15 @@ def rlqr_ipm_solve(model, opts, x0, xg, state: IpmState, ws, stream=None) -> int
 
 def rlqr_ipm_lqr_view(model, opts, state: IpmState, ws) -> dict:
     """Torch views of the LQR data of the last Newton system in the workspace
-    (instance-major: Q (count, N+1, 6, 6), M (count, N, 6, 2), ...; the
-    second control is the decoupled dummy of include/rlqr_ipm.h)."""
+    (instance-major: Q (count, N+1, 6, 6), M (count, N, 6, 1), ...)."""
     out = rlqr_ipm_lqr()
     p, _ = _aligned(ws)
     _check(lib.rlqr_ipm_lqr_view(state.count, ctypes.byref(model), ctypes.byref(opts), p,
                                  ctypes.byref(out)), "rlqr_ipm_lqr_view")
     C, N = state.count, state.N
-    shapes = dict(Q=(C, N + 1, 6, 6), M=(C, N, 6, 2), R=(C, N, 2, 2), q=(C, N + 1, 6),
-                  r=(C, N, 2), A=(C, N, 6, 6), B=(C, N, 6, 2), c=(C, N + 1, 6),
-                  dx=(C, N + 1, 6), du=(C, N, 2), dy=(C, N + 1, 6))
+    shapes = dict(Q=(C, N + 1, 6, 6), M=(C, N, 6, 1), R=(C, N, 1, 1), q=(C, N + 1, 6),
+                  r=(C, N, 1), A=(C, N, 6, 6), B=(C, N, 6, 1), c=(C, N + 1, 6),
+                  dx=(C, N + 1, 6), du=(C, N, 1), dy=(C, N + 1, 6))
     base = ws.data_ptr()
     views = {}
     for k, shp in shapes.items():
