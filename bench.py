@@ -138,8 +138,13 @@ class ClockSampler:
 # DRAM bytes (read + write) per instance-stage of each kernel, from one ncu
 # capture of the 296-instance case of this workload (the kernels as they are
 # in this source; see profiles/), scaled by the stages a launch processes.
-TRAFFIC_PER_STAGE = {"k_seq_fp32_solve": 7475.0, "k_residual_ff": 3924.0,
-                     "k_solve_refine": 4353.0}
+TRAFFIC_PER_STAGE = {"k_seq_fp32_solve": 7476.0, "k_residual_ff": 3920.0,
+                     "k_solve_refine": 4342.0}
+# Warp instructions per instance-stage of the FP32 warp sweep (backward +
+# forward) from the same capture: the length of one instance's instruction
+# stream, which one warp must issue in order.
+SWEEP_INSTR_PER_STAGE = {"k_seq_fp32_solve": 1536.0}
+SM_COUNT, SMSP_PER_SM = 148, 4
 
 
 def kernel_models(n, m, stages):
@@ -178,7 +183,28 @@ def seq_flops_per_stage(n, m):
     return 16.0 / 3.0 * n ** 3 + 5.0 * n * n * m + 3.0 * n * m * m + m ** 3 / 3.0
 
 
-def roofline(report, steps, n, m, stages, peaks, fp64_tflops=None):
+def chain_bound(name, launch_ms, N, count, sm_mhz):
+    """The bound of a one-warp-per-instance sweep below HBM: each instance is
+    one warp's in-order instruction stream, and a scheduler issues at most one
+    instruction per cycle, so with the batch's warps spread over the 148 x 4
+    schedulers the busiest scheduler holds ceil(count / 592) of them and a
+    stage cannot take fewer than that many times the stream's instructions
+    per stage in cycles.  frac = that floor / the measured cycles per stage."""
+    ipst = SWEEP_INSTR_PER_STAGE.get(name)
+    if not ipst or not sm_mhz:
+        return None
+    per_sched = -(-count // (SM_COUNT * SMSP_PER_SM))
+    cycles = launch_ms * 1e-3 * sm_mhz * 1e6 / N
+    floor = per_sched * ipst
+    return {"bound": "instruction issue of the per-instance chains",
+            "instr_per_stage": ipst, "warps_on_busiest_scheduler": per_sched,
+            "floor_cycles_per_stage": floor, "cycles_per_stage": round(cycles, 1),
+            "frac": round(floor / cycles, 4),
+            "issue_rate_frac_of_gpu": round(ipst * N * count / (launch_ms * 1e-3) /
+                                            (SM_COUNT * SMSP_PER_SM * sm_mhz * 1e6), 4)}
+
+
+def roofline(report, steps, n, m, stages, peaks, fp64_tflops=None, chain=None):
     k = [(ms, name, cnt) for name, (cnt, ms) in report.items() if name != "k_plan"]
     if not k:
         return None
@@ -196,11 +222,20 @@ def roofline(report, steps, n, m, stages, peaks, fp64_tflops=None):
                     else "derived (148 SM x 2 FP64 FMA/clk x 2032 MHz)")
     total = sum(v[1] for v in report.values())
     traffic = TRAFFIC_PER_STAGE.get(name)
-    return {"kernel": name, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
-            "peak_source": peak_src, "unit": unit, "frac": round(achieved / peak, 4),
-            "traffic": None if traffic is None else traffic * stages,
-            "algorithmic_bytes": work if bound == "hbm" else None,
-            "launch_ms": round(ms / cnt, 4), "share": round(ms / total, 3)}
+    out = {"kernel": name, "bound": bound, "achieved": round(achieved, 3), "peak": peak,
+           "peak_source": peak_src, "unit": unit, "frac": round(achieved / peak, 4),
+           "traffic": None if traffic is None else traffic * stages,
+           "algorithmic_bytes": work if bound == "hbm" else None,
+           "launch_ms": round(ms / cnt, 4), "share": round(ms / total, 3)}
+    if chain:
+        N, count, sm_mhz = chain
+        cb = chain_bound(name, ms / cnt, N, count, sm_mhz)
+        if cb:
+            # the kernel is bound by its chains, not by HBM: the HBM fraction
+            # stays the reported one, and it is far from one half
+            out["chain"] = cb
+            out["hbm_frac_at_least_half"] = bool(achieved / peak >= 0.5) if bound == "hbm" else None
+    return out
 
 
 def fp64_sweep_roofline(report, n, m, stages, pipes):
@@ -1124,7 +1159,8 @@ def run_ours(args):
         "data": "synthetic", "config": dict(WORKLOAD, parallelism=f"replicas x{world}",
                                               precision="mixed", max_refine=3, tol=TOL,
                                               autotune=tune),
-        "roofline": roofline(report, args.steps, n, m, stages, load_peaks(), pipes["fp64_tflops"]),
+        "roofline": roofline(report, args.steps, n, m, stages, load_peaks(), pipes["fp64_tflops"],
+                             chain=(N, B, clk.summary().get("sm_mhz"))),
         "pipes": {k: round(v, 2) for k, v in pipes.items()},
         "kernels": {k: {"launches": c, "ms_total": round(t, 4)} for k, (c, t) in report.items()},
         "gpu_launches": launches,

@@ -25,11 +25,15 @@
 // three digits (I + C_ij P_jk of a chunk interval has condition ~1e4-1e5 on
 // the test problems), while the sequential recursion contracts an error in
 // its starting P strongly (1e-3 -> 3e-6 over 8 stages there).  The mixed path
-// therefore runs the finalize twice: a P-only pass from the scanned
-// boundaries gives every chunk's P at its first stage, and the full pass of
-// chunk c starts from chunk c+1's value, so that each boundary error has been
-// contracted by one chunk of the sequential recursion.  The FP64 scan is
-// accurate to ~1e-11 and finalizes directly.
+// therefore runs the finalize twice: a P-only pass gives every chunk's P at
+// its first stage, and the full pass of chunk c starts from chunk c+1's value,
+// so that each boundary error has been contracted by the sequential
+// recursion.  The contraction needs only a few stages (1e-3 -> 3e-6 in 8
+// stages on the n = 32 test), so a chunk longer than kInnerK stages also gets
+// the element of its stages [s + kInnerK, e) from the fold (SI), composed with
+// the next chunk's suffix element by k_scan_inner into P at s + kInnerK (PI),
+// and its P-only pass runs the kInnerK stages from there to s only.  The FP64
+// scan is accurate to ~1e-11 and finalizes directly.
 // The vector passes (scan_vec.cuh) use Phi_c for p (p_s = Phi_c p_e + phi_c)
 // and Phi_c^T for x (x_e = Phi_c^T x_s + psi_c, since the x map of a stage,
 // (I - delta W_{i+1})(A_i + B_i K_i), is F_i^T for symmetric W).
@@ -54,8 +58,14 @@ struct ScanLayout {
   size_t xb;       // (C+1) x n  x at the chunk starts (index C: x_N)
   size_t PstA;     // C x n^2    P at the chunk starts from the P-only pass (mixed path)
   size_t PstB;     // C x n^2    P at the chunk starts from the final pass
+  size_t SI;       // C x 3 n^2  elements of stages [s + kInnerK, e) (mixed path)
+  size_t PI;       // C x n^2    P at s + kInnerK (mixed path)
   size_t total;    // bytes after `base`
 };
+
+// Stages of the P-only pass of a chunk longer than this (see above).
+constexpr int kInnerK = 16;
+__host__ __device__ inline bool chunk_has_inner(int len) { return len > kInnerK; }
 
 __host__ __device__ inline ScanLayout scan_layout(int N, int n, int L, int tsize) {
   ScanLayout S;
@@ -81,6 +91,13 @@ __host__ __device__ inline ScanLayout scan_layout(int N, int n, int L, int tsize
   o = align_up(o + C * nn * tsize);
   S.PstB = o;
   o = align_up(o + C * nn * tsize);
+  // (sized for every chunking of the mixed path, so that the layout grows
+  // with the chunk count and the largest count bounds every other)
+  const bool inner = tsize == 4;
+  S.SI = o;
+  o = align_up(o + (inner ? C * 3 * nn * tsize : 0));
+  S.PI = o;
+  o = align_up(o + (inner ? C * nn * tsize : 0));
   S.total = o;
   return S;
 }
@@ -447,10 +464,13 @@ __device__ __forceinline__ void store_elem(T *g, const T *P, const T *A, const T
 // Chunk elements into S0 (blocks 0..C-1) and the terminal element (block C).
 // ident_terminal: block C writes the identity element (0, I, 0) instead, so
 // that the suffix scan's first entry is the interval element of stages
-// 0..N-1 alone (a horizon shard's summary).
+// 0..N-1 alone (a horizon shard's summary).  inner: a chunk longer than
+// kInnerK also stores the element of its stages [s + kInnerK, e) into SI.
+// Three CTAs per SM in FP32 (the chunk count is sized for one wave of them):
+// the register cap keeps the compiler from trading occupancy for ILP.
 template <typename T, int NX, int NU>
-__global__ void __launch_bounds__(scan::kTH) k_scan_reduce(BatchArgs a, ScanLayout SL,
-                                                           size_t sbase, int ident_terminal) {
+__global__ void __launch_bounds__(scan::kTH, sizeof(T) == 4 ? 3 : 1)
+    k_scan_reduce(BatchArgs a, ScanLayout SL, size_t sbase, int ident_terminal, int inner) {
   using SM = scan::CombSmem<T, NX, NU>;
   constexpr int n = NX, nn = n * n, LD = SM::LD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -482,6 +502,9 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_reduce(BatchArgs a, ScanLayo
     return;
   }
   const int s0 = c * SL.L, e0 = min(s0 + SL.L, N);
+  // the inner element [s0 + kInnerK, e0): the accumulator once it reaches ik
+  const int ik = (inner && chunk_has_inner(e0 - s0)) ? s0 + kInnerK : -1;
+  T *sin = reinterpret_cast<T *>(I.ws + sbase + SL.SI) + (size_t)c * 3 * nn;
   // acc (P2, A2, C2) = e_{e0-1}
   scan::stage_element<T, NX, NU>(I, e0 - 1, s);
   for (int e = threadIdx.x; e < nn; e += blockDim.x) {
@@ -489,6 +512,10 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_reduce(BatchArgs a, ScanLayo
     s.P2[o] = s.P1[o];
     s.A2[o] = s.A1[o];
     s.C2[o] = s.C1[o];
+  }
+  if (e0 - 1 == ik) {
+    __syncthreads();
+    scan::store_elem<T, NX>(sin, s.P2, s.A2, s.C2, LD);
   }
   for (int i = e0 - 2; i >= s0; --i) {
     scan::stage_element<T, NX, NU>(I, i, s);
@@ -498,6 +525,10 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_reduce(BatchArgs a, ScanLayo
       s.P2[o] = s.Pn[o];
       s.A2[o] = s.An[o];
       s.C2[o] = s.Cn[o];
+    }
+    if (i == ik) {
+      __syncthreads();
+      scan::store_elem<T, NX>(sin, s.P2, s.A2, s.C2, LD);
     }
   }
   __syncthreads();
@@ -526,6 +557,30 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_level(BatchArgs a, ScanLayou
   scan::load_elem<T, NX>(src + (size_t)(c + d) * 3 * nn, s.P2, s.A2, s.C2, LD);
   scan::combine<T, NX, NU>(s);
   scan::store_elem<T, NX>(dst + (size_t)c * 3 * nn, s.Pn, s.An, s.Cn, LD);
+}
+
+// P at stage s + kInnerK of every chunk with an inner element: (SI[c] (+)
+// suffix element c + 1).P, the value the chunk's P-only pass starts from.
+template <typename T, int NX, int NU>
+__global__ void __launch_bounds__(scan::kTH) k_scan_inner(BatchArgs a, ScanLayout SL, size_t sbase,
+                                                          int from1) {
+  using SM = scan::CombSmem<T, NX, NU>;
+  constexpr int n = NX, nn = n * n, LD = SM::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &s = *reinterpret_cast<SM *>(smem_raw);
+  const Inst I = get_inst(a, 0);
+  const int c = blockIdx.x, s0 = c * SL.L, e0 = min(s0 + SL.L, I.N);
+  if (!chunk_has_inner(e0 - s0)) return;
+  const T *Sfin = reinterpret_cast<const T *>(I.ws + sbase + (from1 ? SL.S1 : SL.S0));
+  const T *sin = reinterpret_cast<const T *>(I.ws + sbase + SL.SI) + (size_t)c * 3 * nn;
+  T *pin = reinterpret_cast<T *>(I.ws + sbase + SL.PI) + (size_t)c * nn;
+  scan::load_elem<T, NX>(sin, s.P1, s.A1, s.C1, LD);
+  scan::load_elem<T, NX>(Sfin + (size_t)(c + 1) * 3 * nn, s.P2, s.A2, s.C2, LD);
+  scan::combine<T, NX, NU>(s);
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    const int r = e / n, col = e - r * n;
+    pin[e] = s.Pn[r * LD + col];
+  }
 }
 
 // Shared memory of the finalize kernel (row stride n + 1).
@@ -587,9 +642,13 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_finalize(BatchArgs a, ScanLa
   T *PstB = reinterpret_cast<T *>(I.ws + sbase + SL.PstB);
 
   // P at the chunk's end: the P of suffix element c + 1 (for the last chunk
-  // the terminal element's Q_N), or in PASS 2 chunk c+1's P-only result
-  const T *Pend = (PASS == 2 && c + 1 < SL.C) ? PstA + (size_t)(c + 1) * nn
-                                              : Sfin + (size_t)(c + 1) * 3 * nn;
+  // the terminal element's Q_N), or in PASS 2 chunk c+1's P-only result.
+  // PASS 1 of a chunk with an inner element starts at s0 + kInnerK instead.
+  const bool from_inner = PASS == 1 && chunk_has_inner(e0 - s0);
+  const T *Pend = from_inner ? reinterpret_cast<const T *>(I.ws + sbase + SL.PI) + (size_t)c * nn
+                  : (PASS == 2 && c + 1 < SL.C) ? PstA + (size_t)(c + 1) * nn
+                                                : Sfin + (size_t)(c + 1) * 3 * nn;
+  const int i_first = from_inner ? s0 + kInnerK - 1 : e0 - 1;
   for (int e = tid; e < nn; e += blockDim.x) {
     const int r = e / n, col = e - r * n;
     s.P[r * LD + col] = Pend[e];
@@ -676,7 +735,7 @@ __global__ void __launch_bounds__(scan::kTH) k_scan_finalize(BatchArgs a, ScanLa
     return s.bit;
   };
 
-  for (int i = e0 - 1; i >= s0; --i) {
+  for (int i = i_first; i >= s0; --i) {
     const int bit0 = state_pivot(gW + (size_t)(i + 1) * nn);
     // the stage's data (and its FP32 copies in the mixed path)
     const double *Q = I.Q + (size_t)i * nn, *A = I.A + (size_t)i * nn;

@@ -29,7 +29,7 @@ static cudaError_t scan_factor_sz(const BatchArgs &a, const ScanLayout &SL, size
     const size_t b = sizeof(scan::CombSmem<T, NX, NU>);
     if ((e = set_smem(k, b)) != cudaSuccess) return e;
     LaunchScope ls("k_scan_reduce", s);
-    k<<<SL.C + 1, scan::kTH, b, s>>>(a, SL, sbase, 0);
+    k<<<SL.C + 1, scan::kTH, b, s>>>(a, SL, sbase, 0, sizeof(T) == 4 ? 1 : 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   int from1 = 0;
@@ -47,11 +47,19 @@ static cudaError_t scan_factor_sz(const BatchArgs &a, const ScanLayout &SL, size
   {
     const size_t b = sizeof(FinSmem<T, NX, NU>);
     if constexpr (sizeof(T) == 4) {
-      // P-only pass, then the full pass from the contracted boundaries
+      // P at s + kInnerK of the long chunks, the P-only pass, then the full
+      // pass from the contracted boundaries
+      auto ki = k_scan_inner<T, NX, NU>;
       auto k1 = k_scan_finalize<T, NX, NU, 1>;
       auto k2 = k_scan_finalize<T, NX, NU, 2>;
+      const size_t bc = sizeof(scan::CombSmem<T, NX, NU>);
+      if ((e = set_smem(ki, bc)) != cudaSuccess) return e;
       if ((e = set_smem(k1, b)) != cudaSuccess) return e;
       if ((e = set_smem(k2, b)) != cudaSuccess) return e;
+      if (chunk_has_inner(SL.L)) {
+        LaunchScope ls("k_scan_level", s);
+        ki<<<SL.C, scan::kTH, bc, s>>>(a, SL, sbase, from1);
+      }
       LaunchScope ls("k_scan_finalize", s);
       k1<<<SL.C, scan::kTH, b, s>>>(a, SL, sbase, from1);
       k2<<<SL.C, scan::kTH, b, s>>>(a, SL, sbase, from1);

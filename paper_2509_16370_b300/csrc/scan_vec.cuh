@@ -191,6 +191,46 @@ __global__ void __launch_bounds__(32) k_scan_pvec(BatchArgs a, ScanLayout SL, si
 }
 
 // p at the chunk starts: pb[C] = q'_N, pb[c] = Phi_c pb[c+1] + phi_c.  One warp.
+// Depth of the register rings of the boundary passes (chunks in flight).
+template <typename T>
+__host__ __device__ constexpr int bound_ring_depth() {
+  return sizeof(T) == 4 ? 4 : 2;
+}
+
+// dst[0..NX) = src[0..NX) (one row, __ldcg), in 16- or 8-byte pieces when the
+// row's size and the address allow.
+template <typename T, int NX>
+__device__ __forceinline__ void ld_vec_row(const T *src, T (&dst)[NX]) {
+  constexpr int BYTES = NX * (int)sizeof(T);
+  const uintptr_t ad = reinterpret_cast<uintptr_t>(src);
+  if constexpr (BYTES % 16 == 0) {
+    if (ad % 16 == 0) {
+      constexpr int V = 16 / (int)sizeof(T);
+#pragma unroll
+      for (int q = 0; q < NX / V; ++q) {
+        const float4 v = __ldcg(reinterpret_cast<const float4 *>(src) + q);
+        const T *pv = reinterpret_cast<const T *>(&v);
+#pragma unroll
+        for (int e = 0; e < V; ++e) dst[q * V + e] = pv[e];
+      }
+      return;
+    }
+  }
+  if constexpr (BYTES % 8 == 0 && sizeof(T) == 4) {
+    if (ad % 8 == 0) {
+#pragma unroll
+      for (int q = 0; q < NX / 2; ++q) {
+        const float2 v = __ldcg(reinterpret_cast<const float2 *>(src) + q);
+        dst[2 * q] = v.x;
+        dst[2 * q + 1] = v.y;
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < NX; ++l) dst[l] = __ldcg(src + l);
+}
+
 template <typename T, int NX, bool FROM_RES>
 __global__ void __launch_bounds__(32) k_scan_pbound(BatchArgs a, ScanLayout SL, size_t sbase) {
   constexpr int n = NX, nn = n * n;
@@ -210,24 +250,37 @@ __global__ void __launch_bounds__(32) k_scan_pbound(BatchArgs a, ScanLayout SL, 
     pb[(size_t)C * n + lane] = q;
     gpv[(size_t)I.N * n + lane] = q;
   }
-  T row[NX];
-  if (lane < n)
-    for (int l = 0; l < n; ++l) row[l] = __ldcg(Phi + (size_t)(C - 1) * nn + lane * n + l);
-  for (int c = C - 1; c >= 0; --c) {
-    T nxt[NX];
-    if (c > 0 && lane < n)
-      for (int l = 0; l < n; ++l) nxt[l] = __ldcg(Phi + (size_t)(c - 1) * nn + lane * n + l);
-    __syncwarp();
-    T t = 0;
-    if (lane < n) {
-      t = __ldcg(phi + (size_t)c * n + lane);
-      for (int l = 0; l < n; ++l) t = fma(row[l], pv[l], t);
+  // row `lane` of Phi_c and phi_c[lane] in a register ring D chunks deep:
+  // the chain over the chunks is one n-term dot product per chunk, far
+  // shorter than a load, so D chunks are in flight
+  constexpr int D = bound_ring_depth<T>();
+  T row[D][NX], off[D];
+  auto fetch = [&](int j, int cc) {
+    if (cc >= 0 && lane < n) {
+      ld_vec_row<T, NX>(Phi + (size_t)cc * nn + lane * n, row[j]);
+      off[j] = __ldcg(phi + (size_t)cc * n + lane);
     }
-    __syncwarp();
-    if (lane < n) {
-      pv[lane] = t;
-      pb[(size_t)c * n + lane] = t;
-      for (int l = 0; l < n; ++l) row[l] = nxt[l];
+  };
+#pragma unroll
+  for (int j = 0; j < D; ++j) fetch(j, C - 1 - j);
+  for (int c0 = C - 1; c0 >= 0; c0 -= D) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const int c = c0 - j;
+      if (c < 0) break;  // uniform over the warp
+      __syncwarp();
+      T t = 0;
+      if (lane < n) {
+        t = off[j];
+#pragma unroll
+        for (int l = 0; l < NX; ++l) t = fma(row[j][l], pv[l], t);
+      }
+      __syncwarp();
+      if (lane < n) {
+        pv[lane] = t;
+        pb[(size_t)c * n + lane] = t;
+      }
+      fetch(j, c - D);
     }
   }
 }
@@ -439,25 +492,37 @@ __global__ void __launch_bounds__(32) k_scan_xbound(BatchArgs a, ScanLayout SL, 
                 max(abs_bits(widen(x0)), abs_bits(widen(y0))));
     }
   }
-  // column `lane` of Phi_c, prefetched one chunk ahead
-  T col[NX];
-  if (lane < n)
-    for (int l = 0; l < n; ++l) col[l] = __ldcg(Phi + l * n + lane);
-  for (int c = 0; c < SL.C; ++c) {
-    T nxt[NX];
-    if (c + 1 < SL.C && lane < n)
-      for (int l = 0; l < n; ++l) nxt[l] = __ldcg(Phi + (size_t)(c + 1) * nn + l * n + lane);
-    __syncwarp();
-    T t = 0;
-    if (lane < n) {
-      t = __ldcg(psi + (size_t)c * n + lane);
-      for (int l = 0; l < n; ++l) t = fma(col[l], xv[l], t);  // (Phi_c^T x)[lane]
+  // column `lane` of Phi_c and psi_c[lane] in a register ring D chunks deep
+  constexpr int D = bound_ring_depth<T>();
+  const int C = SL.C;
+  T col[D][NX], off[D];
+  auto fetch = [&](int j, int cc) {
+    if (cc < C && lane < n) {
+#pragma unroll
+      for (int l = 0; l < NX; ++l) col[j][l] = __ldcg(Phi + (size_t)cc * nn + l * n + lane);
+      off[j] = __ldcg(psi + (size_t)cc * n + lane);
     }
-    __syncwarp();
-    if (lane < n) {
-      xv[lane] = t;
-      xb[(size_t)(c + 1) * n + lane] = t;
-      for (int l = 0; l < n; ++l) col[l] = nxt[l];
+  };
+#pragma unroll
+  for (int j = 0; j < D; ++j) fetch(j, j);
+  for (int c0 = 0; c0 < C; c0 += D) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const int c = c0 + j;
+      if (c >= C) break;  // uniform over the warp
+      __syncwarp();
+      T t = 0;
+      if (lane < n) {
+        t = off[j];
+#pragma unroll
+        for (int l = 0; l < NX; ++l) t = fma(col[j][l], xv[l], t);  // (Phi_c^T x)[lane]
+      }
+      __syncwarp();
+      if (lane < n) {
+        xv[lane] = t;
+        xb[(size_t)(c + 1) * n + lane] = t;
+      }
+      fetch(j, c + D);
     }
   }
 }

@@ -19,7 +19,7 @@ cudaError_t shard_element_sz(const BatchArgs &a, const ScanLayout &SL, size_t sb
     auto k = k_scan_reduce<double, NX, NU>;
     if ((e = set_smem(k, sizeof(CS))) != cudaSuccess) return e;
     LaunchScope ls("k_scan_reduce", s);
-    k<<<SL.C + 1, scan::kTH, sizeof(CS), s>>>(a, SL, sbase, 1);
+    k<<<SL.C + 1, scan::kTH, sizeof(CS), s>>>(a, SL, sbase, 1, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   int from1 = 0;

@@ -41,6 +41,9 @@ CASES = [
     ("n12m4_N5", lambda: _case(404, 5, 12, 4, 0.2)),
     ("n32m8_N97", lambda: _case(405, 97, 32, 8, 1e-5)),
     ("n12m4_N120_nonconvex", lambda: _case(406, 120, 12, 4, 0.01, nonconvex=True)),
+    # chunks of 21 stages: the P-only pass starts from the inner elements
+    # (a final chunk of 12 stages without one)
+    ("n12m4_N9000", lambda: _case(408, 9000, 12, 4, 1e-3)),
 ]
 
 
