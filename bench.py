@@ -1011,6 +1011,20 @@ def measure_ragged(args, count, only_n=0):
             acc["escalated_stages"] = int(sum(N_ for e, (N_, _, _) in zip(esc, dims) if e))
         return e0.elapsed_time(e1) / steps, report, acc
 
+    # setup, not timed: the autotuner times the mixed batch's sweep routes
+    # (one launch per size class on concurrent streams / one persistent
+    # launch) and records the faster one, which the timed solves then take
+    tune = None
+    o_t = rlqr.make_opts(rlqr.RLQR_MIXED, tol=TOL, max_refine=6)
+    try:
+        ws_t = rlqr.alloc_workspace(rlqr.rlqr_batched_workspace_bytes(db, o_t))
+        route, tms = rlqr.rlqr_autotune_batched(db, o_t, ws_t)
+        tune = {"sweep_route": {rlqr.SWEEP_ROUTE_STREAMS: "class streams",
+                                rlqr.SWEEP_ROUTE_PERSISTENT: "persistent launch"}[route],
+                "ms": round(tms, 3)}
+        del ws_t
+    except rlqr.RlqrError:
+        tune = {"sweep_route": "class streams (sizes outside the persistent sweep)"}
     with ClockSampler(0) as clk:
         ms, report, acc = timed(rlqr.RLQR_MIXED, args.steps, args.warmup, True)
     ms64, _, acc64 = timed(rlqr.RLQR_FP64, max(1, args.steps // 4), 1)
@@ -1029,7 +1043,7 @@ def measure_ragged(args, count, only_n=0):
                                    f"the first {count} of the ragged batch of 4096 "
                                    "(N in 32..2048, n in {6,12,24,48}, m = n/3, barrier-scaled "
                                    "diagonals)", "instances": B, "stages": stages,
-                       "data_gb": round(data_gb, 2)},
+                       "data_gb": round(data_gb, 2), "autotune": tune},
             "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in report.items()},
             "roofline": {"kernel": "whole solve (size classes run concurrently)", "bound": "hbm",
                          "achieved": round(achieved, 2), "peak": hbm,

@@ -232,17 +232,27 @@ rlqr_status rlqr_autotune_scan(const rlqr_problem *prob, const rlqr_opts *opts, 
 rlqr_status rlqr_tune_scan_set(int32_t N, int32_t nx, int32_t nu, const rlqr_opts *opts,
                                int32_t chunks);
 
-/* Residual route of uniform batches of the FP32 warp-sweep sizes ((4,2),
- * (6,2), (12,4)): 1 = one warp per instance (float-float in mixed mode),
- * 2 = the stage-parallel grid over all stages of the batch.
- * rlqr_autotune_batched times rlqr_solve_batched on `batch` with each route
- * (a warm-up and three timed runs, CUDA events, host-synchronising) and
- * records the faster one for (nx, nu, opts->prec, floor(log2 max N),
- * floor(log2 count)) in the process-wide table; status (device [count],
- * may be NULL) is scratch for the timed solves; best_route / best_ms (host,
- * may be NULL) receive the choice and its time.  RLQR_ERR_ARG for ragged
- * batches or other sizes.  rlqr_tune_batched_set records a route explicitly
- * (0 removes the entry).  rlqr_tune_reset clears both tables. */
+/* Routes of rlqr_solve_batched that the tuner chooses between.
+ * Uniform batches of the FP32 warp-sweep sizes ((4,1), (4,2), (6,1), (6,2),
+ * (12,3), (12,4)): the residual route, 1 = one warp per instance
+ * (float-float in mixed mode), 2 = the stage-parallel grid over all stages
+ * of the batch.  Ragged mixed-precision batches whose size classes are all
+ * among (4,2), (6,2), (12,4), (24,8), (32,8), (48,16): the sweep route,
+ * 3 = one launch per size class on the library's concurrent streams (the
+ * default), 4 = one persistent launch for every class (CTAs take work items
+ * -- 8 instances of a warp size or one of a CTA size, longest chain first --
+ * from an atomic counter).
+ * rlqr_autotune_batched times rlqr_solve_batched on `batch` with each of
+ * its two routes (a warm-up and three timed runs, CUDA events,
+ * host-synchronising) and records the faster one for (nx, nu, opts->prec,
+ * floor(log2 max N), floor(log2 count)), or for ragged batches (the set of
+ * size classes, floor(log2 max N), floor(log2 count)), in the process-wide
+ * table; status (device [count], may be NULL) is scratch for the timed
+ * solves; best_route / best_ms (host, may be NULL) receive the choice and
+ * its time.  RLQR_ERR_ARG for other batches.  rlqr_tune_batched_set records
+ * a route explicitly (0 removes the entry).  rlqr_tune_reset clears both
+ * tables.  rlqr_solve_batched creates its class streams and events once
+ * per device on first use of a ragged batch and keeps them. */
 rlqr_status rlqr_autotune_batched(const rlqr_batch *batch, const rlqr_opts *opts, void *ws,
                                   size_t ws_bytes, int32_t *status, int32_t *best_route,
                                   double *best_ms, rlqr_stream_t stream);

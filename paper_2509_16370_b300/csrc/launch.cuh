@@ -69,6 +69,35 @@ inline cudaError_t set_smem_carveout(F *kernel, size_t bytes) {
 // Defined in launch_fp32.cu / launch_fp64.cu (explicit instantiations).
 template <typename T, bool SOLVE>
 cudaError_t launch_seq(int n, int m, bool uniform, const BatchArgs &a, cudaStream_t s);
+
+// ---- persistent sweep of a ragged batch (ragged.cuh, mixed precision)
+constexpr int kRaggedClasses = 7;  // the exact size classes of the batched driver
+
+// A size class's place in the persistent sweep: 1 = warp sweep, 2 = CTA
+// sweep, 0 = not covered.  Class indices as size_class() numbers them:
+// (4,2), (6,1), (6,2), (12,4), (24,8), (32,8), (48,16).
+__host__ __device__ inline int ragged_kind(int cls) {
+  switch (cls) {
+    case 0: case 2: case 3: return 1;
+    case 4: case 5: case 6: return 2;
+    default: return 0;
+  }
+}
+
+struct RaggedPlan {
+  int off[kRaggedClasses];  // class c occupies perm[off[c] .. off[c] + cnt[c])
+  int cnt[kRaggedClasses];
+};
+
+// The work items (int4 per item, at most one per instance) and the two-int
+// counter block (meta) live in the batch header.  The FP32 sweeps of every
+// instance of the classes in P, in one launch on s; the deferred state-pivot
+// certificates of the CTA-sweep classes follow (launch_seq_cert).
+cudaError_t launch_ragged_sweep(const BatchArgs &a, const RaggedPlan &P, const int32_t *perm,
+                                int4 *items, int32_t *meta, cudaStream_t s);
+// The deferred certificate of the FP32 CTA sweep for a group of size (n, m)
+// (cudaSuccess and nothing launched for sizes without one).
+cudaError_t launch_seq_cert(int n, int m, const BatchArgs &a, cudaStream_t s);
 template <typename T, bool FROM_RES>
 cudaError_t launch_solve(int n, int m, bool uniform, const BatchArgs &a, cudaStream_t s);
 // First residual of the mixed path (stored for the refinement) with the

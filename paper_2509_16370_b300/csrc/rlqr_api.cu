@@ -89,6 +89,21 @@ static uint64_t route_key(int N, int n, int m, int tsize, int count) {
          ((uint64_t)ilog2(N) << 8) | (uint64_t)ilog2(count);
 }
 
+// Sweep route of a ragged batch: 3 = one launch per size class on
+// concurrent streams (the default), 4 = one persistent launch (ragged.cuh);
+// recorded per (set of size classes, precision, floor(log2 max N),
+// floor(log2 count)).
+static uint64_t ragged_key(int mask, int N, int tsize, int count) {
+  return (1ull << 63) | ((uint64_t)mask << 32) | ((uint64_t)tsize << 24) |
+         ((uint64_t)ilog2(N) << 8) | (uint64_t)ilog2(count);
+}
+
+static int ragged_route(int mask, int N, int tsize, int count) {
+  std::lock_guard<std::mutex> lock(g_route_mu);
+  const auto it = g_res_route.find(ragged_key(mask, N, tsize, count));
+  return it == g_res_route.end() ? 3 : it->second;
+}
+
 static int residual_route(int N, int n, int m, int tsize, int count) {
   std::lock_guard<std::mutex> lock(g_route_mu);
   const auto it = g_res_route.find(route_key(N, n, m, tsize, count));
@@ -228,10 +243,16 @@ static ClassStreams *class_streams_locked() {
 
 // Header of a batch's workspace: per-instance byte offsets (int64), the
 // launch permutation of a ragged batch (int32), the exclusive prefix sum of
-// N_b + 1 (int64, count + 1 entries: the residual's work items).
-__host__ __device__ inline size_t batch_header_bytes(int count) {
+// N_b + 1 (int64, count + 1 entries: the residual's work items), then the
+// persistent ragged sweep's work items (int4, at most count) and its item
+// count and counter (two int32).
+__host__ __device__ inline size_t batch_header_items(int count) {
   return align_up((size_t)count * sizeof(int64_t)) + align_up((size_t)count * sizeof(int32_t)) +
          align_up((size_t)(count + 1) * sizeof(int64_t));
+}
+__host__ __device__ inline size_t batch_header_bytes(int count) {
+  return batch_header_items(count) + align_up((size_t)count * sizeof(int4)) +
+         align_up(2 * sizeof(int32_t));
 }
 
 // Per-instance workspace offsets of a batch (exclusive prefix sum of
@@ -601,6 +622,8 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
   };
   Group groups[kNumClasses];
   int ng = 0;
+  int sweep_route = 3;  // ragged batches: class streams (3) or the persistent sweep (4)
+  RaggedPlan rplan{};
   if (uniform) {
     groups[ng++] = Group{nmax, mmax, rs_max, B.count, 0, true};
   } else {
@@ -630,6 +653,21 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
       if (cudaGetLastError() != cudaSuccess) return RLQR_ERR_CUDA;
     }
     a.perm = perm;
+    if (mixed) {
+      bool covered = true;
+      int mask = 0;
+      for (int c = 0; c < kNumClasses; ++c) {
+        if (!cnt[c]) continue;
+        mask |= 1 << c;
+        if (c >= kRaggedClasses || !ragged_kind(c)) {
+          covered = false;
+        } else {
+          rplan.off[c] = co.off[c];
+          rplan.cnt[c] = cnt[c];
+        }
+      }
+      if (covered) sweep_route = ragged_route(mask, nmaxN, a.tsize, B.count);
+    }
   }
   auto group_args = [&](int g) {
     BatchArgs ag = a;
@@ -661,15 +699,27 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
         return false;
     return true;
   };
-  if (!fork()) return RLQR_ERR_CUDA;
-  for (int g = 0; g < ng; ++g) {
-    const Group &G = groups[g];
-    const BatchArgs ag = group_args(g);
-    e = mixed ? launch_seq<float, true>(G.n, G.m, G.exact, ag, gstream(g))
-              : launch_seq<double, true>(G.n, G.m, G.exact, ag, gstream(g));
+  if (sweep_route == 4) {
+    // one persistent launch for every class's sweep, then the CTA classes'
+    // deferred certificates
+    char *hdr = static_cast<char *>(ws) + batch_header_items(B.count);
+    int4 *items = reinterpret_cast<int4 *>(hdr);
+    int32_t *meta = reinterpret_cast<int32_t *>(hdr + align_up((size_t)B.count * sizeof(int4)));
+    e = launch_ragged_sweep(a, rplan, a.perm, items, meta, s);
+    for (int g = 0; g < ng && e == cudaSuccess; ++g)
+      e = launch_seq_cert(groups[g].n, groups[g].m, group_args(g), s);
     if (e != cudaSuccess) return RLQR_ERR_CUDA;
+  } else {
+    if (!fork()) return RLQR_ERR_CUDA;
+    for (int g = 0; g < ng; ++g) {
+      const Group &G = groups[g];
+      const BatchArgs ag = group_args(g);
+      e = mixed ? launch_seq<float, true>(G.n, G.m, G.exact, ag, gstream(g))
+                : launch_seq<double, true>(G.n, G.m, G.exact, ag, gstream(g));
+      if (e != cudaSuccess) return RLQR_ERR_CUDA;
+    }
+    if (!join()) return RLQR_ERR_CUDA;
   }
-  if (!join()) return RLQR_ERR_CUDA;
   if (mixed || rel_resid) {
     // uniform: the group's first residual; ragged: one stage-parallel
     // residual over every instance
@@ -1079,24 +1129,41 @@ rlqr_status rlqr_tune_reset(void) {
   return RLQR_OK;
 }
 
-static bool batch_tune_key(const rlqr_batch *batch, const rlqr_opts *opts, uint64_t *key) {
+// The tuning key of a batch and whether it is ragged: a uniform batch of a
+// warp-residual size (residual routes 1, 2) or a ragged mixed-precision
+// batch whose classes the persistent sweep covers (sweep routes 3, 4).
+static bool batch_tune_key(const rlqr_batch *batch, const rlqr_opts *opts, uint64_t *key,
+                           bool *ragged) {
   if (!batch || batch->count < 1 || !batch->h_N || !batch->h_nx || !batch->h_nu ||
       !valid_opts(opts))
     return false;
-  int nmaxN = 1;
+  int nmaxN = 1, mask = 0;
+  bool uniform = true;
   for (int b = 0; b < batch->count; ++b) {
-    if (batch->h_nx[b] != batch->h_nx[0] || batch->h_nu[b] != batch->h_nu[0]) return false;
+    if (batch->h_nx[b] != batch->h_nx[0] || batch->h_nu[b] != batch->h_nu[0]) uniform = false;
     nmaxN = std::max(nmaxN, batch->h_N[b]);
+    mask |= 1 << size_class(batch->h_nx[b], batch->h_nu[b]);
   }
-  if (!warp_res32_size(batch->h_nx[0], batch->h_nu[0])) return false;
-  *key = route_key(nmaxN, batch->h_nx[0], batch->h_nu[0], opts->prec == RLQR_MIXED ? 4 : 8,
-                   batch->count);
+  const int tsize = opts->prec == RLQR_MIXED ? 4 : 8;
+  if (uniform) {
+    if (!warp_res32_size(batch->h_nx[0], batch->h_nu[0])) return false;
+    *key = route_key(nmaxN, batch->h_nx[0], batch->h_nu[0], tsize, batch->count);
+    *ragged = false;
+    return true;
+  }
+  if (tsize != 4) return false;
+  for (int c = 0; c < kNumClasses; ++c)
+    if ((mask >> c & 1) && (c >= kRaggedClasses || !ragged_kind(c))) return false;
+  *key = ragged_key(mask, nmaxN, tsize, batch->count);
+  *ragged = true;
   return true;
 }
 
 rlqr_status rlqr_tune_batched_set(const rlqr_batch *batch, const rlqr_opts *opts, int32_t route) {
   uint64_t key;
-  if (!batch_tune_key(batch, opts, &key) || route < 0 || route > 2) return RLQR_ERR_ARG;
+  bool ragged = false;
+  if (!batch_tune_key(batch, opts, &key, &ragged) || route < 0) return RLQR_ERR_ARG;
+  if (route != 0 && (ragged ? (route < 3 || route > 4) : route > 2)) return RLQR_ERR_ARG;
   std::lock_guard<std::mutex> lock(g_route_mu);
   if (route == 0)
     g_res_route.erase(key);
@@ -1109,7 +1176,8 @@ rlqr_status rlqr_autotune_batched(const rlqr_batch *batch, const rlqr_opts *opts
                                   size_t ws_bytes, int32_t *status, int32_t *best_route,
                                   double *best_ms, rlqr_stream_t stream) {
   uint64_t key;
-  if (!batch_tune_key(batch, opts, &key)) return RLQR_ERR_ARG;
+  bool ragged = false;
+  if (!batch_tune_key(batch, opts, &key, &ragged)) return RLQR_ERR_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   rlqr_opts o = *opts;
   o.flags = 0;
@@ -1123,7 +1191,8 @@ rlqr_status rlqr_autotune_batched(const rlqr_batch *batch, const rlqr_opts *opts
   int best = 0;
   float best_t = 0.0f;
   const int reps = 3;
-  for (int route = 1; route <= 2 && err == RLQR_OK; ++route) {
+  const int r0 = ragged ? 3 : 1;
+  for (int route = r0; route <= r0 + 1 && err == RLQR_OK; ++route) {
     err = rlqr_tune_batched_set(batch, opts, route);
     float t = 0.0f;
     for (int r = 0; r <= reps && err == RLQR_OK; ++r) {  // r = 0: warm-up

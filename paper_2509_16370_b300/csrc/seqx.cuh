@@ -34,19 +34,18 @@ struct SxSmem {
   int bit, sing, pass;
 };
 
+// The sweep of instance b by one CTA of scan::kTH threads in the shared
+// memory at smem (an SxSmem<T, NX, NU>); the body of k_seqx and of the
+// persistent ragged sweep.
 template <typename T, int NX, int NU, bool SOLVE>
-__global__ void __launch_bounds__(scan::kTH) k_seqx(BatchArgs a) {
+__device__ __forceinline__ void seqx_body(const BatchArgs &a, int b, unsigned char *smem) {
   static_assert(seqx_fits<NX, NU>(), "size outside the compile-time CTA sweep");
   using SM = SxSmem<T, NX, NU>;
   constexpr bool FP32 = sizeof(T) == 4;
   constexpr int TH = scan::kTH;
   constexpr int n = NX, m = NU, nn = n * n, nm = n * m, mmm = m * m;
   constexpr int LD = SM::LD, LD2 = SM::LD2, LDG = SM::LDG, WG = SM::WG;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SM &s = *reinterpret_cast<SM *>(smem_raw);
-  const int slot = blockIdx.x;
-  if (slot >= a.count) return;
-  const int b = inst_of(a, slot);
+  SM &s = *reinterpret_cast<SM *>(smem);
   const Inst I = get_inst(a, b);
   const int N = I.N, tid = threadIdx.x;
   const T delta = (T)I.delta;
@@ -389,6 +388,14 @@ __global__ void __launch_bounds__(scan::kTH) k_seqx(BatchArgs a) {
     }
     __syncthreads();
   }
+}
+
+template <typename T, int NX, int NU, bool SOLVE>
+__global__ void __launch_bounds__(scan::kTH) k_seqx(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int slot = blockIdx.x;
+  if (slot >= a.count) return;
+  seqx_body<T, NX, NU, SOLVE>(a, inst_of(a, slot), smem_raw);
 }
 
 // Deferred certificate of the state pivots I + delta P_s whose FP32

@@ -154,20 +154,19 @@ __device__ __forceinline__ void commit_sym(const LaneSeg<double, CNT> &pf, int l
   }
 }
 
+// The sweep of instance b by one warp (lane = its lane) in the shared memory
+// at smem (a Sw32<NX, NU>); the body of k_sweep32 and of the persistent
+// ragged sweep.
 template <int NX, int NU, bool SOLVE>
-__global__ void __launch_bounds__(32) k_sweep32(BatchArgs a) {
+__device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned char *smem,
+                                             int lane) {
   static_assert(sweep32_fits<NX, NU>(), "dimensions outside the FP32 warp sweep");
   constexpr int n = NX, m = NU, nn = n * n, nm = n * m, mmm = m * m;
   constexpr int H2 = n / 2, M2 = m / 2;
   using SM = Sw32<NX, NU>;
   constexpr int N4 = SM::N4, M4 = SM::M4;
   constexpr int VL = n + m;  // the lane of the vector recursion (p, g, h, k)
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SM &s = *reinterpret_cast<SM *>(smem_raw);
-  const int lane = threadIdx.x;
-  const int slot = blockIdx.x;
-  if (slot >= a.count) return;
-  const int b = inst_of(a, slot);
+  SM &s = *reinterpret_cast<SM *>(smem);
   const Inst I = get_inst(a, b);
   const int N = I.N;
   const float delta = (float)I.delta;
@@ -688,6 +687,14 @@ __global__ void __launch_bounds__(32) k_sweep32(BatchArgs a) {
     }
     __syncwarp();
   }
+}
+
+template <int NX, int NU, bool SOLVE>
+__global__ void __launch_bounds__(32) k_sweep32(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int slot = blockIdx.x;
+  if (slot >= a.count) return;
+  sweep32_body<NX, NU, SOLVE>(a, inst_of(a, slot), smem_raw, threadIdx.x);
 }
 
 }  // namespace rlqr

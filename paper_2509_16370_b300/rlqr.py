@@ -483,12 +483,15 @@ def rlqr_tune_reset():
 
 
 RES_ROUTE_WARP, RES_ROUTE_GRID = 1, 2
+SWEEP_ROUTE_STREAMS, SWEEP_ROUTE_PERSISTENT = 3, 4
 
 
 def rlqr_autotune_batched(batch: "DeviceBatch", opts: rlqr_opts, ws: torch.Tensor, status=None,
                           stream=None):
-    """Time the residual routes of a uniform batch and record the faster one
-    for its shape; returns (route, ms of one rlqr_solve_batched)."""
+    """Time the two routes of the batch -- the residual routes of a uniform
+    batch, the sweep routes (class streams / persistent launch) of a ragged
+    one -- and record the faster one for its shape; returns (route, ms of
+    one rlqr_solve_batched)."""
     bs = batch.c_struct()
     r = ctypes.c_int32(0)
     t = ctypes.c_double(0.0)

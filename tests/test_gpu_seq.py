@@ -250,17 +250,21 @@ def test_ragged_workload4_sample(prec):
         assert oracle.residual(p, x, u, y).rel <= REL_TOL
 
 
-@pytest.mark.parametrize("prec", PRECS)
-def test_ragged_batch_graph_replay(prec):
+@pytest.mark.parametrize("prec,route", [(rlqr.RLQR_FP64, None), (rlqr.RLQR_MIXED, None),
+                                        (rlqr.RLQR_MIXED, rlqr.SWEEP_ROUTE_PERSISTENT)])
+def test_ragged_batch_graph_replay(prec, route):
     """A ragged batch runs its size classes on the library's own streams,
-    forked from and joined back to the caller's stream: the call can be
-    captured into a CUDA graph, and a replay reproduces the eager call's
-    solution, flags, status and backward errors bit for bit."""
+    forked from and joined back to the caller's stream, or (mixed, route 4)
+    all its sweeps in one persistent launch: the call can be captured into a
+    CUDA graph, and a replay reproduces the eager call's solution, flags,
+    status and backward errors bit for bit."""
     dims = inputs.workload4_dims(4096)[:24]
     probs = [inputs.workload4_instance(b, min(N, 96), n, m) for b, (N, n, m) in enumerate(dims)]
     assert len({(p.n, p.m) for p in probs}) > 1
     db = rlqr.DeviceBatch.from_problems(probs)
     opts = rlqr.make_opts(prec, tol=1e-9, max_refine=6)
+    if route is not None:
+        rlqr.rlqr_tune_batched_set(db, opts, route)
     ws = rlqr.alloc_workspace(rlqr.rlqr_batched_workspace_bytes(db, opts))
     B = db.count
     st = torch.full((B,), -1, dtype=torch.int32, device="cuda")
@@ -289,6 +293,45 @@ def test_ragged_batch_graph_replay(prec):
         x, u, y, f = db.instance_view(b)
         np.testing.assert_array_equal(f, oracle.riccati(p).flags)
         assert oracle.residual(p, x, u, y).rel <= REL_TOL
+    if route is not None:
+        rlqr.rlqr_tune_batched_set(db, opts, 0)
+
+
+def test_ragged_persistent_sweep_matches_class_streams():
+    """The persistent sweep (one launch, work items longest chain first)
+    against the per-class launches on the same ragged batch with every
+    covered size and ragged tails of the 8-instance warp items: the same
+    flags and statuses, each solution within 1e-9 of the oracle's backward
+    error bar, and the tuner choosing one of the two sweep routes."""
+    dims = [(40 + 7 * b, (4, 6, 12, 24, 32, 48)[b % 6], 0) for b in range(29)]
+    probs = []
+    for b, (N, n, _) in enumerate(dims):
+        m = {4: 2, 6: 2, 12: 4, 24: 8, 32: 8, 48: 16}[n]
+        probs.append(inputs.random_instance(600 + b, N, n, m, 10.0 ** (-2 - b % 5)))
+    db = rlqr.DeviceBatch.from_problems(probs)
+    opts = rlqr.make_opts(rlqr.RLQR_MIXED, tol=1e-9, max_refine=6)
+    outs = {}
+    for route in (rlqr.SWEEP_ROUTE_STREAMS, rlqr.SWEEP_ROUTE_PERSISTENT):
+        rlqr.rlqr_tune_batched_set(db, opts, route)
+        out = solve_batch(db, rlqr.RLQR_MIXED, max_refine=6)
+        outs[route] = (out, [tuple(t.copy() for t in db.instance_view(b)) for b in range(len(probs))])
+        for b, p in enumerate(probs):
+            x, u, y, f = db.instance_view(b)
+            ref = oracle.riccati(p)
+            np.testing.assert_array_equal(f, ref.flags, err_msg=f"route {route} instance {b}")
+            assert oracle.residual(p, x, u, y).rel <= REL_TOL, (route, b)
+    a, b_ = outs[rlqr.SWEEP_ROUTE_STREAMS][0], outs[rlqr.SWEEP_ROUTE_PERSISTENT][0]
+    np.testing.assert_array_equal(a["status"], b_["status"])
+    ws = rlqr.alloc_workspace(rlqr.rlqr_batched_workspace_bytes(db, opts))
+    route, ms = rlqr.rlqr_autotune_batched(db, opts, ws)
+    assert route in (rlqr.SWEEP_ROUTE_STREAMS, rlqr.SWEEP_ROUTE_PERSISTENT) and ms > 0
+    rlqr.rlqr_tune_batched_set(db, opts, 0)
+    # a route of the other kind, or a batch the persistent sweep does not cover
+    with pytest.raises(rlqr.RlqrError):
+        rlqr.rlqr_tune_batched_set(db, opts, rlqr.RES_ROUTE_GRID)
+    odd = rlqr.DeviceBatch.from_problems(probs[:3] + [inputs.random_instance(7, 20, 6, 1, 1e-3)])
+    with pytest.raises(rlqr.RlqrError):
+        rlqr.rlqr_tune_batched_set(odd, opts, rlqr.SWEEP_ROUTE_PERSISTENT)
 
 
 @pytest.mark.parametrize("dims", [(6, 1), (12, 4), (24, 8), (32, 8), (48, 16), (10, 3)],
