@@ -609,8 +609,8 @@ struct FinSmem {
 // also pivots P_0 (W_0, flags[0]).  The instance's pivot status is the worst
 // over the chunks (atomicMax).
 template <typename T, int NX, int NU, int PASS>
-__global__ void __launch_bounds__(scan::kTH) k_scan_finalize(BatchArgs a, ScanLayout SL,
-                                                             size_t sbase, int from1) {
+__global__ void __launch_bounds__(scan::kTH, sizeof(T) == 4 ? 3 : 1)
+    k_scan_finalize(BatchArgs a, ScanLayout SL, size_t sbase, int from1) {
   constexpr bool FULL = PASS != 1;
   using SM = FinSmem<T, NX, NU>;
   constexpr bool FP32 = sizeof(T) == 4;
