@@ -1119,7 +1119,8 @@ def run_ours(args):
         o_t, ws_t, st_t, _, _ = setup(prec)
         route, tms = rlqr.rlqr_autotune_batched(db, o_t, ws_t, st_t)
         tune[name] = {"residual_route": {rlqr.RES_ROUTE_WARP: "warp",
-                                         rlqr.RES_ROUTE_GRID: "grid"}[route],
+                                         rlqr.RES_ROUTE_GRID: "grid",
+                                         rlqr.RES_ROUTE_FUSED: "fused into the first pass"}[route],
                       "ms": round(tms, 4)}
         del ws_t
     with ClockSampler(local) as clk:

@@ -236,7 +236,10 @@ rlqr_status rlqr_tune_scan_set(int32_t N, int32_t nx, int32_t nu, const rlqr_opt
  * Uniform batches of the FP32 warp-sweep sizes ((4,1), (4,2), (6,1), (6,2),
  * (12,3), (12,4)): the residual route, 1 = one warp per instance
  * (float-float in mixed mode), 2 = the stage-parallel grid over all stages
- * of the batch.  Ragged mixed-precision batches whose size classes are all
+ * of the batch, 5 = (mixed precision, max_refine >= 1) no separate first
+ * residual: the control pivots are certified by a grid kernel and the first
+ * refinement pass computes the residual (float-float) stage by stage ahead
+ * of its backward chain.  Ragged mixed-precision batches whose size classes are all
  * among (4,2), (6,2), (12,4), (24,8), (32,8), (48,16): the sweep route,
  * 3 = one launch per size class on the library's concurrent streams (the
  * default), 4 = one persistent launch for every class (CTAs take work items

@@ -148,6 +148,9 @@ struct BatchArgs {
   int recheck;
   // refinement launches: index of the pass (0 = first)
   int rpass;
+  // warp sizes of the mixed path: the first refinement pass computes the
+  // residual itself (no separate first-residual launch)
+  int fused_res;
 };
 
 // Instance of a launch slot: the identity, or the group's entry of perm.

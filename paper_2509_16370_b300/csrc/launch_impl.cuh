@@ -118,9 +118,11 @@ static cudaError_t launch_solve_warp(const BatchArgs &a, cudaStream_t s) {
   const char *name =
       FROM_RES ? "k_solve_refine" : (sizeof(T) == 4 ? "k_solve_fp32" : "k_solve_fp64");
   if constexpr (sizeof(T) == 4 && FROM_RES && tab32_fits<NX, NU>()) {
-    // the factor and the FP32 data copies come from k_sweep32 or k_tab32
-    auto kern = k_refine_tab<NX, NU>;
-    const size_t bytes = sizeof(Rt32<NX, NU>);
+    // the factor and the FP32 data copies come from k_sweep32 or k_tab32;
+    // the fused route's first pass computes the residual itself
+    const bool fused = a.fused_res && a.rpass == 0;
+    auto kern = fused ? k_refine_tab<NX, NU, true> : k_refine_tab<NX, NU, false>;
+    const size_t bytes = fused ? refine_tab_smem<NX, NU, true>() : refine_tab_smem<NX, NU, false>();
     cudaError_t e = set_smem_carveout(kern, bytes);
     if (e != cudaSuccess) return e;
     LaunchScope ls(name, s);

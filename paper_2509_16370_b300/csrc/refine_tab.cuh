@@ -21,6 +21,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "residual32.cuh"
 #include "tab32.cuh"
 
 namespace rlqr {
@@ -70,22 +71,32 @@ struct Rt32 {
   alignas(16) float d[4][N4];  // dx_k, dy_k, dx_{k+1}, dy_{k+1} (rotating)
 };
 
-template <int NX, int NU>
+// FUSED (the first pass of the fused route): the residual of the solution
+// is not read but computed here, stage by stage ahead of the backward chain
+// that consumes it (Res32Rows, float-float as in k_res32, in a Rs32Warp
+// after the Rt32 in shared memory), and written for the forward pass; the
+// norms of the backward error come from the same rows.
+template <int NX, int NU, bool FUSED>
 __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot,
                                                     unsigned char *smem_raw);
 
+template <int NX, int NU, bool FUSED>
+__host__ __device__ constexpr size_t refine_tab_smem() {
+  return sizeof(Rt32<NX, NU>) + (FUSED ? sizeof(Rs32Warp<NX, NU>) : 0);
+}
+
 // One instance per block; passes after the first use fewer blocks than
 // instances (most instances have converged) and stride over the slots.
-template <int NX, int NU>
+template <int NX, int NU, bool FUSED>
 __global__ void __launch_bounds__(32) k_refine_tab(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   for (int slot = blockIdx.x; slot < a.count; slot += gridDim.x) {
-    refine_tab_instance<NX, NU>(a, slot, smem_raw);
+    refine_tab_instance<NX, NU, FUSED>(a, slot, smem_raw);
     __syncwarp();
   }
 }
 
-template <int NX, int NU>
+template <int NX, int NU, bool FUSED>
 __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot,
                                                     unsigned char *smem_raw) {
   static_assert(tab32_fits<NX, NU>(), "dimensions outside the tableau kernels");
@@ -98,6 +109,7 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
   constexpr int RS = 2 * n + m;  // residual rows of a stage
   constexpr int CP = (nn + 31) / 32, CB = (nm + 31) / 32, CR = (mmm + 31) / 32;
   SM &s = *reinterpret_cast<SM *>(smem_raw);
+  Rs32Warp<NX, NU> &rsw = *reinterpret_cast<Rs32Warp<NX, NU> *>(smem_raw + sizeof(SM));
   const int lane = threadIdx.x;
   const int b = inst_of(a, slot);
   const Inst I = get_inst(a, b);
@@ -181,17 +193,35 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
         const int e = lane + 32 * i;
         if (e < mmm) cp_async4(&d.Gi[oR[i]], G + e);
       }
-      if (lane < n) {
-        cp_async8(&d.q[lane], rq + (size_t)k * n + lane);
-        cp_async8(&d.c[lane], rc + (size_t)(k + 1) * n + lane);
+      if constexpr (!FUSED) {
+        if (lane < n) {
+          cp_async8(&d.q[lane], rq + (size_t)k * n + lane);
+          cp_async8(&d.c[lane], rc + (size_t)(k + 1) * n + lane);
+        }
+        if (lane < m) cp_async8(&d.r[lane], rr + (size_t)k * m + lane);
       }
-      if (lane < m) cp_async8(&d.r[lane], rr + (size_t)k * m + lane);
     }
     cp_async_commit();
   };
   __syncwarp();
+  // the residual rows computed here (FUSED): this lane's norms of the
+  // backward error, and the stage pipeline of Res32Rows
+  Res32Rows<NX, NU> R;
+  float kmaxf = 0.f;
+  unsigned long long fzbits = 0, fbbits = 0;
+  if constexpr (FUSED) {
+    R.init(rsw, lane, delta64);
+    R.prefetch(I, N - 1, lane);
+  }
   if (lane < n) {
-    const float v = f64_to_f32_rz(__ldcg(rq + (size_t)N * n + lane));
+    float v;
+    if constexpr (FUSED) {
+      const double v64 = res_end_row(I, lane, kmaxf, fzbits, fbbits);  // row x_N
+      rq[(size_t)N * n + lane] = v64;
+      v = f64_to_f32_rz(v64);
+    } else {
+      v = f64_to_f32_rz(__ldcg(rq + (size_t)N * n + lane));
+    }
     s.p[lane] = v;
     gpv[(size_t)N * n + lane] = v;
   }
@@ -199,15 +229,41 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
   for (int j = 0; j < DB - 1; ++j) bissue(N - 1 - j);
 #pragma unroll 1
   for (int k = N - 1; k >= 0; --k) {
+    if constexpr (FUSED) {
+      // the residual rows of stage k (lane r: row r), kept in FP64 for the
+      // forward pass and handed to the chain in FP32 (c rows through s.w)
+      R.commit(rsw, lane, fzbits, fbbits);
+      if (k > 0) R.prefetch(I, k - 1, lane);
+      __syncwarp();
+      if (lane < RS) {
+        const double v = R.row(rsw, lane, kmaxf);
+        const float vf = f64_to_f32_rz(v);
+        if (lane < n) {
+          rq[(size_t)k * n + lane] = v;
+          s.qr[lane] = vf;
+        } else if (lane < n + m) {
+          rr[(size_t)k * m + lane - n] = v;
+          s.rr[lane - n] = vf;
+        } else {
+          rc[(size_t)(k + 1) * n + lane - n - m] = v;
+          s.w[lane - n - m] = vf;
+        }
+      }
+    }
     bissue(k - (DB - 1));
     cp_async_wait<DB - 1>();
     const BS &d = bring[(N - 1 - k) % DB];
-    // this lane's residual entries, truncated to FP32 (it copied them)
-    if (lane < n) {
-      s.qr[lane] = f64_to_f32_rz(d.q[lane]);
-      s.cr[lane] = fmaf(-delta, s.p[lane], f64_to_f32_rz(d.c[lane]));  // v = c' - delta p
+    if constexpr (FUSED) {
+      __syncwarp();
+      if (lane < n) s.cr[lane] = fmaf(-delta, s.p[lane], s.w[lane]);  // v = c' - delta p
+    } else {
+      // this lane's residual entries, truncated to FP32 (it copied them)
+      if (lane < n) {
+        s.qr[lane] = f64_to_f32_rz(d.q[lane]);
+        s.cr[lane] = fmaf(-delta, s.p[lane], f64_to_f32_rz(d.c[lane]));  // v = c' - delta p
+      }
+      if (lane < m) s.rr[lane] = f64_to_f32_rz(d.r[lane]);
     }
-    if (lane < m) s.rr[lane] = f64_to_f32_rz(d.r[lane]);
     __syncwarp();
     // g = p + W v
     if (lane < n) {
@@ -251,8 +307,11 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
     }
     __syncwarp();  // the slot may be refilled from here on
   }
+  if constexpr (FUSED) {
+    if (lane < n) rc[lane] = res_end_row(I, n + lane, kmaxf, fzbits, fbbits);  // row c_0
+  }
   cp_async_wait<0>();
-  __threadfence_block();  // p and k of the correction, read back by cp.async below
+  __threadfence_block();  // p, k and the residual rows, read back by cp.async below
   __syncwarp();
 
   // ---------------- forward rollout, FP64 update of z and of the residual
@@ -467,6 +526,19 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
     rbits = max(rbits, __shfl_xor_sync(0xffffffffu, rbits, o));
     zbits = max(zbits, __shfl_xor_sync(0xffffffffu, zbits, o));
     sbits = max(sbits, __shfl_xor_sync(0xffffffffu, sbits, o));
+  }
+  if constexpr (FUSED) {
+    // the norms of K and b from the rows computed in the backward pass; the
+    // rounding bound starts from this freshly computed residual
+    for (int o = 16; o > 0; o >>= 1) {
+      kmaxf = fmaxf(kmaxf, __shfl_xor_sync(0xffffffffu, kmaxf, o));
+      fbbits = max(fbbits, __shfl_xor_sync(0xffffffffu, fbbits, o));
+    }
+    if (lane == 0) {
+      stp->kmax = (double)kmaxf;
+      stp->bmax = bits_to_double(fbbits);
+      stp->upd = 0.0;
+    }
   }
   if (lane == 0) {
     const double rmax = bits_to_double(rbits), zmax = bits_to_double(zbits);

@@ -125,6 +125,188 @@ __device__ __forceinline__ float2 abs_sum2(const float2 (&r)[L / 2], float2 acc)
   return acc;
 }
 
+// The residual rows of one stage by one warp (lane r < 2n+m: row r of the
+// stage, as in k_res32): prefetch() loads the stage's FP64 data and this
+// lane's z and b entries into registers, commit() splits them into the FP32
+// hi / lo parts in shared memory (the caller then syncs the warp), row()
+// returns this lane's row of K z + b in FP64 accuracy and raises kmaxf to
+// the row's |K| sum.  Used by k_res32 and by the fused first refinement pass.
+template <int NX, int NU>
+struct Res32Rows {
+  static constexpr int n = NX, m = NU, nn = n * n, nm = n * m, mmm = m * m;
+  static constexpr int ME = m + (m & 1), H2 = n / 2, M2 = ME / 2, RS = 2 * n + m;
+  static constexpr int CP = (nn + 31) / 32, CB = (nm + 31) / 32, CR = (mmm + 31) / 32;
+  using SW = Rs32Warp<NX, NU>;
+  static constexpr int N4 = SW::N4, M4 = SW::M4;
+  LaneSeg<double, CP> pA, pQ;
+  LaneSeg<double, CB> pB, pM;
+  LaneSeg<double, CR> pR;
+  double zv, b1, b2;  // this lane's z entry and row data
+  const float *s1h, *s1l, *s2h, *s2l, *s3h, *s3l;
+  float kconst, bh, bl;
+  float2 dsp;
+
+  // Row pointers of this lane; the pad column of odd m and s.zero cleared.
+  __device__ __forceinline__ void init(SW &s, int lane, double delta) {
+    if constexpr (ME != m) {
+      float4 *z4 = reinterpret_cast<float4 *>(&s);
+      for (int e = lane; e < (int)(sizeof(SW) / 16); e += 32) z4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    zv = b1 = b2 = 0.0;
+    s1h = s1l = s2h = s2l = s3h = s3l = s.zero;
+    kconst = 0.f;
+    if (lane < n) {
+      s1h = s.Qh + lane * N4; s1l = s.Ql + lane * N4;
+      s2h = s.Mh + lane * M4; s2l = s.Ml + lane * M4;
+      s3h = s.Ath + lane * N4; s3l = s.Atl + lane * N4;
+      kconst = 1.f;
+    } else if (lane < n + m) {
+      const int t = lane - n;
+      s1h = s.Mth + t * N4; s1l = s.Mtl + t * N4;
+      s2h = s.Rh + t * M4; s2l = s.Rl + t * M4;
+      s3h = s.Bth + t * N4; s3l = s.Btl + t * N4;
+    } else if (lane < RS) {
+      const int i = lane - n - m;
+      s1h = s.Ah + i * N4; s1l = s.Al + i * N4;
+      s2h = s.Bh + i * M4; s2l = s.Bl + i * M4;
+      kconst = 1.f + abs_f32_trunc(delta);
+    }
+    if (lane < N4) s.zero[lane] = 0.f;
+    dsp = split_f64(-delta);
+  }
+
+  __device__ __forceinline__ void prefetch(const Inst &I, int st, int lane) {
+    pA.load(I.A + (size_t)st * nn, nn, lane);
+    pQ.load(I.Q + (size_t)st * nn, nn, lane);
+    pB.load(I.B + (size_t)st * nm, nm, lane);
+    pM.load(I.M + (size_t)st * nm, nm, lane);
+    pR.load(I.R + (size_t)st * mmm, mmm, lane);
+    if (lane < n) {
+      zv = __ldg(I.x + (size_t)st * n + lane);
+      b1 = __ldg(I.q + (size_t)st * n + lane);
+      b2 = __ldg(I.y + (size_t)st * n + lane);
+    } else if (lane < n + m) {
+      zv = __ldg(I.u + (size_t)st * m + lane - n);
+      b1 = __ldg(I.r + (size_t)st * m + lane - n);
+    } else if (lane < RS) {
+      const size_t o = (size_t)(st + 1) * n + lane - n - m;
+      zv = __ldg(I.y + o);
+      b1 = __ldg(I.c + o);
+      b2 = __ldg(I.x + o);
+    }
+  }
+
+  // Split the prefetched stage into shared memory (the caller syncs the warp
+  // before and after: the previous stage's rows may still be reading it).
+  __device__ __forceinline__ void commit(SW &s, int lane, unsigned long long &zbits,
+                                         unsigned long long &bbits) {
+    __syncwarp();
+    commit_split<CP, n, N4, N4>(pA, nn, lane, s.Ah, s.Al, s.Ath, s.Atl);
+    commit_split_sym<CP, n, N4>(pQ, lane, s.Qh, s.Ql);
+    commit_split<CB, m, M4, N4>(pB, nm, lane, s.Bh, s.Bl, s.Bth, s.Btl);
+    commit_split<CB, m, M4, N4>(pM, nm, lane, s.Mh, s.Ml, s.Mth, s.Mtl);
+    commit_split_sym<CR, m, M4>(pR, lane, s.Rh, s.Rl);
+    // z entry of this lane and the row's data terms (float-float)
+    bh = 0.f;
+    bl = 0.f;
+    if (lane < RS) {
+      const float2 zs = split_f64(zv);
+      if (lane < n) {
+        s.xh[lane] = zs.x;
+        s.xl[lane] = zs.y;
+        ff_add(bh, bl, split_f64(b1));
+        ff_add(bh, bl, ff_neg(split_f64(b2)));
+      } else if (lane < n + m) {
+        s.uh[lane - n] = zs.x;
+        s.ul[lane - n] = zs.y;
+        ff_add(bh, bl, split_f64(b1));
+      } else {
+        s.yh[lane - n - m] = zs.x;
+        s.yl[lane - n - m] = zs.y;
+        ff_add(bh, bl, split_f64(b1));
+        ff_add(bh, bl, ff_neg(split_f64(b2)));
+        ff_fma(bh, bl, dsp, zs);
+      }
+      zbits = max(zbits, abs_bits(zv));
+      bbits = max(bbits, abs_bits(b1));
+    }
+  }
+
+  // This lane's row (lane < RS) after commit() and a warp sync.
+  __device__ __forceinline__ double row(const SW &s, int lane, float &kmaxf) const {
+    float2 sh = make_float2(bh, 0.f), sl = make_float2(bl, 0.f), ka = make_float2(kconst, 0.f);
+    {
+      float2 ch[H2], cl[H2], zh[H2], zl[H2];
+      lds_row2<n>(s1h, ch);
+      lds_row2<n>(s1l, cl);
+      lds_row2<n>(s.xh, zh);
+      lds_row2<n>(s.xl, zl);
+#pragma unroll
+      for (int q = 0; q < H2; ++q)
+        ff2_fma(sh, sl, ch[q], cl[q], zh[q], make_float2(-zh[q].x, -zh[q].y), zl[q]);
+      ka = abs_sum2<n>(ch, ka);
+    }
+    {
+      float2 ch[M2], cl[M2], zh[M2], zl[M2];
+      lds_row2<ME>(s2h, ch);
+      lds_row2<ME>(s2l, cl);
+      lds_row2<ME>(s.uh, zh);
+      lds_row2<ME>(s.ul, zl);
+#pragma unroll
+      for (int q = 0; q < M2; ++q)
+        ff2_fma(sh, sl, ch[q], cl[q], zh[q], make_float2(-zh[q].x, -zh[q].y), zl[q]);
+      ka = abs_sum2<ME>(ch, ka);
+    }
+    {
+      float2 ch[H2], cl[H2], zh[H2], zl[H2];
+      lds_row2<n>(s3h, ch);
+      lds_row2<n>(s3l, cl);
+      lds_row2<n>(s.yh, zh);
+      lds_row2<n>(s.yl, zl);
+#pragma unroll
+      for (int q = 0; q < H2; ++q)
+        ff2_fma(sh, sl, ch[q], cl[q], zh[q], make_float2(-zh[q].x, -zh[q].y), zl[q]);
+      ka = abs_sum2<n>(ch, ka);
+    }
+    // merge the two accumulators of the pair
+    float h0 = sh.x, l0 = sl.x;
+    ff_add(h0, l0, make_float2(sh.y, sl.y));
+    kmaxf = fmaxf(kmaxf, ka.x + ka.y);
+    return widen(h0) + widen(l0);
+  }
+};
+
+// Rows x_N (Q_N x_N + q_N - y_N) and c_0 (c_0 - delta y_0 - x_0) in FP64,
+// row r < 2n of the pair; the maxima of the backward error are raised.
+__device__ __forceinline__ double res_end_row(const Inst &I, int r, float &kmaxf,
+                                              unsigned long long &zbits,
+                                              unsigned long long &bbits) {
+  const int N = I.N, n = I.n, nn = n * n;
+  double v;
+  if (r < n) {
+    const double *QN = I.Q + (size_t)N * nn, *xN = I.x + (size_t)N * n;
+    const double qv = __ldg(I.q + (size_t)N * n + r), yv = __ldg(I.y + (size_t)N * n + r);
+    v = qv - yv;
+    float ra = 1.f;
+    for (int j = 0; j < n; ++j) {
+      const double q = (r <= j) ? __ldg(QN + r * n + j) : __ldg(QN + j * n + r);
+      v = fma(q, __ldg(xN + j), v);
+      ra += abs_f32_trunc(q);
+    }
+    zbits = max(zbits, max(abs_bits(__ldg(xN + r)), abs_bits(yv)));
+    kmaxf = fmaxf(kmaxf, ra);
+    bbits = max(bbits, abs_bits(qv));
+  } else {
+    const int i = r - n;
+    const double xv = __ldg(I.x + i), yv = __ldg(I.y + i), cv = __ldg(I.c + i);
+    v = cv - I.delta * yv - xv;
+    zbits = max(zbits, max(abs_bits(xv), abs_bits(yv)));
+    kmaxf = fmaxf(kmaxf, 1.f + abs_f32_trunc(I.delta));
+    bbits = max(bbits, abs_bits(cv));
+  }
+  return v;
+}
+
 // store: write res into the workspace for the refinement; cert_g: FP64
 // certificate of the stored control pivots (bit1 of the flags).
 template <int NX, int NU>
@@ -144,22 +326,14 @@ template <int NX, int NU>
 __device__ __forceinline__ void res32_instance(const BatchArgs &a, int slot, int store, int cert_g,
                                                unsigned char *smem_raw) {
   static_assert(res32_fits<NX, NU>(), "dimensions outside the warp residual");
-  constexpr int n = NX, m = NU, nn = n * n, nm = n * m, mmm = m * m;
-  constexpr int ME = m + (m & 1);  // control segments padded to an even length
-  constexpr int H2 = n / 2, M2 = ME / 2, RS = 2 * n + m;
+  constexpr int n = NX, m = NU, mmm = m * m, RS = 2 * n + m;
   using SW = Rs32Warp<NX, NU>;
-  constexpr int N4 = SW::N4, M4 = SW::M4;
   __shared__ double s_red[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   SW &s = reinterpret_cast<SW *>(smem_raw)[warp];
   const int b = inst_of(a, slot);
   const Inst I = get_inst(a, b);
   if (a.recheck && (I.st->converged || I.st->pivot_status == RLQR_ERR_SINGULAR)) return;
-  if constexpr (ME != m) {
-    // the pad column of the control segments reads zeros
-    float4 *z4 = reinterpret_cast<float4 *>(&s);
-    for (int e = lane; e < (int)(sizeof(SW) / 16); e += 32) z4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
   const int N = I.N;
   const double delta = I.delta;
   double *rq = reinterpret_cast<double *>(I.ws + I.L.res);
@@ -188,130 +362,18 @@ __device__ __forceinline__ void res32_instance(const BatchArgs &a, int slot, int
   }
 
   // ---- residual rows of the stages of this warp
-  constexpr int CP = (nn + 31) / 32, CB = (nm + 31) / 32, CR = (mmm + 31) / 32;
-  LaneSeg<double, CP> pA, pQ;
-  LaneSeg<double, CB> pB, pM;
-  LaneSeg<double, CR> pR;
-  double zv = 0.0, b1 = 0.0, b2 = 0.0;  // this lane's z entry and row data
-  // lane roles: x row i = lane, u row t = lane - n, c row i = lane - n - m
-  const float *s1h = s.zero, *s1l = s.zero, *s2h = s.zero, *s2l = s.zero, *s3h = s.zero,
-              *s3l = s.zero;
-  float kconst = 0.f;
-  if (lane < n) {
-    s1h = s.Qh + lane * N4; s1l = s.Ql + lane * N4;
-    s2h = s.Mh + lane * M4; s2l = s.Ml + lane * M4;
-    s3h = s.Ath + lane * N4; s3l = s.Atl + lane * N4;
-    kconst = 1.f;
-  } else if (lane < n + m) {
-    const int t = lane - n;
-    s1h = s.Mth + t * N4; s1l = s.Mtl + t * N4;
-    s2h = s.Rh + t * M4; s2l = s.Rl + t * M4;
-    s3h = s.Bth + t * N4; s3l = s.Btl + t * N4;
-  } else if (lane < RS) {
-    const int i = lane - n - m;
-    s1h = s.Ah + i * N4; s1l = s.Al + i * N4;
-    s2h = s.Bh + i * M4; s2l = s.Bl + i * M4;
-    kconst = 1.f + abs_f32_trunc(delta);
-  }
-  auto prefetch = [&](int st) {
-    pA.load(I.A + (size_t)st * nn, nn, lane);
-    pQ.load(I.Q + (size_t)st * nn, nn, lane);
-    pB.load(I.B + (size_t)st * nm, nm, lane);
-    pM.load(I.M + (size_t)st * nm, nm, lane);
-    pR.load(I.R + (size_t)st * mmm, mmm, lane);
-    if (lane < n) {
-      zv = __ldg(I.x + (size_t)st * n + lane);
-      b1 = __ldg(I.q + (size_t)st * n + lane);
-      b2 = __ldg(I.y + (size_t)st * n + lane);
-    } else if (lane < n + m) {
-      zv = __ldg(I.u + (size_t)st * m + lane - n);
-      b1 = __ldg(I.r + (size_t)st * m + lane - n);
-    } else if (lane < RS) {
-      const size_t o = (size_t)(st + 1) * n + lane - n - m;
-      zv = __ldg(I.y + o);
-      b1 = __ldg(I.c + o);
-      b2 = __ldg(I.x + o);
-    }
-  };
-  if (lane < N4) s.zero[lane] = 0.f;
+  Res32Rows<NX, NU> R;
+  R.init(s, lane, delta);
   float kmaxf = 0.f;
   unsigned long long rbits = 0, zbits = 0, bbits = 0;
-  const float2 dsp = split_f64(-delta);
   int st = warp;
-  if (st < N) prefetch(st);
+  if (st < N) R.prefetch(I, st, lane);
   for (; st < N; st += kResWarps) {
-    __syncwarp();
-    commit_split<CP, n, N4, N4>(pA, nn, lane, s.Ah, s.Al, s.Ath, s.Atl);
-    commit_split_sym<CP, n, N4>(pQ, lane, s.Qh, s.Ql);
-    commit_split<CB, m, M4, N4>(pB, nm, lane, s.Bh, s.Bl, s.Bth, s.Btl);
-    commit_split<CB, m, M4, N4>(pM, nm, lane, s.Mh, s.Ml, s.Mth, s.Mtl);
-    commit_split_sym<CR, m, M4>(pR, lane, s.Rh, s.Rl);
-    // z entry of this lane and the row's data terms (float-float)
-    const double z = zv, d1 = b1, d2 = b2;
-    float bh = 0.f, bl = 0.f;
-    if (lane < RS) {
-      const float2 zs = split_f64(z);
-      if (lane < n) {
-        s.xh[lane] = zs.x;
-        s.xl[lane] = zs.y;
-        ff_add(bh, bl, split_f64(d1));
-        ff_add(bh, bl, ff_neg(split_f64(d2)));
-      } else if (lane < n + m) {
-        s.uh[lane - n] = zs.x;
-        s.ul[lane - n] = zs.y;
-        ff_add(bh, bl, split_f64(d1));
-      } else {
-        s.yh[lane - n - m] = zs.x;
-        s.yl[lane - n - m] = zs.y;
-        ff_add(bh, bl, split_f64(d1));
-        ff_add(bh, bl, ff_neg(split_f64(d2)));
-        ff_fma(bh, bl, dsp, zs);
-      }
-      zbits = max(zbits, abs_bits(z));
-      bbits = max(bbits, abs_bits(d1));
-    }
-    if (st + kResWarps < N) prefetch(st + kResWarps);
+    R.commit(s, lane, zbits, bbits);
+    if (st + kResWarps < N) R.prefetch(I, st + kResWarps, lane);
     __syncwarp();
     if (lane < RS) {
-      float2 sh = make_float2(bh, 0.f), sl = make_float2(bl, 0.f), ka = make_float2(kconst, 0.f);
-      {
-        float2 ch[H2], cl[H2], zh[H2], zl[H2];
-        lds_row2<n>(s1h, ch);
-        lds_row2<n>(s1l, cl);
-        lds_row2<n>(s.xh, zh);
-        lds_row2<n>(s.xl, zl);
-#pragma unroll
-        for (int q = 0; q < H2; ++q)
-          ff2_fma(sh, sl, ch[q], cl[q], zh[q], make_float2(-zh[q].x, -zh[q].y), zl[q]);
-        ka = abs_sum2<n>(ch, ka);
-      }
-      {
-        float2 ch[M2], cl[M2], zh[M2], zl[M2];
-        lds_row2<ME>(s2h, ch);
-        lds_row2<ME>(s2l, cl);
-        lds_row2<ME>(s.uh, zh);
-        lds_row2<ME>(s.ul, zl);
-#pragma unroll
-        for (int q = 0; q < M2; ++q)
-          ff2_fma(sh, sl, ch[q], cl[q], zh[q], make_float2(-zh[q].x, -zh[q].y), zl[q]);
-        ka = abs_sum2<ME>(ch, ka);
-      }
-      {
-        float2 ch[H2], cl[H2], zh[H2], zl[H2];
-        lds_row2<n>(s3h, ch);
-        lds_row2<n>(s3l, cl);
-        lds_row2<n>(s.yh, zh);
-        lds_row2<n>(s.yl, zl);
-#pragma unroll
-        for (int q = 0; q < H2; ++q)
-          ff2_fma(sh, sl, ch[q], cl[q], zh[q], make_float2(-zh[q].x, -zh[q].y), zl[q]);
-        ka = abs_sum2<n>(ch, ka);
-      }
-      // merge the two accumulators of the pair
-      float h0 = sh.x, l0 = sl.x;
-      ff_add(h0, l0, make_float2(sh.y, sl.y));
-      const double v = widen(h0) + widen(l0);
-      kmaxf = fmaxf(kmaxf, ka.x + ka.y);
+      const double v = R.row(s, lane, kmaxf);
       rbits = max(rbits, abs_bits(v));
       if (store) {
         if (lane < n) rq[(size_t)st * n + lane] = v;
@@ -322,29 +384,10 @@ __device__ __forceinline__ void res32_instance(const BatchArgs &a, int slot, int
   }
   // ---- rows x_N (Q_N x_N + q_N - y_N) and c_0 (c_0 - delta y_0 - x_0), FP64
   for (int r = threadIdx.x; r < 2 * n; r += blockDim.x) {
-    double v;
-    if (r < n) {
-      const double *QN = I.Q + (size_t)N * nn, *xN = I.x + (size_t)N * n;
-      const double qv = __ldg(I.q + (size_t)N * n + r), yv = __ldg(I.y + (size_t)N * n + r);
-      v = qv - yv;
-      float ra = 1.f;
-      for (int j = 0; j < n; ++j) {
-        const double q = (r <= j) ? __ldg(QN + r * n + j) : __ldg(QN + j * n + r);
-        v = fma(q, __ldg(xN + j), v);
-        ra += abs_f32_trunc(q);
-      }
-      zbits = max(zbits, max(abs_bits(__ldg(xN + r)), abs_bits(yv)));
-      kmaxf = fmaxf(kmaxf, ra);
-      bbits = max(bbits, abs_bits(qv));
-      if (store) rq[(size_t)N * n + r] = v;
-    } else {
-      const int i = r - n;
-      const double xv = __ldg(I.x + i), yv = __ldg(I.y + i), cv = __ldg(I.c + i);
-      v = cv - delta * yv - xv;
-      zbits = max(zbits, max(abs_bits(xv), abs_bits(yv)));
-      kmaxf = fmaxf(kmaxf, 1.f + abs_f32_trunc(delta));
-      bbits = max(bbits, abs_bits(cv));
-      if (store) rc[i] = v;
+    const double v = res_end_row(I, r, kmaxf, zbits, bbits);
+    if (store) {
+      if (r < n) rq[(size_t)N * n + r] = v;
+      else rc[r - n] = v;
     }
     rbits = max(rbits, abs_bits(v));
   }

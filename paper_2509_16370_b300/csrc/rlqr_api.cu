@@ -62,6 +62,19 @@ static cudaError_t launch_grid_residual(const BatchArgs &a, const int64_t *spre,
   return cudaGetLastError();
 }
 
+// FP64 certificate with margin of every stored FP32 control pivot of a batch
+// (k_certb), without a residual: the fused route's first refinement pass
+// computes that.
+static cudaError_t launch_cert_g(const BatchArgs &a, const int64_t *spre, int64_t items,
+                                 cudaStream_t s) {
+  BatchArgs ab = a;
+  ab.perm = nullptr;
+  ab.goff = 0;
+  LaunchScope ls("k_cert_g", s);
+  k_certb<<<(int)std::min<int64_t>((items + 255) / 256, 148 * 16), 256, 0, s>>>(ab, spre, items);
+  return cudaGetLastError();
+}
+
 // First residual of a uniform launch group (or one instance): stored for the
 // refinement and certifying the control pivots when cert_g (mixed), or the
 // FP64 backward error only.  The sizes of the FP32 warp sweeps take the
@@ -73,7 +86,8 @@ static bool warp_res32_size(int n, int m) {
 
 // Residual route of a uniform launch group of a warp size: 0 = by size (the
 // warp residual), 1 = the warp residual, 2 = the stage-parallel grid
-// residual.  Batches record the autotuner's choice (rlqr_autotune_batched)
+// residual, 5 = (mixed, with refinement) no separate first residual: the
+// first refinement pass computes it.  Batches record the autotuner's choice (rlqr_autotune_batched)
 // per (nx, nu, precision, floor(log2 max N), floor(log2 count)).
 static std::mutex g_route_mu;
 static std::map<uint64_t, int> g_res_route;
@@ -733,8 +747,15 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
       nmaxN = std::max(nmaxN, B.h_N[b]);
     }
     const int route = uniform ? residual_route(nmaxN, nmax, mmax, a.tsize, B.count) : 0;
-    e = uniform ? launch_first_residual(a, nmax, mmax, mixed, 1, spre, items, s, route)
-                : launch_grid_residual(a, spre, items, mixed, 1, s);
+    if (mixed && uniform && route == 5 && opts->max_refine > 0 && warp_res32_size(nmax, mmax)) {
+      // fused route: the control-pivot certificate alone here; the first
+      // refinement pass computes the residual as it goes
+      a.fused_res = 1;
+      e = launch_cert_g(a, spre, items, s);
+    } else {
+      e = uniform ? launch_first_residual(a, nmax, mmax, mixed, 1, spre, items, s, route)
+                  : launch_grid_residual(a, spre, items, mixed, 1, s);
+    }
     if (e == cudaSuccess && mixed) {
       if (cs && opts->max_refine > 0) {
         // the FP64 re-decision changes only flags and pivot status, which
@@ -1163,7 +1184,9 @@ rlqr_status rlqr_tune_batched_set(const rlqr_batch *batch, const rlqr_opts *opts
   uint64_t key;
   bool ragged = false;
   if (!batch_tune_key(batch, opts, &key, &ragged) || route < 0) return RLQR_ERR_ARG;
-  if (route != 0 && (ragged ? (route < 3 || route > 4) : route > 2)) return RLQR_ERR_ARG;
+  if (route != 0 && (ragged ? (route < 3 || route > 4)
+                            : !(route == 1 || route == 2 || (route == 5 && opts->prec == RLQR_MIXED))))
+    return RLQR_ERR_ARG;
   std::lock_guard<std::mutex> lock(g_route_mu);
   if (route == 0)
     g_res_route.erase(key);
@@ -1191,8 +1214,17 @@ rlqr_status rlqr_autotune_batched(const rlqr_batch *batch, const rlqr_opts *opts
   int best = 0;
   float best_t = 0.0f;
   const int reps = 3;
-  const int r0 = ragged ? 3 : 1;
-  for (int route = r0; route <= r0 + 1 && err == RLQR_OK; ++route) {
+  int cand[3], nc = 0;
+  if (ragged) {
+    cand[nc++] = 3;
+    cand[nc++] = 4;
+  } else {
+    cand[nc++] = 1;
+    cand[nc++] = 2;
+    if (opts->prec == RLQR_MIXED && opts->max_refine > 0) cand[nc++] = 5;
+  }
+  for (int ci = 0; ci < nc && err == RLQR_OK; ++ci) {
+    const int route = cand[ci];
     err = rlqr_tune_batched_set(batch, opts, route);
     float t = 0.0f;
     for (int r = 0; r <= reps && err == RLQR_OK; ++r) {  // r = 0: warm-up

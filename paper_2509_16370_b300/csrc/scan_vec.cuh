@@ -190,7 +190,6 @@ __global__ void __launch_bounds__(32) k_scan_pvec(BatchArgs a, ScanLayout SL, si
   if (MODE == 0 && lane < n) phi[(size_t)c * n + lane] = s.p[lane];
 }
 
-// p at the chunk starts: pb[C] = q'_N, pb[c] = Phi_c pb[c+1] + phi_c.  One warp.
 // Depth of the register rings of the boundary passes (chunks in flight).
 template <typename T>
 __host__ __device__ constexpr int bound_ring_depth() {
@@ -231,6 +230,7 @@ __device__ __forceinline__ void ld_vec_row(const T *src, T (&dst)[NX]) {
   for (int l = 0; l < NX; ++l) dst[l] = __ldcg(src + l);
 }
 
+// p at the chunk starts: pb[C] = q'_N, pb[c] = Phi_c pb[c+1] + phi_c.  One warp.
 template <typename T, int NX, bool FROM_RES>
 __global__ void __launch_bounds__(32) k_scan_pbound(BatchArgs a, ScanLayout SL, size_t sbase) {
   constexpr int n = NX, nn = n * n;

@@ -482,7 +482,7 @@ def rlqr_tune_reset():
     _check(lib.rlqr_tune_reset(), "rlqr_tune_reset")
 
 
-RES_ROUTE_WARP, RES_ROUTE_GRID = 1, 2
+RES_ROUTE_WARP, RES_ROUTE_GRID, RES_ROUTE_FUSED = 1, 2, 5
 SWEEP_ROUTE_STREAMS, SWEEP_ROUTE_PERSISTENT = 3, 4
 
 

@@ -67,25 +67,46 @@ def test_autotuner_choice_and_solves_after_it():
         rlqr.rlqr_tune_reset()
 
 
-@pytest.mark.parametrize("prec", [rlqr.RLQR_FP64, rlqr.RLQR_MIXED])
-def test_both_batched_residual_routes_are_exact_and_the_tuner_picks_one(prec):
+@pytest.mark.parametrize("prec,nm", [(rlqr.RLQR_FP64, (12, 4)), (rlqr.RLQR_MIXED, (12, 4)),
+                                     (rlqr.RLQR_MIXED, (6, 1))])
+def test_every_batched_residual_route_is_exact_and_the_tuner_picks_one(prec, nm):
+    """Routes 1 (warp residual), 2 (grid residual) and, mixed, 5 (the first
+    refinement pass computes the residual itself): the oracle's flags, its
+    backward error <= 1e-9 for every instance, the reported backward error
+    an upper bound of the oracle's, the same statuses on every route."""
     from tests.gpu_helpers import REL_TOL
-    probs = [inputs.random_instance(300 + b, 96 + 8 * (b % 5), 12, 4, 1e-3) for b in range(64)]
+    n, m = nm
+    probs = [inputs.random_instance(300 + b, 96 + 8 * (b % 5), n, m, 1e-3) for b in range(64)]
+    probs[7].Q[20] -= 3.0 * np.eye(n)  # a non-PD pivot somewhere in the batch
     db = rlqr.DeviceBatch.from_problems(probs)
     opts = rlqr.make_opts(prec, tol=1e-9, max_refine=4)
     ws = rlqr.alloc_workspace(rlqr.rlqr_batched_workspace_bytes(db, opts))
     st = torch.zeros(db.count, dtype=torch.int32, device="cuda")
+    rel = torch.zeros(db.count, dtype=torch.float64, device="cuda")
     refs = [oracle.riccati(p) for p in probs]
+    routes = [rlqr.RES_ROUTE_WARP, rlqr.RES_ROUTE_GRID]
+    if prec == rlqr.RLQR_MIXED:
+        routes.append(rlqr.RES_ROUTE_FUSED)
+    statuses = []
     try:
-        for route in (rlqr.RES_ROUTE_WARP, rlqr.RES_ROUTE_GRID):
+        for route in routes:
             rlqr.rlqr_tune_batched_set(db, opts, route)
-            rlqr.rlqr_solve_batched(db, opts, ws, st)
+            rlqr.rlqr_solve_batched(db, opts, ws, st, rel)
             torch.cuda.synchronize()
+            rels = rel.cpu().numpy()
             for b, p in enumerate(probs):
                 x, u, y, f = db.instance_view(b)
-                np.testing.assert_array_equal(f, refs[b].flags)
-                assert oracle.residual(p, x, u, y).rel <= REL_TOL
+                np.testing.assert_array_equal(f, refs[b].flags, err_msg=f"route {route} {b}")
+                r = oracle.residual(p, x, u, y).rel
+                assert r <= REL_TOL, (route, b, r)
+                assert rels[b] <= REL_TOL and r <= 1.05 * rels[b] + 1e-15, (route, b, r, rels[b])
+            statuses.append(st.cpu().numpy().copy())
+        for sv in statuses[1:]:
+            np.testing.assert_array_equal(sv, statuses[0])
         route, ms = rlqr.rlqr_autotune_batched(db, opts, ws, st)
-        assert route in (rlqr.RES_ROUTE_WARP, rlqr.RES_ROUTE_GRID) and ms > 0
+        assert route in routes and ms > 0
+        if prec == rlqr.RLQR_FP64:
+            with pytest.raises(rlqr.RlqrError):
+                rlqr.rlqr_tune_batched_set(db, opts, rlqr.RES_ROUTE_FUSED)
     finally:
         rlqr.rlqr_tune_reset()
