@@ -67,6 +67,22 @@ rlqr_status rlqr_mlp_adam(const rlqr_mlp_dims *d, float *params, uint16_t *param
                           float *m, float *v, const float *grad, int32_t step, float lr,
                           float beta1, float beta2, float eps, rlqr_stream_t stream);
 
+/* One training step (rlqr_mlp_grad, then rlqr_mlp_adam: the same kernels)
+ * whose step-dependent inputs are read on the device, so that the call can
+ * be captured once into a CUDA graph and replayed for consecutive steps.
+ * With s = *counter (device int32: steps of the sequence done so far) the
+ * batch is the rows indices idx_all[s rows .. s rows + rows) and the Adam
+ * step takes lr = sched[3 s], the bias corrections c1 = sched[3 s + 1] =
+ * 1 - beta1^t and c2 = sched[3 s + 2] = 1 - beta2^t (t its global step
+ * number); the call then increments *counter on the device.  idx_all,
+ * sched, counter and loss are device pointers; the caller sizes idx_all
+ * and sched for every step it replays. */
+rlqr_status rlqr_mlp_train_step(const rlqr_mlp_dims *d, float *params, uint16_t *params_bf16,
+                                float *m, float *v, float *grad, const float *x, const float *t,
+                                const int32_t *idx_all, int32_t rows, int32_t *counter,
+                                const float *sched, float beta1, float beta2, float eps,
+                                float *loss, void *ws, size_t ws_bytes, rlqr_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -98,10 +98,19 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const bf16 *A
   wm::store_matrix_sync(C + (size_t)m0 * N + n0, acc, N, wm::mem_row_major);
 }
 
-__global__ void k_input(const float *x, const int32_t *idx, int rows, int n_in, bf16 *a0) {
+// Row indices of a batch: idx, advanced by *counter batches when counter is
+// given (a graph-replayed training step reads its batch on the device).
+__device__ __forceinline__ const int32_t *batch_rows(const int32_t *idx, const int32_t *counter,
+                                                     int rows) {
+  return (idx && counter) ? idx + (size_t)(*counter) * rows : idx;
+}
+
+__global__ void k_input(const float *x, const int32_t *idx0, const int32_t *counter, int rows,
+                        int n_in, bf16 *a0) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= rows * 16) return;
   const int r = e >> 4, c = e & 15;
+  const int32_t *idx = batch_rows(idx0, counter, rows);
   const int64_t src = idx ? idx[r] : r;
   a0[e] = __float2bfloat16_rn(c < n_in ? x[src * n_in + c] : 0.0f);
 }
@@ -123,10 +132,12 @@ __global__ void k_bias_out(const float *C, const bf16 *b, int rows, int npad, in
 // dy = bf16(2 (y - t) / (rows n_out)) on the real columns (0 on the padding),
 // per-row partial sums of (y - t)^2 (one block per row).
 __global__ void __launch_bounds__(256) k_loss_grad(const float *C, const bf16 *b, const float *t,
-                                                   const int32_t *idx, int rows, int npad,
-                                                   int n_out, bf16 *dy, float *part) {
+                                                   const int32_t *idx0, const int32_t *counter,
+                                                   int rows, int npad, int n_out, bf16 *dy,
+                                                   float *part) {
   __shared__ float sh[8];
   const int r = blockIdx.x;
+  const int32_t *idx = batch_rows(idx0, counter, rows);
   const float scale = 2.0f / ((float)rows * (float)n_out);
   float acc = 0.0f;
   for (int c = threadIdx.x; c < npad; c += blockDim.x) {
@@ -186,10 +197,19 @@ __global__ void k_to_bf16(const float *p, size_t n, bf16 *q) {
   if (e < n) q[e] = __float2bfloat16_rn(p[e]);
 }
 
+// Adam; with sched / counter given, lr, c1, c2 = sched[3 s .. 3 s + 2] for
+// s = *counter instead of the arguments.
 __global__ void k_adam(float *p, bf16 *q, float *m, float *v, const float *g, size_t n, float lr,
-                       float b1, float b2, float eps, float c1, float c2) {
+                       float b1, float b2, float eps, float c1, float c2, const float *sched,
+                       const int32_t *counter) {
   const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (e >= n) return;
+  if (sched) {
+    const float *sc = sched + 3 * (size_t)(*counter);
+    lr = sc[0];
+    c1 = sc[1];
+    c2 = sc[2];
+  }
   const float gg = g[e];
   const float mm = b1 * m[e] + (1.0f - b1) * gg;
   const float vv = b2 * v[e] + (1.0f - b2) * gg * gg;
@@ -199,6 +219,8 @@ __global__ void k_adam(float *p, bf16 *q, float *m, float *v, const float *g, si
   p[e] = pn;
   q[e] = __float2bfloat16_rn(pn);
 }
+
+__global__ void k_counter_inc(int32_t *counter) { *counter += 1; }
 
 template <bool AT, bool BT>
 cudaError_t gemm(int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb, float *C,
@@ -213,14 +235,14 @@ inline int blocks(size_t n, int t = 256) { return (int)((n + t - 1) / t); }
 // Forward pass of `rows` rows into the workspace (h1, h2 and the output
 // pre-bias product in w.y); returns the first CUDA error.
 cudaError_t forward(const rlqr_mlp_dims &d, const bf16 *q, const float *x, const int32_t *idx,
-                    int rows, char *ws, cudaStream_t s) {
+                    const int32_t *counter, int rows, char *ws, cudaStream_t s) {
   const Off o = offsets(d);
   const Ws w = ws_layout(d);
   const int W = d.width, P = o.npad;
   bf16 *a0 = reinterpret_cast<bf16 *>(ws + w.a0), *h1 = reinterpret_cast<bf16 *>(ws + w.h1);
   bf16 *h2 = reinterpret_cast<bf16 *>(ws + w.h2);
   float *c = reinterpret_cast<float *>(ws + w.c), *y = reinterpret_cast<float *>(ws + w.y);
-  k_input<<<blocks((size_t)rows * 16), 256, 0, s>>>(x, idx, rows, d.n_in, a0);
+  k_input<<<blocks((size_t)rows * 16), 256, 0, s>>>(x, idx, counter, rows, d.n_in, a0);
   cudaError_t e = gemm<false, true>(rows, W, 16, a0, 16, q + o.W1, 16, c, s);
   if (e != cudaSuccess) return e;
   k_bias_relu<<<blocks((size_t)rows * W), 256, 0, s>>>(c, q + o.b1, rows, W, h1);
@@ -234,6 +256,35 @@ cudaError_t forward(const rlqr_mlp_dims &d, const bf16 *q, const float *x, const
 }  // namespace rlqr
 
 using namespace rlqr::mlp;
+
+// The loss and gradient of a batch (rows of x, t selected by idx, advanced on
+// the device by *counter batches when counter is given).
+static cudaError_t grad_impl(const rlqr_mlp_dims &d, const bf16 *q, const float *x, const float *t,
+                             const int32_t *idx, const int32_t *counter, int rows, float *loss,
+                             float *grad, char *w, cudaStream_t s) {
+  if (cudaError_t e = forward(d, q, x, idx, counter, rows, w, s)) return e;
+  const Off o = offsets(d);
+  const Ws L = ws_layout(d);
+  const int W = d.width, P = o.npad;
+  bf16 *a0 = reinterpret_cast<bf16 *>(w + L.a0), *h1 = reinterpret_cast<bf16 *>(w + L.h1);
+  bf16 *h2 = reinterpret_cast<bf16 *>(w + L.h2), *dy = reinterpret_cast<bf16 *>(w + L.dy);
+  bf16 *dz2 = reinterpret_cast<bf16 *>(w + L.dz2), *dz1 = reinterpret_cast<bf16 *>(w + L.dz1);
+  float *dh = reinterpret_cast<float *>(w + L.dh), *part = reinterpret_cast<float *>(w + L.part);
+  k_loss_grad<<<rows, 256, 0, s>>>(reinterpret_cast<float *>(w + L.y), q + o.b3, t, idx, counter,
+                                   rows, P, d.n_out, dy, part);
+  k_loss_final<<<1, 32, 0, s>>>(part, rows, rows, d.n_out, loss);
+  if (cudaError_t e = gemm<true, false>(P, W, rows, dy, P, h2, W, grad + o.W3, s)) return e;
+  k_colsum<<<(P + 31) / 32, dim3(32, 8), 0, s>>>(dy, rows, P, grad + o.b3);
+  if (cudaError_t e = gemm<false, false>(rows, W, P, dy, P, q + o.W3, W, dh, s)) return e;
+  k_relu_back<<<blocks((size_t)rows * W), 256, 0, s>>>(dh, h2, rows * W, dz2);
+  if (cudaError_t e = gemm<true, false>(W, W, rows, dz2, W, h1, W, grad + o.W2, s)) return e;
+  k_colsum<<<(W + 31) / 32, dim3(32, 8), 0, s>>>(dz2, rows, W, grad + o.b2);
+  if (cudaError_t e = gemm<false, false>(rows, W, W, dz2, W, q + o.W2, W, dh, s)) return e;
+  k_relu_back<<<blocks((size_t)rows * W), 256, 0, s>>>(dh, h1, rows * W, dz1);
+  if (cudaError_t e = gemm<true, false>(W, 16, rows, dz1, W, a0, 16, grad + o.W1, s)) return e;
+  k_colsum<<<(W + 31) / 32, dim3(32, 8), 0, s>>>(dz1, rows, W, grad + o.b1);
+  return cudaGetLastError();
+}
 
 extern "C" {
 
@@ -266,7 +317,7 @@ rlqr_status rlqr_mlp_forward(const rlqr_mlp_dims *d, const uint16_t *params_bf16
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   char *w = static_cast<char *>(ws);
   const bf16 *q = reinterpret_cast<const bf16 *>(params_bf16);
-  if (forward(*d, q, x, nullptr, rows, w, s) != cudaSuccess) return RLQR_ERR_CUDA;
+  if (forward(*d, q, x, nullptr, nullptr, rows, w, s) != cudaSuccess) return RLQR_ERR_CUDA;
   const Off o = offsets(*d);
   const Ws L = ws_layout(*d);
   k_bias_out<<<blocks((size_t)rows * d->n_out), 256, 0, s>>>(
@@ -283,36 +334,11 @@ rlqr_status rlqr_mlp_grad(const rlqr_mlp_dims *d, const uint16_t *params_bf16, c
       reinterpret_cast<uintptr_t>(grad) % 32)
     return RLQR_ERR_ARG;
   if (!ws_ok(d, ws, ws_bytes)) return RLQR_ERR_WORKSPACE;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  char *w = static_cast<char *>(ws);
-  const bf16 *q = reinterpret_cast<const bf16 *>(params_bf16);
-  if (forward(*d, q, x, idx, rows, w, s) != cudaSuccess) return RLQR_ERR_CUDA;
-  const Off o = offsets(*d);
-  const Ws L = ws_layout(*d);
-  const int W = d->width, P = o.npad;
-  bf16 *a0 = reinterpret_cast<bf16 *>(w + L.a0), *h1 = reinterpret_cast<bf16 *>(w + L.h1);
-  bf16 *h2 = reinterpret_cast<bf16 *>(w + L.h2), *dy = reinterpret_cast<bf16 *>(w + L.dy);
-  bf16 *dz2 = reinterpret_cast<bf16 *>(w + L.dz2), *dz1 = reinterpret_cast<bf16 *>(w + L.dz1);
-  float *dh = reinterpret_cast<float *>(w + L.dh), *part = reinterpret_cast<float *>(w + L.part);
-  k_loss_grad<<<rows, 256, 0, s>>>(reinterpret_cast<float *>(w + L.y), q + o.b3, t, idx, rows,
-                                   P, d->n_out, dy, part);
-  k_loss_final<<<1, 32, 0, s>>>(part, rows, rows, d->n_out, loss);
-  if (gemm<true, false>(P, W, rows, dy, P, h2, W, grad + o.W3, s) != cudaSuccess)
-    return RLQR_ERR_CUDA;
-  k_colsum<<<(P + 31) / 32, dim3(32, 8), 0, s>>>(dy, rows, P, grad + o.b3);
-  if (gemm<false, false>(rows, W, P, dy, P, q + o.W3, W, dh, s) != cudaSuccess)
-    return RLQR_ERR_CUDA;
-  k_relu_back<<<blocks((size_t)rows * W), 256, 0, s>>>(dh, h2, rows * W, dz2);
-  if (gemm<true, false>(W, W, rows, dz2, W, h1, W, grad + o.W2, s) != cudaSuccess)
-    return RLQR_ERR_CUDA;
-  k_colsum<<<(W + 31) / 32, dim3(32, 8), 0, s>>>(dz2, rows, W, grad + o.b2);
-  if (gemm<false, false>(rows, W, W, dz2, W, q + o.W2, W, dh, s) != cudaSuccess)
-    return RLQR_ERR_CUDA;
-  k_relu_back<<<blocks((size_t)rows * W), 256, 0, s>>>(dh, h1, rows * W, dz1);
-  if (gemm<true, false>(W, 16, rows, dz1, W, a0, 16, grad + o.W1, s) != cudaSuccess)
-    return RLQR_ERR_CUDA;
-  k_colsum<<<(W + 31) / 32, dim3(32, 8), 0, s>>>(dz1, rows, W, grad + o.b1);
-  return cudaGetLastError() == cudaSuccess ? RLQR_OK : RLQR_ERR_CUDA;
+  return grad_impl(*d, reinterpret_cast<const bf16 *>(params_bf16), x, t, idx, nullptr, rows, loss,
+                   grad, static_cast<char *>(ws), reinterpret_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? RLQR_OK
+             : RLQR_ERR_CUDA;
 }
 
 rlqr_status rlqr_mlp_adam(const rlqr_mlp_dims *d, float *params, uint16_t *params_bf16,
@@ -325,7 +351,29 @@ rlqr_status rlqr_mlp_adam(const rlqr_mlp_dims *d, float *params, uint16_t *param
   const float c1 = 1.0f - powf(beta1, (float)step), c2 = 1.0f - powf(beta2, (float)step);
   k_adam<<<blocks(n), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
       params, reinterpret_cast<bf16 *>(params_bf16), m, v, grad, n, lr, beta1, beta2, eps, c1,
-      c2);
+      c2, nullptr, nullptr);
+  return cudaGetLastError() == cudaSuccess ? RLQR_OK : RLQR_ERR_CUDA;
+}
+
+rlqr_status rlqr_mlp_train_step(const rlqr_mlp_dims *d, float *params, uint16_t *params_bf16,
+                                float *m, float *v, float *grad, const float *x, const float *t,
+                                const int32_t *idx_all, int32_t rows, int32_t *counter,
+                                const float *sched, float beta1, float beta2, float eps,
+                                float *loss, void *ws, size_t ws_bytes, rlqr_stream_t stream) {
+  if (!valid(d) || !params || !params_bf16 || !m || !v || !grad || !x || !t || !idx_all ||
+      !counter || !sched || !loss || rows < 16 || rows % 16 || rows > d->max_rows ||
+      reinterpret_cast<uintptr_t>(params_bf16) % 32 || reinterpret_cast<uintptr_t>(grad) % 32 ||
+      !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+    return RLQR_ERR_ARG;
+  if (!ws_ok(d, ws, ws_bytes)) return RLQR_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (grad_impl(*d, reinterpret_cast<const bf16 *>(params_bf16), x, t, idx_all, counter, rows,
+                loss, grad, static_cast<char *>(ws), s) != cudaSuccess)
+    return RLQR_ERR_CUDA;
+  const size_t n = offsets(*d).total;
+  k_adam<<<blocks(n), 256, 0, s>>>(params, reinterpret_cast<bf16 *>(params_bf16), m, v, grad, n,
+                                   0.0f, beta1, beta2, eps, 1.0f, 1.0f, sched, counter);
+  k_counter_inc<<<1, 1, 0, s>>>(counter);
   return cudaGetLastError() == cudaSuccess ? RLQR_OK : RLQR_ERR_CUDA;
 }
 

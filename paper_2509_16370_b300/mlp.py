@@ -17,7 +17,7 @@ import torch
 from .rlqr import _check, _ptr, _stream, lib
 
 EXPORTED = ("rlqr_mlp_param_count", "rlqr_mlp_workspace_bytes", "rlqr_mlp_sync_bf16",
-            "rlqr_mlp_forward", "rlqr_mlp_grad", "rlqr_mlp_adam")
+            "rlqr_mlp_forward", "rlqr_mlp_grad", "rlqr_mlp_adam", "rlqr_mlp_train_step")
 
 
 class rlqr_mlp_dims(ctypes.Structure):
@@ -39,6 +39,9 @@ lib.rlqr_mlp_grad.argtypes = [_P(rlqr_mlp_dims), _dp, _dp, _dp, _dp, _i, _dp, _d
                               ctypes.c_size_t, _dp]
 lib.rlqr_mlp_adam.restype = ctypes.c_int
 lib.rlqr_mlp_adam.argtypes = [_P(rlqr_mlp_dims), _dp, _dp, _dp, _dp, _dp, _i, _f, _f, _f, _f, _dp]
+lib.rlqr_mlp_train_step.restype = ctypes.c_int
+lib.rlqr_mlp_train_step.argtypes = [_P(rlqr_mlp_dims), _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _i,
+                                    _dp, _dp, _f, _f, _f, _dp, _dp, ctypes.c_size_t, _dp]
 
 
 def make_dims(n_in, width, n_out, max_rows) -> rlqr_mlp_dims:
@@ -91,6 +94,15 @@ class WarmStartNet:
                                  _ptr(self.v), _ptr(self.g), self.step, lr, b1, b2, eps,
                                  _stream(None)), "rlqr_mlp_adam")
 
+    def train_step(self, x, t, idx_all, rows, counter, sched, b1=0.9, b2=0.999, eps=1e-8):
+        """One step of a device-scheduled sequence (rlqr_mlp_train_step); the
+        caller advances self.step by the steps it replays."""
+        _check(lib.rlqr_mlp_train_step(ctypes.byref(self.d), _ptr(self.p), _ptr(self.q),
+                                       _ptr(self.m), _ptr(self.v), _ptr(self.g), _ptr(x), _ptr(t),
+                                       _ptr(idx_all), rows, _ptr(counter), _ptr(sched), b1, b2,
+                                       eps, _ptr(self.loss), _ptr(self.ws), self.ws.numel(),
+                                       _stream(None)), "rlqr_mlp_train_step")
+
 
 def init_params(d: rlqr_mlp_dims, seed: int) -> np.ndarray:
     """He-uniform weights, zero biases, zero padding (host, seeded)."""
@@ -125,6 +137,60 @@ def train(net: WarmStartNet, x: torch.Tensor, t: torch.Tensor, steps: int, batch
         net.adam(rate)
         if s % 100 == 0 or s == steps - 1:
             losses.append(float(loss.item()))
+    return losses
+
+
+def train_schedule(n: int, steps: int, batch: int, lr: float, seed: int = 0,
+                   lr_final: float | None = None, step0: int = 0, b1: float = 0.9,
+                   b2: float = 0.999):
+    """The batches and Adam constants of train()'s steps, on the host: int32
+    indices [steps][batch] (the same seeded permutations) and FP32 (lr, 1 -
+    b1^t, 1 - b2^t) [steps][3], t = step0 + s + 1 (the C library's powf, as
+    rlqr_mlp_adam forms them on the host)."""
+    powf = _libm_powf()
+    g = torch.Generator().manual_seed(seed)
+    perm, at = torch.randperm(n, generator=g), 0
+    idx = np.empty((steps, batch), np.int32)
+    sched = np.empty((steps, 3), np.float32)
+    one = np.float32(1.0)
+    for s in range(steps):
+        if at + batch > n:
+            perm, at = torch.randperm(n, generator=g), 0
+        idx[s] = perm[at:at + batch].numpy()
+        at += batch
+        rate = lr if lr_final is None else lr * (lr_final / lr) ** (s / max(steps - 1, 1))
+        tt = float(step0 + s + 1)
+        sched[s] = (np.float32(rate), one - np.float32(powf(b1, tt)),
+                    one - np.float32(powf(b2, tt)))
+    return idx, sched
+
+
+def _libm_powf():
+    libm = ctypes.CDLL("libm.so.6")
+    libm.powf.restype = ctypes.c_float
+    libm.powf.argtypes = [ctypes.c_float, ctypes.c_float]
+    return libm.powf
+
+
+def train_graph(net: WarmStartNet, x: torch.Tensor, t: torch.Tensor, steps: int, batch: int,
+                lr: float, seed: int = 0, lr_final: float | None = None) -> list:
+    """train(), with the whole step (gradient and Adam: 19 launches) captured
+    once into a CUDA graph and replayed; the batches and the learning-rate
+    schedule are read on the device.  The same kernels on the same inputs:
+    the parameters equal train()'s.  Returns the loss every 100 steps."""
+    idx, sched = train_schedule(x.shape[0], steps, batch, lr, seed, lr_final, net.step)
+    idx_d = torch.from_numpy(idx).to(x.device)
+    sched_d = torch.from_numpy(sched).to(x.device)
+    counter = torch.zeros(1, dtype=torch.int32, device=x.device)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        net.train_step(x, t, idx_d, batch, counter, sched_d)
+    losses = []
+    for s in range(steps):
+        graph.replay()
+        if s % 100 == 0 or s == steps - 1:
+            losses.append(float(net.loss.item()))
+    net.step += steps
     return losses
 
 

@@ -155,6 +155,26 @@ def test_training_fits_a_teacher_network():
     assert losses[-1] < 0.1 * losses[0]
 
 
+def test_graph_replayed_training_equals_eager_training():
+    """mlp.train_graph (one captured step, batches and schedule read on the
+    device) against mlp.train from the same start: bit-identical parameters,
+    moments and losses after 320 steps over epoch boundaries with a decaying
+    learning rate, and the step counters in agreement."""
+    n_in, width, n_out = 7, 64, 40
+    d, p, a = _net(n_in, width, n_out, 64, 41)
+    _, _, b = _net(n_in, width, n_out, 64, 41)
+    rng = np.random.default_rng(42)
+    X = torch.from_numpy(rng.uniform(-1, 1, size=(1000, n_in)).astype(np.float32)).cuda()
+    T = torch.from_numpy(rng.normal(size=(1000, n_out)).astype(np.float32)).cuda()
+    la = mlp.train(a, X, T, steps=320, batch=64, lr=2e-3, seed=5, lr_final=1e-4)
+    lb = mlp.train_graph(b, X, T, steps=320, batch=64, lr=2e-3, seed=5, lr_final=1e-4)
+    torch.cuda.synchronize()
+    assert la == lb
+    for k in ("p", "q", "m", "v"):
+        assert torch.equal(getattr(a, k), getattr(b, k)), k
+    assert a.step == b.step == 320
+
+
 def test_learned_warm_start_beats_the_cold_start():
     """The network trained (by these kernels) on the converged cold-start
     solutions of 32768 instances, against the plain cold start on 4096
