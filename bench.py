@@ -1134,7 +1134,10 @@ def run_ours(args):
         route, tms = rlqr.rlqr_autotune_batched(db, o_t, ws_t, st_t)
         tune[name] = {"residual_route": {rlqr.RES_ROUTE_WARP: "warp",
                                          rlqr.RES_ROUTE_GRID: "grid",
-                                         rlqr.RES_ROUTE_FUSED: "fused into the first pass"}[route],
+                                         rlqr.RES_ROUTE_FUSED: "fused into the first pass",
+                                         rlqr.RES_ROUTE_WARP_DUO: "warp, two-warp refinement",
+                                         rlqr.RES_ROUTE_FUSED_DUO:
+                                             "fused into the first pass, two-warp refinement"}[route],
                       "ms": round(tms, 4)}
         del ws_t
     with ClockSampler(local) as clk:

@@ -239,15 +239,21 @@ rlqr_status rlqr_tune_scan_set(int32_t N, int32_t nx, int32_t nu, const rlqr_opt
  * of the batch, 5 = (mixed precision, max_refine >= 1) no separate first
  * residual: the control pivots are certified by a grid kernel and the first
  * refinement pass computes the residual (float-float) stage by stage ahead
- * of its backward chain.  Ragged mixed-precision batches whose size classes are all
+ * of its backward chain; 6 and 7 = routes 1 and 5 with every refinement
+ * pass on two warps per instance (one runs the recursion, the other the
+ * copies, right-hand sides, the rows of K dz and, route 7, the residual),
+ * which shortens each instance's chain at more instructions in all.
+ * Without a recorded route the refinement takes two warps per instance when
+ * a launch holds at most 296 instances, else one.  Ragged mixed-precision
+ * batches whose size classes are all
  * among (4,2), (6,2), (12,4), (24,8), (32,8), (48,16): the sweep route,
  * 3 = one launch per size class on the library's concurrent streams (the
  * default), 4 = one persistent launch for every class (CTAs take work items
  * -- 8 instances of a warp size or one of a CTA size, longest chain first --
  * from an atomic counter).
  * rlqr_autotune_batched times rlqr_solve_batched on `batch` with each of
- * its two routes (a warm-up and three timed runs, CUDA events,
- * host-synchronising) and records the faster one for (nx, nu, opts->prec,
+ * its routes (a warm-up and three timed runs, CUDA events,
+ * host-synchronising) and records the fastest for (nx, nu, opts->prec,
  * floor(log2 max N), floor(log2 count)), or for ragged batches (the set of
  * size classes, floor(log2 max N), floor(log2 count)), in the process-wide
  * table; status (device [count], may be NULL) is scratch for the timed

@@ -151,6 +151,10 @@ struct BatchArgs {
   // warp sizes of the mixed path: the first refinement pass computes the
   // residual itself (no separate first-residual launch)
   int fused_res;
+  // warps per instance of the mixed refinement passes of the warp sizes:
+  // 1 (k_refine_tab), 2 (k_refine_duo), 0 = 2 when the launch holds at most
+  // two instances per SM, else 1
+  int refine_warps;
 };
 
 // Instance of a launch slot: the identity, or the group's entry of perm.

@@ -12,6 +12,7 @@
 #include "residual32.cuh"
 #include "seqx.cuh"
 #include "tab32.cuh"
+#include "refine_duo.cuh"
 #include "refine_tab.cuh"
 
 namespace rlqr {
@@ -121,13 +122,25 @@ static cudaError_t launch_solve_warp(const BatchArgs &a, cudaStream_t s) {
     // the factor and the FP32 data copies come from k_sweep32 or k_tab32;
     // the fused route's first pass computes the residual itself
     const bool fused = a.fused_res && a.rpass == 0;
+    // later passes find most instances converged: fewer, striding blocks
+    const int grid = a.rpass == 0 ? a.count : std::min(a.count, 148 * 4);
+    // two warps per instance shorten each instance's chain but issue more
+    // instructions: they win while the SMs hold few instances
+    const bool duo = a.refine_warps == 2 || (a.refine_warps == 0 && a.count <= 2 * 148);
+    if (duo) {
+      auto kern = fused ? k_refine_duo<NX, NU, true> : k_refine_duo<NX, NU, false>;
+      const size_t bytes = refine_duo_smem<NX, NU>();
+      cudaError_t e = set_smem_carveout(kern, bytes);
+      if (e != cudaSuccess) return e;
+      LaunchScope ls(name, s);
+      kern<<<grid, 64, bytes, s>>>(a);
+      return cudaGetLastError();
+    }
     auto kern = fused ? k_refine_tab<NX, NU, true> : k_refine_tab<NX, NU, false>;
     const size_t bytes = fused ? refine_tab_smem<NX, NU, true>() : refine_tab_smem<NX, NU, false>();
     cudaError_t e = set_smem_carveout(kern, bytes);
     if (e != cudaSuccess) return e;
     LaunchScope ls(name, s);
-    // later passes find most instances converged: fewer, striding blocks
-    const int grid = a.rpass == 0 ? a.count : std::min(a.count, 148 * 4);
     kern<<<grid, 32, bytes, s>>>(a);
     return cudaGetLastError();
   } else {

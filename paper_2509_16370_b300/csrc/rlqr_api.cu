@@ -747,7 +747,10 @@ rlqr_status rlqr_solve_batched(const rlqr_batch *batch, const rlqr_opts *opts, v
       nmaxN = std::max(nmaxN, B.h_N[b]);
     }
     const int route = uniform ? residual_route(nmaxN, nmax, mmax, a.tsize, B.count) : 0;
-    if (mixed && uniform && route == 5 && opts->max_refine > 0 && warp_res32_size(nmax, mmax)) {
+    if (route == 6 || route == 7) a.refine_warps = 2;
+    else if (route != 0) a.refine_warps = 1;
+    if (mixed && uniform && (route == 5 || route == 7) && opts->max_refine > 0 &&
+        warp_res32_size(nmax, mmax)) {
       // fused route: the control-pivot certificate alone here; the first
       // refinement pass computes the residual as it goes
       a.fused_res = 1;
@@ -1185,7 +1188,8 @@ rlqr_status rlqr_tune_batched_set(const rlqr_batch *batch, const rlqr_opts *opts
   bool ragged = false;
   if (!batch_tune_key(batch, opts, &key, &ragged) || route < 0) return RLQR_ERR_ARG;
   if (route != 0 && (ragged ? (route < 3 || route > 4)
-                            : !(route == 1 || route == 2 || (route == 5 && opts->prec == RLQR_MIXED))))
+                            : !(route == 1 || route == 2 ||
+                                (route >= 5 && route <= 7 && opts->prec == RLQR_MIXED))))
     return RLQR_ERR_ARG;
   std::lock_guard<std::mutex> lock(g_route_mu);
   if (route == 0)
@@ -1214,14 +1218,18 @@ rlqr_status rlqr_autotune_batched(const rlqr_batch *batch, const rlqr_opts *opts
   int best = 0;
   float best_t = 0.0f;
   const int reps = 3;
-  int cand[3], nc = 0;
+  int cand[5], nc = 0;
   if (ragged) {
     cand[nc++] = 3;
     cand[nc++] = 4;
   } else {
     cand[nc++] = 1;
     cand[nc++] = 2;
-    if (opts->prec == RLQR_MIXED && opts->max_refine > 0) cand[nc++] = 5;
+    if (opts->prec == RLQR_MIXED && opts->max_refine > 0) {
+      cand[nc++] = 5;
+      cand[nc++] = 6;
+      cand[nc++] = 7;
+    }
   }
   for (int ci = 0; ci < nc && err == RLQR_OK; ++ci) {
     const int route = cand[ci];

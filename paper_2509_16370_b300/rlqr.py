@@ -483,15 +483,17 @@ def rlqr_tune_reset():
 
 
 RES_ROUTE_WARP, RES_ROUTE_GRID, RES_ROUTE_FUSED = 1, 2, 5
+# the same residual routes with refinement passes on two warps per instance
+RES_ROUTE_WARP_DUO, RES_ROUTE_FUSED_DUO = 6, 7
 SWEEP_ROUTE_STREAMS, SWEEP_ROUTE_PERSISTENT = 3, 4
 
 
 def rlqr_autotune_batched(batch: "DeviceBatch", opts: rlqr_opts, ws: torch.Tensor, status=None,
                           stream=None):
-    """Time the two routes of the batch -- the residual routes of a uniform
-    batch, the sweep routes (class streams / persistent launch) of a ragged
-    one -- and record the faster one for its shape; returns (route, ms of
-    one rlqr_solve_batched)."""
+    """Time the routes of the batch -- the residual / refinement routes of a
+    uniform batch (1, 2 and, mixed, 5, 6, 7), the sweep routes (class
+    streams / persistent launch) of a ragged one -- and record the fastest
+    for its shape; returns (route, ms of one rlqr_solve_batched)."""
     bs = batch.c_struct()
     r = ctypes.c_int32(0)
     t = ctypes.c_double(0.0)

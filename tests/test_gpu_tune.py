@@ -71,7 +71,8 @@ def test_autotuner_choice_and_solves_after_it():
                                      (rlqr.RLQR_MIXED, (6, 1))])
 def test_every_batched_residual_route_is_exact_and_the_tuner_picks_one(prec, nm):
     """Routes 1 (warp residual), 2 (grid residual) and, mixed, 5 (the first
-    refinement pass computes the residual itself): the oracle's flags, its
+    refinement pass computes the residual itself), 6 and 7 (routes 1 and 5
+    with the refinement passes on two warps per instance): the oracle's flags, its
     backward error <= 1e-9 for every instance, the reported backward error
     an upper bound of the oracle's, the same statuses on every route."""
     from tests.gpu_helpers import REL_TOL
@@ -86,7 +87,7 @@ def test_every_batched_residual_route_is_exact_and_the_tuner_picks_one(prec, nm)
     refs = [oracle.riccati(p) for p in probs]
     routes = [rlqr.RES_ROUTE_WARP, rlqr.RES_ROUTE_GRID]
     if prec == rlqr.RLQR_MIXED:
-        routes.append(rlqr.RES_ROUTE_FUSED)
+        routes += [rlqr.RES_ROUTE_FUSED, rlqr.RES_ROUTE_WARP_DUO, rlqr.RES_ROUTE_FUSED_DUO]
     statuses = []
     try:
         for route in routes:
@@ -106,7 +107,8 @@ def test_every_batched_residual_route_is_exact_and_the_tuner_picks_one(prec, nm)
         route, ms = rlqr.rlqr_autotune_batched(db, opts, ws, st)
         assert route in routes and ms > 0
         if prec == rlqr.RLQR_FP64:
-            with pytest.raises(rlqr.RlqrError):
-                rlqr.rlqr_tune_batched_set(db, opts, rlqr.RES_ROUTE_FUSED)
+            for r in (rlqr.RES_ROUTE_FUSED, rlqr.RES_ROUTE_WARP_DUO, rlqr.RES_ROUTE_FUSED_DUO):
+                with pytest.raises(rlqr.RlqrError):
+                    rlqr.rlqr_tune_batched_set(db, opts, r)
     finally:
         rlqr.rlqr_tune_reset()
