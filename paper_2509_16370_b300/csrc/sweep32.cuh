@@ -596,28 +596,33 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
     I.x[lane] = widen(xv);
     I.y[lane] = widen(yv);
   }
-  // the stage's FP32 copies and factors, prefetched into registers
-  LaneSeg<float, CP> fA, fW;
-  LaneSeg<float, CB> fB, fK;
-  LaneSeg<float, CV> fc, fp;
-  LaneSeg<float, CM> fk;
-  auto fprefetch = [&](int k) {
-    fA.load_cg(gAf + (size_t)k * nn, nn, lane);
-    fB.load_cg(gBf + (size_t)k * nm, nm, lane);
-    fc.load_cg(gcf + (size_t)(k + 1) * n, n, lane);
-    fW.load_cg(gW + (size_t)(k + 1) * nn, nn, lane);
-    fK.load_cg(gK + (size_t)k * nm, nm, lane);
-    fk.load_cg(gkv + (size_t)k * m, m, lane);
-    fp.load_cg(gpv + (size_t)(k + 1) * n, n, lane);
+  // The stage's FP32 copies and factors, prefetched into registers two
+  // stages ahead (two alternating sets): a forward stage is short enough
+  // that a one-stage-ahead load of the factor, written by the backward pass
+  // and evicted from L2 since, would still be in flight at its commit.
+  struct FwdSet {
+    LaneSeg<float, CP> A, W;
+    LaneSeg<float, CB> B, K;
+    LaneSeg<float, CV> c, p;
+    LaneSeg<float, CM> k;
   };
-  auto fcommit = [&]() {
+  auto fprefetch = [&](FwdSet &f, int k) {
+    f.A.load_cg(gAf + (size_t)k * nn, nn, lane);
+    f.B.load_cg(gBf + (size_t)k * nm, nm, lane);
+    f.c.load_cg(gcf + (size_t)(k + 1) * n, n, lane);
+    f.W.load_cg(gW + (size_t)(k + 1) * nn, nn, lane);
+    f.K.load_cg(gK + (size_t)k * nm, nm, lane);
+    f.k.load_cg(gkv + (size_t)k * m, m, lane);
+    f.p.load_cg(gpv + (size_t)(k + 1) * n, n, lane);
+  };
+  auto fcommit = [&](const FwdSet &f) {
 #pragma unroll
     for (int i = 0; i < CP; ++i) {
       const int idx = lane + 32 * i;
       if (idx < nn) {
         const int row = idx / n, o = row * N4 + idx - row * n;
-        s.A[o] = fA.v[i];
-        s.W[o] = fW.v[i];
+        s.A[o] = f.A.v[i];
+        s.W[o] = f.W.v[i];
       }
     }
 #pragma unroll
@@ -625,29 +630,29 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
       const int idx = lane + 32 * i;
       if (idx < nm) {
         const int rb = idx / m, rk = idx / n;
-        s.B[rb * M4 + idx - rb * m] = fB.v[i];
-        s.K[rk * N4 + idx - rk * n] = fK.v[i];
+        s.B[rb * M4 + idx - rb * m] = f.B.v[i];
+        s.K[rk * N4 + idx - rk * n] = f.K.v[i];
       }
     }
 #pragma unroll
     for (int i = 0; i < CV; ++i) {
       const int idx = lane + 32 * i;
       if (idx < n) {
-        s.c[idx] = fc.v[i];
-        s.p[idx] = fp.v[i];
+        s.c[idx] = f.c.v[i];
+        s.p[idx] = f.p.v[i];
       }
     }
 #pragma unroll
     for (int i = 0; i < CM; ++i) {
       const int idx = lane + 32 * i;
-      if (idx < m) s.kk[idx] = fk.v[i];
+      if (idx < m) s.kk[idx] = f.k.v[i];
     }
   };
-  __syncwarp();
-  fprefetch(0);
-  for (int k = 0; k < N; ++k) {
-    fcommit();
-    if (k + 1 < N) fprefetch(k + 1);
+  // one forward stage from the set holding its data; the set is refilled
+  // with stage k + 2 once committed
+  auto fstage = [&](FwdSet &f, int k) {
+    fcommit(f);
+    if (k + 2 < N) fprefetch(f, k + 2);
     __syncwarp();
     // u_k = K_k x_k + k_k
     if (lane < m) {
@@ -686,6 +691,14 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
       I.y[(size_t)(k + 1) * n + lane] = widen(yv);
     }
     __syncwarp();
+  };
+  __syncwarp();
+  FwdSet f0, f1;
+  fprefetch(f0, 0);
+  if (N > 1) fprefetch(f1, 1);
+  for (int k = 0; k < N; k += 2) {
+    fstage(f0, k);
+    if (k + 1 < N) fstage(f1, k + 1);
   }
 }
 
