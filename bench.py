@@ -904,7 +904,9 @@ def measure_long_horizon(args, fp64_reps=1, fp64_warmup=1):
     oracle.riccati(sub)
     cpu_s = time.perf_counter() - t0
     # roofline of the dominant kernel against the measured FP32 FMA rate (the
-    # scan's combine and finalize products run on the FP32 pipes)
+    # eliminations and solves of the scan run on the FP32 pipes), and the
+    # fold's n x n products against a third of the measured TF32 mma rate
+    # (they run as 3xTF32 mma.sync on the tensor pipe)
     pipes = rlqr.rlqr_measure_pipes()
     dom = max(report.items(), key=lambda kv: kv[1][1]) if report else None
     roof = None
@@ -919,6 +921,17 @@ def measure_long_horizon(args, fp64_reps=1, fp64_warmup=1):
                     "peak_source": "measured FP32 FMA rate (rlqr_measure_pipes)",
                     "flops_per_stage": flops, "launch_ms": round(tot / cnt, 4),
                     "share": round(tot / sum(v[1] for v in report.values()), 3), "traffic": None}
+    roof_tc = None
+    if "k_scan_reduce" in report and pipes.get("tf32_mma_tflops"):
+        cnt, tot = report["k_scan_reduce"]
+        prod = 10.0 * n ** 3  # the five n x n products of one combination per stage
+        achieved = prod * N / (tot / cnt / 1e3) / 1e12
+        peak = pipes["tf32_mma_tflops"] / 3.0
+        roof_tc = {"kernel": "k_scan_reduce (its n x n products)", "bound": "tensor",
+                   "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                   "frac": round(achieved / peak, 4),
+                   "peak_source": "measured TF32 mma.sync rate (rlqr_measure_tf32) / 3 for 3xTF32",
+                   "flops_per_stage": prod, "launch_ms": round(tot / cnt, 4)}
     line = {"metric": METRIC, "value": value, "unit": "stage-solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -935,7 +948,7 @@ def measure_long_horizon(args, fp64_reps=1, fp64_warmup=1):
             "fp64_plain_seq": {"value": N / (ms64 / 1e3), "ms_per_step": ms64,
                                "rel_resid": float(bufs64["rel"].item())},
             "speedup_vs_fp64_plain": ms64 / ms,
-            "roofline": roof,
+            "roofline": roof, "roofline_tensor": roof_tc,
             "cpu_baseline": {"value": S / cpu_s, "unit": "stage-solves/s", "cores": 1,
                              "kind": "oracle", "sample": f"the first {S} stages, {cpu_s:.2f} s"},
             "flags_all_pd": bool((flags_gpu == 3).all()),

@@ -478,6 +478,17 @@ size_t rlqr_measure_pipes_bytes(void);
 rlqr_status rlqr_measure_pipes(void *scratch, size_t scratch_bytes, double *fp64_tflops,
                                double *fp32_tflops, double *fp32x2_tflops);
 
+/* Microbenchmark of the tensor pipe on the current device: the rate of
+ * mma.sync.m16n8k8 with TF32 operands and FP32 accumulation (2 * 16 * 8 * 8
+ * flops per instruction; 8 independent accumulator tiles per warp over 4
+ * CTAs of 256 threads per SM; best of 5 CUDA-event-timed launches), in
+ * TFLOP/s.  The scan's 3xTF32 products issue three such instructions per
+ * product tile, so their effective peak is a third of this rate.  scratch:
+ * as for rlqr_measure_pipes (the same buffer size suffices; 4-byte aligned);
+ * allocates nothing; synchronous on the default stream; RLQR_ERR_WORKSPACE
+ * for a missing or small buffer, RLQR_ERR_CUDA on any CUDA error. */
+rlqr_status rlqr_measure_tf32(void *scratch, size_t scratch_bytes, double *tf32_tflops);
+
 #ifdef __cplusplus
 }
 #endif

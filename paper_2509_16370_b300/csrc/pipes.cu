@@ -1,8 +1,10 @@
 // pipes.cu -- microbenchmarks of the arithmetic pipes the hot path uses, for
 // the roofline denominators: FP64 FMA (the plain path and the certificates),
-// FP32 FMA and packed f32x2 FMA (the mixed path's sweeps).  Each thread runs
-// independent FMA chains (enough to cover the pipe latency) over a grid of
-// several CTAs per SM; rate = 2 flops per FMA lane-operation / CUDA-event time.
+// FP32 FMA and packed f32x2 FMA (the mixed path's sweeps), and the TF32
+// mma.sync.m16n8k8 rate of the tensor pipe (the scan's 3xTF32 products).
+// Each thread (warp, for the mma) runs independent chains (enough to cover
+// the pipe latency) over a grid of several CTAs per SM; rate = 2 flops per
+// multiply-add / CUDA-event time.
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -40,6 +42,34 @@ __global__ void k_pipe_fma2(float *out, int iters, float a, float b) {
   float s = 0.f;
 #pragma unroll
   for (int c = 0; c < kChains; ++c) s += acc[c].x + acc[c].y;
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// Independent accumulator tiles per warp of the TF32 mma chain.
+constexpr int kMmaChains = 8;
+
+// Back-to-back mma.sync.m16n8k8 TF32 with FP32 accumulation (2 * 16 * 8 * 8
+// flops each) on kMmaChains independent accumulators per warp.  The operands
+// are small constants (their TF32 bit patterns), so the sums stay finite.
+__global__ void k_pipe_tf32(float *out, int iters) {
+  float acc[kMmaChains][4];
+#pragma unroll
+  for (int c = 0; c < kMmaChains; ++c)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[c][j] = 0.f;
+  const uint32_t a = __float_as_uint(1e-3f) & 0xffffe000u, b = __float_as_uint(1e-3f) & 0xffffe000u;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < kMmaChains; ++c)
+      asm volatile(
+          "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, "
+          "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+          : "+f"(acc[c][0]), "+f"(acc[c][1]), "+f"(acc[c][2]), "+f"(acc[c][3])
+          : "r"(a), "r"(a), "r"(a), "r"(a), "r"(b), "r"(b));
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < kMmaChains; ++c) s += acc[c][0] + acc[c][1] + acc[c][2] + acc[c][3];
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
@@ -109,5 +139,23 @@ extern "C" rlqr_status rlqr_measure_pipes(void *scratch, size_t scratch_bytes, d
   *fp64_tflops = 2.0 * lanes * it64 / (ms64 * 1e-3) / 1e12;
   *fp32_tflops = 2.0 * lanes * it32 / (ms32 * 1e-3) / 1e12;
   *fp32x2_tflops = 2.0 * 2.0 * lanes * it32 / (ms2 * 1e-3) / 1e12;
+  return RLQR_OK;
+}
+
+extern "C" rlqr_status rlqr_measure_tf32(void *scratch, size_t scratch_bytes,
+                                         double *tf32_tflops) {
+  if (!tf32_tflops) return RLQR_ERR_ARG;
+  const int threads = 256, blocks = pipe_blocks();
+  if (blocks <= 0) return RLQR_ERR_CUDA;
+  if (!scratch || scratch_bytes < (size_t)blocks * threads * sizeof(float) ||
+      (reinterpret_cast<uintptr_t>(scratch) % sizeof(float)) != 0)
+    return RLQR_ERR_WORKSPACE;
+  const int iters = 4096;
+  const float ms = time_best([&] {
+    k_pipe_tf32<<<blocks, threads>>>((float *)scratch, iters);
+  }, 5);
+  if (ms <= 0.f) return RLQR_ERR_CUDA;
+  const double mmas = (double)blocks * (threads / 32) * kMmaChains * iters;
+  *tf32_tflops = 2.0 * 16 * 8 * 8 * mmas / (ms * 1e-3) / 1e12;
   return RLQR_OK;
 }

@@ -119,6 +119,8 @@ def _load():
     lib.rlqr_measure_pipes_bytes.argtypes = []
     lib.rlqr_measure_pipes.restype = st
     lib.rlqr_measure_pipes.argtypes = [_dp, sz] + [P(ctypes.c_double)] * 3
+    lib.rlqr_measure_tf32.restype = st
+    lib.rlqr_measure_tf32.argtypes = [_dp, sz, P(ctypes.c_double)]
     lib.rlqr_instrument.restype = st
     lib.rlqr_instrument.argtypes = [ctypes.c_int]
     lib.rlqr_instrument_report.restype = ctypes.c_int
@@ -417,15 +419,19 @@ def rlqr_shard_entry(nx: int, delta: float, P_start, x_start, x_first, c0, strea
 
 
 def rlqr_measure_pipes() -> dict:
-    """Measured FP64 / FP32 / packed-FP32 FMA rates of the current device in
-    TFLOP/s (synchronous microbenchmark; the sink buffer is a torch tensor)."""
+    """Measured FP64 / FP32 / packed-FP32 FMA rates and the TF32 mma.sync
+    rate of the current device in TFLOP/s (synchronous microbenchmarks; the
+    sink buffer is a torch tensor)."""
     nb = int(lib.rlqr_measure_pipes_bytes())
     buf = torch.empty(max(nb, 8), dtype=torch.uint8, device="cuda")
     v = [ctypes.c_double() for _ in range(3)]
     _check(lib.rlqr_measure_pipes(_ptr(buf), nb, *[ctypes.byref(x) for x in v]),
            "rlqr_measure_pipes")
+    t = ctypes.c_double()
+    _check(lib.rlqr_measure_tf32(_ptr(buf), nb, ctypes.byref(t)), "rlqr_measure_tf32")
     torch.cuda.synchronize()
-    return dict(fp64_tflops=v[0].value, fp32_tflops=v[1].value, fp32x2_tflops=v[2].value)
+    return dict(fp64_tflops=v[0].value, fp32_tflops=v[1].value, fp32x2_tflops=v[2].value,
+                tf32_mma_tflops=t.value)
 
 
 def rlqr_cross_scratch_bytes(N: int, nx: int, nu: int, p: int, opts: rlqr_opts) -> int:

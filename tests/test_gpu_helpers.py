@@ -235,9 +235,10 @@ def test_fp32_cholesky_pd_proof(probe, n, tau):
 
 def test_measured_pipe_rates_are_consistent():
     """rlqr_measure_pipes (the roofline denominators): positive rates, FP32
-    far above FP64 on this part, and the packed f32x2 FMA at least as fast
-    as the scalar one."""
+    far above FP64 on this part, the packed f32x2 FMA at least as fast as
+    the scalar one, and the TF32 tensor-core rate above the FP32 FMA rate."""
     from paper_2509_16370_b300 import rlqr
     p = rlqr.rlqr_measure_pipes()
     assert 0.0 < p["fp64_tflops"] < p["fp32_tflops"] / 10
     assert p["fp32x2_tflops"] >= 0.9 * p["fp32_tflops"]
+    assert p["tf32_mma_tflops"] > p["fp32_tflops"]
