@@ -71,6 +71,13 @@ __host__ __device__ constexpr bool tab_size(int n, int m) {
   return ((n == 4 || n == 6) && (m == 1 || m == 2)) || (n == 12 && (m == 3 || m == 4));
 }
 
+// (n, m) whose refinement stages the contiguous per-stage blocks (rows of a
+// multiple of 16 bytes: n, m multiples of 4, the tableau warp sizes) as
+// 16-byte chunks.
+__host__ __device__ constexpr bool chunk16_size(int n, int m) {
+  return n % 4 == 0 && m % 4 == 0 && n >= 4 && m >= 4 && 2 * n <= 32 && 2 * m + n + 1 <= 32;
+}
+
 // Margin of the mixed path's pivot certificate: a decision taken from an
 // FP32-computed pivot matrix X is kept only when X - tau D (PD claims) or
 // X + tau D (indefinite claims) provably has the same inertia, D = |diag X|
@@ -360,6 +367,55 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
 }
+// 16-byte copy, L2 only (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// A per-stage block of 16-byte chunks: the chunk j of stage k sits at
+// p + k * stride + 16 j (bytes) in global memory and goes to byte dst + 16 j
+// of a shared-memory slot.
+struct Blk16 {
+  const char *p;
+  uint32_t stride, dst;
+  int n;
+};
+
+// This lane's chunks (lane, lane + 32, ...) of the blocks b[0..NB), numbered
+// consecutively, as (source at stage 0, stride, slot offset); dst = ~0u past
+// the last chunk.
+template <int NB, int CH>
+struct ChunkPlan {
+  const char *src[CH];
+  uint32_t stride[CH], dst[CH];
+  __device__ __forceinline__ void init(const Blk16 (&b)[NB], int lane) {
+#pragma unroll
+    for (int i = 0; i < CH; ++i) {
+      const int c = lane + 32 * i;
+      src[i] = b[0].p;
+      stride[i] = 0u;
+      dst[i] = ~0u;
+      int start = 0;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        if (c >= start && c < start + b[j].n) {
+          src[i] = b[j].p + 16 * (c - start);
+          stride[i] = b[j].stride;
+          dst[i] = b[j].dst + 16u * (uint32_t)(c - start);
+        }
+        start += b[j].n;
+      }
+    }
+  }
+  // the copies of stage k into slot
+  __device__ __forceinline__ void issue(unsigned char *slot, int k) const {
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+      if (dst[i] != ~0u) cp_async16(slot + dst[i], src[i] + (size_t)k * stride[i]);
+  }
+};
+
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");

@@ -38,6 +38,8 @@
 // is overwritten while it is read.
 #pragma once
 
+#include <cstddef>
+
 #include "common.cuh"
 #include "residual32.cuh"
 #include "tab32.cuh"
@@ -296,8 +298,57 @@ __device__ __forceinline__ void refine_duo_instance(const BatchArgs &a, int slot
       if (t < N - DB) duo_arrive<DB + 1, DB + NE>(DB + 1 + t % NE);  // EMPTY: slot free
     }
   } else {
-    // ----- helper: copies of stage k = N - 1 - t into slot t % DB
+    // ----- helper: copies of stage k = N - 1 - t into slot t % DB.  Sizes of
+    // chunk16_size: the blocks contiguous in global memory (W rows, G^{-1},
+    // residual rows) as 16-byte chunks, the lanes taking them in turn.
+    constexpr bool kC16 = chunk16_size(NX, NU);
+    constexpr int NBB = FUSED ? 2 : 5;
+    constexpr int CB16 = (nn * 4 + mmm * 4 + (FUSED ? 0 : (2 * n + m) * 8)) / 16;
+    ChunkPlan<NBB, kC16 ? (CB16 + 31) / 32 : 1> bplan;
+    if constexpr (kC16) {
+      static_assert(SM::N4 == NX && SM::M4 == NU, "unpadded slots");
+      static_assert(sizeof(BS) % 16 == 0 && offsetof(BS, W) % 16 == 0 &&
+                        offsetof(BS, Gi) % 16 == 0 && offsetof(BS, q) % 16 == 0 &&
+                        offsetof(BS, r) % 16 == 0 && offsetof(BS, c) % 16 == 0,
+                    "16-byte block offsets");
+      auto cp = [](const void *p) { return reinterpret_cast<const char *>(p); };
+      if constexpr (FUSED) {
+        const Blk16 bb[NBB] = {{cp(gW + nn), nn * 4, offsetof(BS, W), nn / 4},
+                               {cp(gGi), mmm * 4, offsetof(BS, Gi), mmm / 4}};
+        bplan.init(bb, lane);
+      } else {
+        const Blk16 bb[NBB] = {{cp(gW + nn), nn * 4, offsetof(BS, W), nn / 4},
+                               {cp(gGi), mmm * 4, offsetof(BS, Gi), mmm / 4},
+                               {cp(rq), n * 8, offsetof(BS, q), n / 2},
+                               {cp(rr), m * 8, offsetof(BS, r), m / 2},
+                               {cp(rc + n), n * 8, offsetof(BS, c), n / 2}};
+        bplan.init(bb, lane);
+      }
+    }
     auto bissue = [&](int t) {
+      if constexpr (kC16) {
+        if (t < N) {
+          const int k = N - 1 - t;
+          BS &d = bring[t % DB];
+          bplan.issue(reinterpret_cast<unsigned char *>(&d), k);
+          const float *A = gAf + (size_t)k * nn, *K = gK + (size_t)k * nm, *B = gBf + (size_t)k * nm;
+#pragma unroll
+          for (int i = 0; i < CP; ++i) {
+            const int e = lane + 32 * i;
+            if (e < nn) cp_async4(&d.At[oNt[i]], A + e);
+          }
+#pragma unroll
+          for (int i = 0; i < CB; ++i) {
+            const int e = lane + 32 * i;
+            if (e < nm) {
+              cp_async4(&d.Kt[oKt[i]], K + e);
+              cp_async4(&d.Bt[oBt[i]], B + e);
+            }
+          }
+        }
+        cp_async_commit();
+        return;
+      }
       if (t < N) {
         const int k = N - 1 - t;
         BS &d = bring[t % DB];
@@ -477,7 +528,70 @@ __device__ __forceinline__ void refine_duo_instance(const BatchArgs &a, int slot
     } else if (cr_) {
       zp = I.y + n + (lane - n - m); zs = n; resp = rc + n + (lane - n - m); rs = n;
     }
+    // sizes of chunk16_size: the blocks contiguous in global memory as
+    // 16-byte chunks, the transposed and mirrored ones element by element
+    constexpr bool kC16f = chunk16_size(NX, NU);
+    constexpr int NBF = 8;
+    constexpr int CF16 = (2 * nn * 4 + 3 * nm * 4 + n * 4 + m * 4 + n * 8) / 16;
+    ChunkPlan<NBF, kC16f ? (CF16 + 31) / 32 : 1> fplan;
+    if constexpr (kC16f) {
+      static_assert(sizeof(FS) % 16 == 0 && offsetof(FS, K) % 16 == 0 &&
+                        offsetof(FS, A) % 16 == 0 && offsetof(FS, B) % 16 == 0 &&
+                        offsetof(FS, W) % 16 == 0 && offsetof(FS, M) % 16 == 0 &&
+                        offsetof(FS, p) % 16 == 0 && offsetof(FS, kk) % 16 == 0 &&
+                        offsetof(FS, c) % 16 == 0,
+                    "16-byte block offsets");
+      auto cp = [](const void *p) { return reinterpret_cast<const char *>(p); };
+      const Blk16 fb[NBF] = {
+          {cp(gK), nm * 4, offsetof(FS, K), nm / 4},    {cp(gAf), nn * 4, offsetof(FS, A), nn / 4},
+          {cp(gBf), nm * 4, offsetof(FS, B), nm / 4},   {cp(gW + nn), nn * 4, offsetof(FS, W), nn / 4},
+          {cp(gMf), nm * 4, offsetof(FS, M), nm / 4},   {cp(gpv + n), n * 4, offsetof(FS, p), n / 4},
+          {cp(gkv), m * 4, offsetof(FS, kk), m / 4},    {cp(rc + n), n * 8, offsetof(FS, c), n / 2}};
+      fplan.init(fb, lane);
+    }
     auto fissue = [&](int k) {
+      if constexpr (kC16f) {
+        if (k < N) {
+          FS &f = fring[k % DF];
+          fplan.issue(reinterpret_cast<unsigned char *>(&f), k);
+          const float *A = gAf + (size_t)k * nn, *Q = gQf + (size_t)k * nn;
+          const float *B = gBf + (size_t)k * nm, *M = gMf + (size_t)k * nm;
+          const float *R = gRf + (size_t)k * mmm;
+#pragma unroll
+          for (int i = 0; i < CP; ++i) {
+            const int e = lane + 32 * i;
+            if (e < nn) {
+              cp_async4(&f.At[oNt[i]], A + e);
+              if (upN[i]) {
+                cp_async4(&f.Q[oN[i]], Q + e);
+                cp_async4(&f.Q[oNt[i]], Q + e);
+              }
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < CB; ++i) {
+            const int e = lane + 32 * i;
+            if (e < nm) {
+              cp_async4(&f.Bt[oBt[i]], B + e);
+              cp_async4(&f.Mt[oBt[i]], M + e);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < CR; ++i) {
+            const int e = lane + 32 * i;
+            if (e < mmm && upR[i]) {
+              cp_async4(&f.R[oR[i]], R + e);
+              cp_async4(&f.R[oRs[i]], R + e);
+            }
+          }
+          if (zp) {
+            cp_async8(&f.z[lane], zp + (size_t)k * zs);
+            cp_async8(&f.res[lane], resp + (size_t)k * rs);
+          }
+        }
+        cp_async_commit();
+        return;
+      }
       if (k < N) {
         FS &f = fring[k % DF];
         const float *W = gW + (size_t)(k + 1) * nn, *A = gAf + (size_t)k * nn, *Q = gQf + (size_t)k * nn;

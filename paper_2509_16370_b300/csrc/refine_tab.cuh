@@ -20,6 +20,8 @@
 // products.
 #pragma once
 
+#include <cstddef>
+
 #include "common.cuh"
 #include "residual32.cuh"
 #include "tab32.cuh"
@@ -165,9 +167,74 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
     for (int e = lane; e < (int)(sizeof(SM) / 16); e += 32) z4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 
+  // Sizes of chunk16_size (rows of a multiple of 16 bytes, so the slots have
+  // no row padding): the per-stage blocks that are contiguous in global
+  // memory (factor rows, row-major data copies, residual rows) are staged as
+  // 16-byte chunks, the lanes taking them in turn; the transposed and the
+  // mirrored copies element by element as for the other sizes.
+  constexpr bool kC16 = chunk16_size(NX, NU);
+  constexpr int NBB = FUSED ? 2 : 5, NBF = 8;
+  constexpr int CB16 = (nn * 4 + mmm * 4 + (FUSED ? 0 : (2 * n + m) * 8)) / 16;
+  constexpr int CF16 = (2 * nn * 4 + 3 * nm * 4 + n * 4 + m * 4 + n * 8) / 16;
+  ChunkPlan<NBB, kC16 ? (CB16 + 31) / 32 : 1> bplan;
+  ChunkPlan<NBF, kC16 ? (CF16 + 31) / 32 : 1> fplan;
+  if constexpr (kC16) {
+    static_assert(SM::N4 == NX && SM::M4 == NU, "unpadded slots");
+    static_assert(sizeof(BS) % 16 == 0 && sizeof(FS) % 16 == 0, "16-byte slot strides");
+    static_assert(offsetof(BS, W) % 16 == 0 && offsetof(BS, Gi) % 16 == 0 &&
+                      offsetof(BS, q) % 16 == 0 && offsetof(BS, r) % 16 == 0 &&
+                      offsetof(BS, c) % 16 == 0 && offsetof(FS, K) % 16 == 0 &&
+                      offsetof(FS, A) % 16 == 0 && offsetof(FS, B) % 16 == 0 &&
+                      offsetof(FS, W) % 16 == 0 && offsetof(FS, M) % 16 == 0 &&
+                      offsetof(FS, c) % 16 == 0 && offsetof(FS, p) % 16 == 0 &&
+                      offsetof(FS, kk) % 16 == 0,
+                  "16-byte block offsets");
+    auto cp = [](const void *p) { return reinterpret_cast<const char *>(p); };
+    if constexpr (FUSED) {
+      const Blk16 bb[NBB] = {{cp(gW + nn), nn * 4, offsetof(BS, W), nn / 4},
+                             {cp(gGi), mmm * 4, offsetof(BS, Gi), mmm / 4}};
+      bplan.init(bb, lane);
+    } else {
+      const Blk16 bb[NBB] = {{cp(gW + nn), nn * 4, offsetof(BS, W), nn / 4},
+                             {cp(gGi), mmm * 4, offsetof(BS, Gi), mmm / 4},
+                             {cp(rq), n * 8, offsetof(BS, q), n / 2},
+                             {cp(rr), m * 8, offsetof(BS, r), m / 2},
+                             {cp(rc + n), n * 8, offsetof(BS, c), n / 2}};
+      bplan.init(bb, lane);
+    }
+    const Blk16 fb[NBF] = {
+        {cp(gK), nm * 4, offsetof(FS, K), nm / 4},    {cp(gAf), nn * 4, offsetof(FS, A), nn / 4},
+        {cp(gBf), nm * 4, offsetof(FS, B), nm / 4},   {cp(gW + nn), nn * 4, offsetof(FS, W), nn / 4},
+        {cp(gMf), nm * 4, offsetof(FS, M), nm / 4},   {cp(gpv + n), n * 4, offsetof(FS, p), n / 4},
+        {cp(gkv), m * 4, offsetof(FS, kk), m / 4},    {cp(rc + n), n * 8, offsetof(FS, c), n / 2}};
+    fplan.init(fb, lane);
+  }
+
   // ---------------- backward: p-recurrence with the residual as right-hand side
   BS *bring = reinterpret_cast<BS *>(s.ring);
   auto bissue = [&](int k) {
+    if constexpr (kC16) {
+      if (k >= 0) {
+        BS &d = bring[(N - 1 - k) % DB];
+        bplan.issue(reinterpret_cast<unsigned char *>(&d), k);
+        const float *A = gAf + (size_t)k * nn, *K = gK + (size_t)k * nm, *B = gBf + (size_t)k * nm;
+#pragma unroll
+        for (int i = 0; i < CP; ++i) {
+          const int e = lane + 32 * i;
+          if (e < nn) cp_async4(&d.At[oNt[i]], A + e);
+        }
+#pragma unroll
+        for (int i = 0; i < CB; ++i) {
+          const int e = lane + 32 * i;
+          if (e < nm) {
+            cp_async4(&d.Kt[oKt[i]], K + e);
+            cp_async4(&d.Bt[oBt[i]], B + e);
+          }
+        }
+      }
+      cp_async_commit();
+      return;
+    }
     if (k >= 0) {
       BS &d = bring[(N - 1 - k) % DB];
       const float *W = gW + (size_t)(k + 1) * nn, *A = gAf + (size_t)k * nn;
@@ -332,6 +399,48 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
   }
   FS *fring = reinterpret_cast<FS *>(s.ring);
   auto fissue = [&](int k) {
+    if constexpr (kC16) {
+      if (k < N) {
+        FS &f = fring[k % DF];
+        fplan.issue(reinterpret_cast<unsigned char *>(&f), k);
+        const float *A = gAf + (size_t)k * nn, *Q = gQf + (size_t)k * nn;
+        const float *B = gBf + (size_t)k * nm, *M = gMf + (size_t)k * nm;
+        const float *R = gRf + (size_t)k * mmm;
+#pragma unroll
+        for (int i = 0; i < CP; ++i) {
+          const int e = lane + 32 * i;
+          if (e < nn) {
+            cp_async4(&f.At[oNt[i]], A + e);
+            if (upN[i]) {
+              cp_async4(&f.Q[oN[i]], Q + e);
+              cp_async4(&f.Q[oNt[i]], Q + e);
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < CB; ++i) {
+          const int e = lane + 32 * i;
+          if (e < nm) {
+            cp_async4(&f.Bt[oBt[i]], B + e);
+            cp_async4(&f.Mt[oBt[i]], M + e);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < CR; ++i) {
+          const int e = lane + 32 * i;
+          if (e < mmm && upR[i]) {
+            cp_async4(&f.R[oR[i]], R + e);
+            cp_async4(&f.R[oRs[i]], R + e);
+          }
+        }
+        if (zp) {
+          cp_async8(&f.z[lane], zp + (size_t)k * zs);
+          cp_async8(&f.res[lane], resp + (size_t)k * rs);
+        }
+      }
+      cp_async_commit();
+      return;
+    }
     if (k < N) {
       FS &f = fring[k % DF];
       const float *W = gW + (size_t)(k + 1) * nn, *A = gAf + (size_t)k * nn, *Q = gQf + (size_t)k * nn;
