@@ -210,6 +210,11 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
     fplan.init(fb, lane);
   }
 
+  // rows of the backward rounds this lane works on: bi (a row < n), bt (a
+  // row < m) and bk (row lane - n of G^{-1} on lanes n .. n+m-1); 0 elsewhere
+  const int bi = lane < n ? lane : 0, bt = lane < m ? lane : 0;
+  const int bk = (lane >= n && lane < n + m) ? lane - n : 0;
+
   // ---------------- backward: p-recurrence with the residual as right-hand side
   BS *bring = reinterpret_cast<BS *>(s.ring);
   auto bissue = [&](int k) {
@@ -325,52 +330,60 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
       if (lane < n) s.cr[lane] = fmaf(-delta, s.p[lane], s.w[lane]);  // v = c' - delta p
     } else {
       // this lane's residual entries, truncated to FP32 (it copied them)
+      const float qv = f64_to_f32_rz(d.q[bi]);
+      const float cv = fmaf(-delta, s.p[bi], f64_to_f32_rz(d.c[bi]));  // v = c' - delta p
+      const float rv = f64_to_f32_rz(d.r[bt]);
       if (lane < n) {
-        s.qr[lane] = f64_to_f32_rz(d.q[lane]);
-        s.cr[lane] = fmaf(-delta, s.p[lane], f64_to_f32_rz(d.c[lane]));  // v = c' - delta p
+        s.qr[lane] = qv;
+        s.cr[lane] = cv;
       }
-      if (lane < m) s.rr[lane] = f64_to_f32_rz(d.r[lane]);
+      if (lane < m) s.rr[lane] = rv;
     }
     __syncwarp();
+    // The rounds below run on every lane (lanes past a round's rows work on
+    // row 0 and discard it): only the stores depend on the lane, so the warp
+    // takes no divergent branch.
     // g = p + W v
-    if (lane < n) {
+    {
       float2 wr[H2], vr[H2];
-      ld_seg<H2, 0, H2>(d.W + lane * N4, wr);
+      ld_seg<H2, 0, H2>(d.W + bi * N4, wr);
       ld_seg<H2, 0, H2>(s.cr, vr);
-      s.g[lane] = s.p[lane] + dot2<n>(wr, vr);
+      const float gv = s.p[bi] + dot2<n>(wr, vr);
+      if (lane < n) s.g[lane] = gv;
     }
     __syncwarp();
     // h = r' + B^T g
     float2 gr[H2];
     ld_seg<H2, 0, H2>(s.g, gr);
-    if (lane < m) {
+    {
       float2 br[H2];
-      ld_seg<H2, 0, H2>(d.Bt + lane * N4, br);
-      s.h[lane] = s.rr[lane] + dot2<n>(br, gr);
+      ld_seg<H2, 0, H2>(d.Bt + bt * N4, br);
+      const float hv = s.rr[bt] + dot2<n>(br, gr);
+      if (lane < m) s.h[lane] = hv;
     }
     __syncwarp();
     // p_k = q' + A^T g + K^T h (lanes < n);  k_k = -G^{-1} h (lanes n .. n+m-1)
     float2 hr[U2];
     ld_seg<U2, 0, U2>(s.h, hr);
-    if (lane < n) {
-      float2 ar[H2], kr[U2];
-      ld_seg<H2, 0, H2>(d.At + lane * N4, ar);
-      ld_seg<U2, 0, U2>(d.Kt + lane * M4, kr);
-      float2 acc = mul2(ar[0], gr[0]);
+    {
+      float2 ar[H2], kr[U2], gi[U2];
+      ld_seg<H2, 0, H2>(d.At + bi * N4, ar);
+      ld_seg<U2, 0, U2>(d.Kt + bi * M4, kr);
+      ld_seg<U2, 0, U2>(d.Gi + bk * M4, gi);
+      float2 acc = mul2(ar[0], gr[0]), acck = mul2(gi[0], hr[0]);
 #pragma unroll
       for (int q = 1; q < H2; ++q) acc = fma2(ar[q], gr[q], acc);
 #pragma unroll
       for (int q = 0; q < U2; ++q) acc = fma2(kr[q], hr[q], acc);
-      const float pv = s.qr[lane] + (acc.x + acc.y);
-      s.p[lane] = pv;
-      gpv[(size_t)k * n + lane] = pv;
-    } else if (lane < n + m) {
-      float2 gi[U2];
-      ld_seg<U2, 0, U2>(d.Gi + (lane - n) * M4, gi);
-      float2 acc = mul2(gi[0], hr[0]);
 #pragma unroll
-      for (int q = 1; q < U2; ++q) acc = fma2(gi[q], hr[q], acc);
-      gkv[(size_t)k * m + lane - n] = -(acc.x + acc.y);
+      for (int q = 1; q < U2; ++q) acck = fma2(gi[q], hr[q], acck);
+      const float pv = s.qr[bi] + (acc.x + acc.y), kv = -(acck.x + acck.y);
+      if (lane < n) {
+        s.p[lane] = pv;
+        gpv[(size_t)k * n + lane] = pv;
+      } else if (lane < n + m) {
+        gkv[(size_t)k * m + lane - n] = kv;
+      }
     }
     __syncwarp();  // the slot may be refilled from here on
   }
@@ -527,41 +540,47 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
     cp_async_wait<DF - 1>();
     __syncwarp();
     const FS &f = fring[k % DF];
+    // (every lane runs each round, lanes past its rows on row 0; only the
+    // stores depend on the lane)
     // du_k = K_k dx_k + k_k
     float2 xr[H2];
     ld_seg<H2, 0, H2>(dx, xr);
-    if (lane < m) {
+    {
       float2 kr[H2];
-      ld_seg<H2, 0, H2>(f.K + lane * N4, kr);
-      s.du[lane] = dot2<n>(kr, xr) + f.kk[lane];
+      ld_seg<H2, 0, H2>(f.K + bt * N4, kr);
+      const float duv = dot2<n>(kr, xr) + f.kk[bt];
+      if (lane < m) s.du[lane] = duv;
     }
     __syncwarp();
     // w = A dx + B du + c'_{k+1} - delta p_{k+1}
     float2 ur[U2];
     ld_seg<U2, 0, U2>(s.du, ur);
-    float wv = 0.f;
-    if (lane < n) {
+    float wv;
+    {
       float2 ar[H2], br[U2];
-      ld_seg<H2, 0, H2>(f.A + lane * N4, ar);
-      ld_seg<U2, 0, U2>(f.B + lane * M4, br);
+      ld_seg<H2, 0, H2>(f.A + bi * N4, ar);
+      ld_seg<U2, 0, U2>(f.B + bi * M4, br);
       float2 acc = mul2(ar[0], xr[0]);
 #pragma unroll
       for (int q = 1; q < H2; ++q) acc = fma2(ar[q], xr[q], acc);
 #pragma unroll
       for (int q = 0; q < U2; ++q) acc = fma2(br[q], ur[q], acc);
-      wv = (acc.x + acc.y) + fmaf(-delta, f.p[lane], f64_to_f32_rz(f.c[lane]));
-      s.w[lane] = wv;
+      wv = (acc.x + acc.y) + fmaf(-delta, f.p[bi], f64_to_f32_rz(f.c[bi]));
+      if (lane < n) s.w[lane] = wv;
     }
     __syncwarp();
     // dx_{k+1} = w - delta W w, dy_{k+1} = W w + p_{k+1}
     float2 vr[H2];
     ld_seg<H2, 0, H2>(s.w, vr);
-    if (lane < n) {
+    {
       float2 wr[H2];
-      ld_seg<H2, 0, H2>(f.W + lane * N4, wr);
+      ld_seg<H2, 0, H2>(f.W + bi * N4, wr);
       const float t = dot2<n>(wr, vr);
-      dxn[lane] = fmaf(-delta, t, wv);
-      dyn[lane] = t + f.p[lane];
+      const float dxv = fmaf(-delta, t, wv), dyv = t + f.p[bi];
+      if (lane < n) {
+        dxn[lane] = dxv;
+        dyn[lane] = dyv;
+      }
     }
     __syncwarp();
     // K dz rows of stage k and the FP64 updates (lanes < RS)
@@ -590,19 +609,16 @@ __device__ __forceinline__ void refine_tab_instance(const BatchArgs &a, int slot
         acc = fma2(a3[q], y3[q], acc);
         sab = fma2(abs2(a3[q]), abs2(y3[q]), sab);
       }
-      float t = acc.x + acc.y, sa = sab.x + sab.y, dz;
-      if (xr_) {
-        t -= dy[lane];
-        sa += fabsf(dy[lane]);
-        dz = dxn[lane];
-      } else if (ur_) {
-        dz = s.du[lane - n];
-      } else {
-        const int i = lane - n - m;
-        t -= fmaf(delta, dyn[i], dxn[i]);
-        sa += fmaf(delta, fabsf(dyn[i]), fabsf(dxn[i]));
-        dz = dyn[i];
-      }
+      // the row's own terms, by selects rather than branches: x rows -dy_k
+      // (dz = dx_{k+1}), u rows none (dz = du_k), c rows -dx_{k+1} - delta
+      // dy_{k+1} (dz = dy_{k+1})
+      const float dyx = dy[bi], dxx = dxn[bi], duu = s.du[bk];
+      const int ic = cr_ ? lane - n - m : 0;
+      const float dxc = dxn[ic], dyc = dyn[ic];
+      float t = acc.x + acc.y, sa = sab.x + sab.y;
+      t -= xr_ ? dyx : (cr_ ? fmaf(delta, dyc, dxc) : 0.f);
+      sa += xr_ ? fabsf(dyx) : (cr_ ? fmaf(delta, fabsf(dyc), fabsf(dxc)) : 0.f);
+      const float dz = xr_ ? dxx : (ur_ ? duu : dyc);
       const double zv = f.z[lane] + widen(dz), rv = f.res[lane] + widen(t);
       zp[(size_t)k * zs] = zv;
       resp[(size_t)k * rs] = rv;
