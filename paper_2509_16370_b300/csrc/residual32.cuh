@@ -181,19 +181,17 @@ struct Res32Rows {
     pB.load(I.B + (size_t)st * nm, nm, lane);
     pM.load(I.M + (size_t)st * nm, nm, lane);
     pR.load(I.R + (size_t)st * mmm, mmm, lane);
-    if (lane < n) {
-      zv = __ldg(I.x + (size_t)st * n + lane);
-      b1 = __ldg(I.q + (size_t)st * n + lane);
-      b2 = __ldg(I.y + (size_t)st * n + lane);
-    } else if (lane < n + m) {
-      zv = __ldg(I.u + (size_t)st * m + lane - n);
-      b1 = __ldg(I.r + (size_t)st * m + lane - n);
-    } else if (lane < RS) {
-      const size_t o = (size_t)(st + 1) * n + lane - n - m;
-      zv = __ldg(I.y + o);
-      b1 = __ldg(I.c + o);
-      b2 = __ldg(I.x + o);
-    }
+    // this lane's z entry and data terms, chosen by selects (lanes past RS
+    // load entry 0 of the c rows and never use it): no divergent branch
+    const bool xr = lane < n, ur = !xr && lane < n + m;
+    const int i = xr ? lane : ur ? lane - n : (lane < RS ? lane - n - m : 0);
+    const size_t ox = (size_t)st * n, ou = (size_t)st * m, oc = (size_t)(st + 1) * n;
+    const double *zb = xr ? I.x + ox : ur ? I.u + ou : I.y + oc;
+    const double *b1b = xr ? I.q + ox : ur ? I.r + ou : I.c + oc;
+    const double *b2b = xr ? I.y + ox : I.x + oc;
+    zv = __ldg(zb + i);
+    b1 = __ldg(b1b + i);
+    b2 = ur ? 0.0 : __ldg(b2b + i);
   }
 
   // Split the prefetched stage into shared memory (the caller syncs the warp
@@ -207,29 +205,26 @@ struct Res32Rows {
     commit_split<CB, m, M4, N4>(pM, nm, lane, s.Mh, s.Ml, s.Mth, s.Mtl);
     commit_split_sym<CR, m, M4>(pR, lane, s.Rh, s.Rl);
     // z entry of this lane and the row's data terms (float-float)
+    // x rows b = q - y_k, u rows r, c rows c - x_{k+1} - delta y_{k+1}, on
+    // every lane (b2 is zero on the u rows, the delta term a zero product
+    // off the c rows: both add exactly nothing); only the stores and the
+    // maxima depend on the lane
     bh = 0.f;
     bl = 0.f;
+    const bool xr = lane < n, ur = !xr && lane < n + m, cr = !xr && !ur && lane < RS;
+    const float2 zs = split_f64(zv);
+    ff_add(bh, bl, split_f64(b1));
+    ff_add(bh, bl, ff_neg(split_f64(b2)));
+    ff_fma(bh, bl, cr ? dsp : make_float2(0.f, 0.f), zs);
     if (lane < RS) {
-      const float2 zs = split_f64(zv);
-      if (lane < n) {
-        s.xh[lane] = zs.x;
-        s.xl[lane] = zs.y;
-        ff_add(bh, bl, split_f64(b1));
-        ff_add(bh, bl, ff_neg(split_f64(b2)));
-      } else if (lane < n + m) {
-        s.uh[lane - n] = zs.x;
-        s.ul[lane - n] = zs.y;
-        ff_add(bh, bl, split_f64(b1));
-      } else {
-        s.yh[lane - n - m] = zs.x;
-        s.yl[lane - n - m] = zs.y;
-        ff_add(bh, bl, split_f64(b1));
-        ff_add(bh, bl, ff_neg(split_f64(b2)));
-        ff_fma(bh, bl, dsp, zs);
-      }
-      zbits = max(zbits, abs_bits(zv));
-      bbits = max(bbits, abs_bits(b1));
+      float *dh = xr ? s.xh + lane : ur ? s.uh + (lane - n) : s.yh + (lane - n - m);
+      float *dl = xr ? s.xl + lane : ur ? s.ul + (lane - n) : s.yl + (lane - n - m);
+      *dh = zs.x;
+      *dl = zs.y;
     }
+    const bool act = lane < RS;
+    zbits = act ? max(zbits, abs_bits(zv)) : zbits;
+    bbits = act ? max(bbits, abs_bits(b1)) : bbits;
   }
 
   // This lane's row (lane < RS) after commit() and a warp sync.

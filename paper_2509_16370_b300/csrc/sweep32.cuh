@@ -265,20 +265,21 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
     // else a non-positive pivot of I + delta P + tau D proves it not PD
     // (bit 0); else the instance is escalated to the FP64 recursion (`sing`;
     // the bit stays 1 until that decides).
+    // (every lane runs the test on its column lane mod n of P; only lanes
+    // n..2n-1 count, so the warp takes no divergent branch)
     int bit = 1;
     bool pass = true;
-    if (lane >= n && lane < 2 * n) {
-      const int c = lane - n;
+    {
+      const int c = lane % n;
       float off = 0.f, diag = 0.f;
 #pragma unroll
       for (int i = 0; i < n; ++i) {
         const float val = el(Pc[i / 2], i & 1);
-        if (i == c)
-          diag = val;
-        else
-          off = __fadd_ru(off, fabsf(val));
+        diag = (i == c) ? val : diag;
+        off = (i == c) ? off : __fadd_ru(off, fabsf(val));
       }
-      pass = gershgorin_row_margin(diag, off, delta_dn, delta_up, kMarginTau);
+      const bool g = gershgorin_row_margin(diag, off, delta_dn, delta_up, kMarginTau);
+      pass = (lane >= n && lane < 2 * n) ? g : true;
     }
     if (!__all_sync(0xffffffffu, pass)) {
       // largest diagonal magnitude of I + delta P (shift floor)
@@ -346,15 +347,17 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
     // exact symmetry: W[i][c] = computed entry max(i,c) of column min(i,c)
     if (lane >= n && lane < 2 * n) st_row2<n>(s.Wc + (lane - n) * N4, v2);
     __syncwarp();
-    if (lane >= n && lane < 2 * n) {
-      const int c = lane - n;
+    {  // every lane gathers a column (lane mod n); lanes n..2n-1 store theirs
+      const int c = lane % n;
 #pragma unroll
       for (int q = 0; q < H2; ++q) {
         const int i0 = 2 * q, i1 = 2 * q + 1;
         v2[q] = make_float2(s.Wc[min(i0, c) * N4 + max(i0, c)], s.Wc[min(i1, c) * N4 + max(i1, c)]);
       }
-      st_row2<n>(s.W + c * N4, v2);
-      st_row2<n>(gWk + c * n, v2);
+      if (lane >= n && lane < 2 * n) {
+        st_row2<n>(s.W + c * N4, v2);
+        st_row2<n>(gWk + c * n, v2);
+      }
     }
     __syncwarp();
     return bit;
@@ -648,47 +651,55 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
       if (idx < m) s.kk[idx] = f.k.v[i];
     }
   };
+  const int fx = lane < n ? lane : 0, fu = lane < m ? lane : 0;  // rows of the rounds
   // one forward stage from the set holding its data; the set is refilled
   // with stage k + 2 once committed
   auto fstage = [&](FwdSet &f, int k) {
     fcommit(f);
     if (k + 2 < N) fprefetch(f, k + 2);
     __syncwarp();
+    // (every lane runs each round, lanes past its rows on row 0; only the
+    // stores depend on the lane)
     // u_k = K_k x_k + k_k
-    if (lane < m) {
-      float2 kr[H2], xr[H2];
-      lds_row2<n>(s.K + lane * N4, kr);
-      lds_row2<n>(s.x, xr);
-      const float t = dot2<n>(kr, xr) + s.kk[lane];
-      s.u[lane] = t;
-      I.u[(size_t)k * m + lane] = widen(t);
+    float2 xr[H2];
+    lds_row2<n>(s.x, xr);
+    {
+      float2 kr[H2];
+      lds_row2<n>(s.K + fu * N4, kr);
+      const float t = dot2<n>(kr, xr) + s.kk[fu];
+      if (lane < m) {
+        s.u[lane] = t;
+        I.u[(size_t)k * m + lane] = widen(t);
+      }
     }
     __syncwarp();
     // v = A x + B u + c_{k+1} - delta p_{k+1}
-    if (lane < n) {
-      float2 ar[H2], xr[H2], br[M2], ur[M2];
-      lds_row2<n>(s.A + lane * N4, ar);
-      lds_row2<n>(s.x, xr);
-      lds_row2<m>(s.B + lane * M4, br);
+    {
+      float2 ar[H2], br[M2], ur[M2];
+      lds_row2<n>(s.A + fx * N4, ar);
+      lds_row2<m>(s.B + fx * M4, br);
       lds_row2<m>(s.u, ur);
       float2 acc = mul2(ar[0], xr[0]);
 #pragma unroll
       for (int q = 1; q < H2; ++q) acc = fma2(ar[q], xr[q], acc);
 #pragma unroll
       for (int q = 0; q < M2; ++q) acc = fma2(br[q], ur[q], acc);
-      s.v[lane] = acc.x + acc.y + fmaf(-delta, s.p[lane], s.c[lane]);
+      const float vv = acc.x + acc.y + fmaf(-delta, s.p[fx], s.c[fx]);
+      if (lane < n) s.v[lane] = vv;
     }
     __syncwarp();
     // x_{k+1} = v - delta W v, y_{k+1} = W v + p_{k+1}
-    if (lane < n) {
+    {
       float2 wr[H2], vr[H2];
-      lds_row2<n>(s.W + lane * N4, wr);
+      lds_row2<n>(s.W + fx * N4, wr);
       lds_row2<n>(s.v, vr);
       const float t = dot2<n>(wr, vr);
-      const float xv = fmaf(-delta, t, s.v[lane]), yv = t + s.p[lane];
-      s.x[lane] = xv;
-      I.x[(size_t)(k + 1) * n + lane] = widen(xv);
-      I.y[(size_t)(k + 1) * n + lane] = widen(yv);
+      const float xv = fmaf(-delta, t, s.v[fx]), yv = t + s.p[fx];
+      if (lane < n) {
+        s.x[lane] = xv;
+        I.x[(size_t)(k + 1) * n + lane] = widen(xv);
+        I.y[(size_t)(k + 1) * n + lane] = widen(yv);
+      }
     }
     __syncwarp();
   };
