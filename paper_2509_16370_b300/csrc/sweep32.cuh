@@ -364,13 +364,14 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
   };
 
   for (int k = N - 1; k >= 0; --k) {
-    // v = c_{k+1} - delta p_{k+1} (lane VL), read by phase (a)
-    if (SOLVE && lane == VL) {
+    // v = c_{k+1} - delta p_{k+1} (lane VL), read by phase (a); every lane
+    // forms it (pv is zero off lane VL), lane VL stores it
+    if (SOLVE) {
       float2 cr[H2];
       lds_row2<n>(s.c, cr);
 #pragma unroll
       for (int q = 0; q < H2; ++q) cr[q] = fma2(bcast2(-delta), pv[q], cr[q]);
-      st_row2<n>(s.v, cr);
+      if (lane == VL) st_row2<n>(s.v, cr);
     }
     bool sing = false;
     const int bit0 = state_pivot(gW + (size_t)(k + 1) * nn, sing);
@@ -378,18 +379,8 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
     // ---- (a) column lane of W [A | B | v]; lane VL then adds p: g
     float2 wz[H2];
     {
-      const float *yp;
-      int ys;
-      if (lane < n) {
-        yp = s.A + lane;
-        ys = N4;
-      } else if (lane < n + m) {
-        yp = s.B + (lane - n);
-        ys = M4;
-      } else {
-        yp = s.v;
-        ys = 1;
-      }
+      const float *yp = lane < n ? s.A + lane : (lane < n + m ? s.B + (lane - n) : s.v);
+      const int ys = lane < n ? N4 : (lane < n + m ? M4 : 1);
 #pragma unroll
       for (int q = 0; q < H2; ++q) wz[q] = make_float2(0.f, 0.f);
 #pragma unroll
@@ -400,7 +391,7 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
 #pragma unroll
         for (int q = 0; q < H2; ++q) wz[q] = fma2(wr[q], y, wz[q]);
       }
-      if (SOLVE && lane == VL) {
+      if (SOLVE) {  // lane VL adds p (pv is zero elsewhere)
 #pragma unroll
         for (int q = 0; q < H2; ++q) wz[q] = add2(wz[q], pv[q]);
       }
@@ -426,17 +417,8 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
 #pragma unroll
         for (int q = 0; q < M2; ++q) fb[q] = fma2(br[q], w, fb[q]);
       }
-      const float *qa, *qb;
-      if (lane < n) {
-        qa = s.Q + lane * N4;
-        qb = s.M + lane * M4;
-      } else if (lane < n + m) {
-        qa = s.Q;
-        qb = s.R + (lane - n) * M4;
-      } else {
-        qa = s.q;
-        qb = s.r;
-      }
+      const float *qa = lane < n ? s.Q + lane * N4 : (lane < n + m ? s.Q : s.q);
+      const float *qb = lane < n ? s.M + lane * M4 : (lane < n + m ? s.R + (lane - n) * M4 : s.r);
       float2 ta[H2], tb[M2];
       lds_row2<n>(qa, ta);
       lds_row2<m>(qb, tb);
@@ -444,9 +426,9 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
       for (int q = 0; q < H2; ++q) fa[q] = add2(fa[q], ta[q]);
 #pragma unroll
       for (int q = 0; q < M2; ++q) fb[q] = add2(fb[q], tb[q]);
-      if (!SOLVE && lane == VL) {
+      if (!SOLVE) {
 #pragma unroll
-        for (int q = 0; q < M2; ++q) fb[q] = make_float2(0.f, 0.f);
+        for (int q = 0; q < M2; ++q) fb[q] = lane == VL ? make_float2(0.f, 0.f) : fb[q];
       }
     }
 
@@ -506,23 +488,24 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
     float kc[m];
 #pragma unroll
     for (int t = 0; t < m; ++t) kc[t] = -rhs[t];
-    if (lane < n) {
+    // (stores only, each under its own lane predicate)
+    {
+      float2 k2[M2], r2[M2];
 #pragma unroll
-      for (int t = 0; t < m; ++t) {
-        gK[(size_t)k * nm + t * n + lane] = kc[t];
-        s.H[t * N4 + lane] = el(fb[t / 2], t & 1);
+      for (int q = 0; q < M2; ++q) {
+        k2[q] = make_float2(kc[2 * q], kc[2 * q + 1]);
+        r2[q] = make_float2(rhs[2 * q], rhs[2 * q + 1]);
       }
-    } else if (SOLVE && lane == VL) {
-      float2 k2[M2];
+      if (lane < n) {
 #pragma unroll
-      for (int q = 0; q < M2; ++q) k2[q] = make_float2(kc[2 * q], kc[2 * q + 1]);
-      st_row2<m>(gkv + (size_t)k * m, k2);
-    } else if (lane > VL && lane <= VL + m) {
+        for (int t = 0; t < m; ++t) {
+          gK[(size_t)k * nm + t * n + lane] = kc[t];
+          s.H[t * N4 + lane] = el(fb[t / 2], t & 1);
+        }
+      }
+      if (SOLVE && lane == VL) st_row2<m>(gkv + (size_t)k * m, k2);
       // G^{-1} is symmetric up to rounding: column t stored as row t
-      float2 r2[M2];
-#pragma unroll
-      for (int q = 0; q < M2; ++q) r2[q] = make_float2(rhs[2 * q], rhs[2 * q + 1]);
-      st_row2<m>(gGi + (size_t)k * mmm + (lane - VL - 1) * m, r2);
+      if (lane > VL && lane <= VL + m) st_row2<m>(gGi + (size_t)k * mmm + (lane - VL - 1) * m, r2);
     }
     __syncwarp();
 
@@ -535,10 +518,10 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
 #pragma unroll
       for (int q = 0; q < H2; ++q) fa[q] = fma2(hr[q], kt, fa[q]);
     }
-    if (SOLVE && lane == VL) {
-      st_row2<n>(gpv + (size_t)k * n, fa);
+    if (SOLVE) {
+      if (lane == VL) st_row2<n>(gpv + (size_t)k * n, fa);
 #pragma unroll
-      for (int q = 0; q < H2; ++q) pv[q] = fa[q];
+      for (int q = 0; q < H2; ++q) pv[q] = lane == VL ? fa[q] : pv[q];
     }
     // exact symmetry: P[i][c] = computed entry max(i,c) of column min(i,c)
     if (lane < n) st_row2<n>(s.Pt + lane * N4, fa);
