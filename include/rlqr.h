@@ -243,8 +243,7 @@ rlqr_status rlqr_tune_scan_set(int32_t N, int32_t nx, int32_t nu, const rlqr_opt
  * pass on two warps per instance (one runs the recursion, the other the
  * copies, right-hand sides, the rows of K dz and, route 7, the residual),
  * which shortens each instance's chain at more instructions in all.
- * Without a recorded route the refinement takes two warps per instance when
- * a launch holds at most 296 instances, else one.  Ragged mixed-precision
+ * Without a recorded route the refinement takes one warp per instance.  Ragged mixed-precision
  * batches whose size classes are all
  * among (4,2), (6,2), (12,4), (24,8), (32,8), (48,16): the sweep route,
  * 3 = one launch per size class on the library's concurrent streams (the

@@ -159,8 +159,7 @@ struct BatchArgs {
   // residual itself (no separate first-residual launch)
   int fused_res;
   // warps per instance of the mixed refinement passes of the warp sizes:
-  // 1 (k_refine_tab), 2 (k_refine_duo), 0 = 2 when the launch holds at most
-  // two instances per SM, else 1
+  // 1 (k_refine_tab), 2 (k_refine_duo), 0 = 1
   int refine_warps;
 };
 

@@ -124,9 +124,11 @@ static cudaError_t launch_solve_warp(const BatchArgs &a, cudaStream_t s) {
     const bool fused = a.fused_res && a.rpass == 0;
     // later passes find most instances converged: fewer, striding blocks
     const int grid = a.rpass == 0 ? a.count : std::min(a.count, 148 * 4);
-    // two warps per instance shorten each instance's chain but issue more
-    // instructions: they win while the SMs hold few instances
-    const bool duo = a.refine_warps == 2 || (a.refine_warps == 0 && a.count <= 2 * 148);
+    // two warps per instance (routes 6 and 7 of the tuner) split each
+    // stage's work between a chain warp and a copy / row warp; with the
+    // branch-free one-warp rounds the single warp is faster at every batch
+    // size measured (1 to 1024 instances), so it is the default
+    const bool duo = a.refine_warps == 2;
     if (duo) {
       auto kern = fused ? k_refine_duo<NX, NU, true> : k_refine_duo<NX, NU, false>;
       const size_t bytes = refine_duo_smem<NX, NU>();

@@ -169,6 +169,10 @@ __device__ __forceinline__ void refine_duo_instance(const BatchArgs &a, int slot
   constexpr int CP = (nn + 31) / 32, CB = (nm + 31) / 32, CR = (mmm + 31) / 32;
   SM &s = *reinterpret_cast<SM *>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // rows of the chain's rounds this lane works on: bi (< n), bt (< m), bk (row
+  // lane - n of G^{-1} on lanes n .. n+m-1); 0 elsewhere
+  const int bi = lane < n ? lane : 0, bt = lane < m ? lane : 0;
+  const int bk = (lane >= n && lane < n + m) ? lane - n : 0;
   const int b = inst_of(a, slot);
   const Inst I = get_inst(a, b);
   InstState *stp = I.st;
@@ -252,47 +256,54 @@ __device__ __forceinline__ void refine_duo_instance(const BatchArgs &a, int slot
       const int k = N - 1 - t;
       duo_sync<1, DB>(1 + t % DB);  // FULL: stage k's slot is ready
       const BS &d = bring[t % DB];
-      if (lane < n) s.cr[lane] = fmaf(-delta, s.p[lane], d.cf[lane]);  // v = c' - delta p
+      // (every lane runs each round on a clamped row; only the stores depend
+      // on the lane, so the chain takes no divergent branch)
+      {
+        const float cv = fmaf(-delta, s.p[bi], d.cf[bi]);  // v = c' - delta p
+        if (lane < n) s.cr[lane] = cv;
+      }
       __syncwarp();
       // g = p + W v
-      if (lane < n) {
+      {
         float2 wr[H2], vr[H2];
-        ld_seg<H2, 0, H2>(d.W + lane * N4, wr);
+        ld_seg<H2, 0, H2>(d.W + bi * N4, wr);
         ld_seg<H2, 0, H2>(s.cr, vr);
-        s.g[lane] = s.p[lane] + dot2<n>(wr, vr);
+        const float gv = s.p[bi] + dot2<n>(wr, vr);
+        if (lane < n) s.g[lane] = gv;
       }
       __syncwarp();
       // h = r' + B^T g
       float2 gr[H2];
       ld_seg<H2, 0, H2>(s.g, gr);
-      if (lane < m) {
+      {
         float2 br[H2];
-        ld_seg<H2, 0, H2>(d.Bt + lane * N4, br);
-        s.h[lane] = d.rf[lane] + dot2<n>(br, gr);
+        ld_seg<H2, 0, H2>(d.Bt + bt * N4, br);
+        const float hv = d.rf[bt] + dot2<n>(br, gr);
+        if (lane < m) s.h[lane] = hv;
       }
       __syncwarp();
       // p_k = q' + A^T g + K^T h (lanes < n);  k_k = -G^{-1} h (lanes n .. n+m-1)
       float2 hr[U2];
       ld_seg<U2, 0, U2>(s.h, hr);
-      if (lane < n) {
-        float2 ar[H2], kr[U2];
-        ld_seg<H2, 0, H2>(d.At + lane * N4, ar);
-        ld_seg<U2, 0, U2>(d.Kt + lane * M4, kr);
-        float2 acc = mul2(ar[0], gr[0]);
+      {
+        float2 ar[H2], kr[U2], gi[U2];
+        ld_seg<H2, 0, H2>(d.At + bi * N4, ar);
+        ld_seg<U2, 0, U2>(d.Kt + bi * M4, kr);
+        ld_seg<U2, 0, U2>(d.Gi + bk * M4, gi);
+        float2 acc = mul2(ar[0], gr[0]), acck = mul2(gi[0], hr[0]);
 #pragma unroll
         for (int q = 1; q < H2; ++q) acc = fma2(ar[q], gr[q], acc);
 #pragma unroll
         for (int q = 0; q < U2; ++q) acc = fma2(kr[q], hr[q], acc);
-        const float pv = d.qf[lane] + (acc.x + acc.y);
-        s.p[lane] = pv;
-        gpv[(size_t)k * n + lane] = pv;
-      } else if (lane < n + m) {
-        float2 gi[U2];
-        ld_seg<U2, 0, U2>(d.Gi + (lane - n) * M4, gi);
-        float2 acc = mul2(gi[0], hr[0]);
 #pragma unroll
-        for (int q = 1; q < U2; ++q) acc = fma2(gi[q], hr[q], acc);
-        gkv[(size_t)k * m + lane - n] = -(acc.x + acc.y);
+        for (int q = 1; q < U2; ++q) acck = fma2(gi[q], hr[q], acck);
+        const float pv = d.qf[bi] + (acc.x + acc.y), kv = -(acck.x + acck.y);
+        if (lane < n) {
+          s.p[lane] = pv;
+          gpv[(size_t)k * n + lane] = pv;
+        } else if (lane < n + m) {
+          gkv[(size_t)k * m + lane - n] = kv;
+        }
       }
       __syncwarp();
       if (t < N - DB) duo_arrive<DB + 1, DB + NE>(DB + 1 + t % NE);  // EMPTY: slot free
@@ -478,38 +489,42 @@ __device__ __forceinline__ void refine_duo_instance(const BatchArgs &a, int slot
       // du_k = K_k dx_k + k_k
       float2 xr[H2];
       ld_seg<H2, 0, H2>(vk.dx, xr);
-      if (lane < m) {
+      {
         float2 kr[H2];
-        ld_seg<H2, 0, H2>(f.K + lane * N4, kr);
-        vk.du[lane] = dot2<n>(kr, xr) + f.kk[lane];
+        ld_seg<H2, 0, H2>(f.K + bt * N4, kr);
+        const float duv = dot2<n>(kr, xr) + f.kk[bt];
+        if (lane < m) vk.du[lane] = duv;
       }
       __syncwarp();
       // w = A dx + B du + c'_{k+1} - delta p_{k+1}
       float2 ur[U2];
       ld_seg<U2, 0, U2>(vk.du, ur);
-      float wv = 0.f;
-      if (lane < n) {
+      float wv;
+      {
         float2 ar[H2], br[U2];
-        ld_seg<H2, 0, H2>(f.A + lane * N4, ar);
-        ld_seg<U2, 0, U2>(f.B + lane * M4, br);
+        ld_seg<H2, 0, H2>(f.A + bi * N4, ar);
+        ld_seg<U2, 0, U2>(f.B + bi * M4, br);
         float2 acc = mul2(ar[0], xr[0]);
 #pragma unroll
         for (int q = 1; q < H2; ++q) acc = fma2(ar[q], xr[q], acc);
 #pragma unroll
         for (int q = 0; q < U2; ++q) acc = fma2(br[q], ur[q], acc);
-        wv = (acc.x + acc.y) + f.cv[lane];
-        s.w[lane] = wv;
+        wv = (acc.x + acc.y) + f.cv[bi];
+        if (lane < n) s.w[lane] = wv;
       }
       __syncwarp();
       // dx_{k+1} = w - delta W w, dy_{k+1} = W w + p_{k+1}
       float2 vr[H2];
       ld_seg<H2, 0, H2>(s.w, vr);
-      if (lane < n) {
+      {
         float2 wr[H2];
-        ld_seg<H2, 0, H2>(f.W + lane * N4, wr);
+        ld_seg<H2, 0, H2>(f.W + bi * N4, wr);
         const float t = dot2<n>(wr, vr);
-        vn.dx[lane] = fmaf(-delta, t, wv);
-        vn.dy[lane] = t + f.p[lane];
+        const float dxv = fmaf(-delta, t, wv), dyv = t + f.p[bi];
+        if (lane < n) {
+          vn.dx[lane] = dxv;
+          vn.dy[lane] = dyv;
+        }
       }
       __syncwarp();
       duo_arrive<NF + 1, NF + NV>(NF + 1 + k % NV);  // VEC: stage k's vectors written
