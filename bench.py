@@ -1154,14 +1154,21 @@ def run_ours(args):
     tune = {}
     for prec, name in ((rlqr.RLQR_MIXED, "mixed"), (rlqr.RLQR_FP64, "fp64")):
         o_t, ws_t, st_t, _, _ = setup(prec)
-        route, tms = rlqr.rlqr_autotune_batched(db, o_t, ws_t, st_t)
+        if args.residual_route:
+            # a fixed route (profiling runs: timings under a profiler would
+            # steer the tuner to another route than the plain bench takes)
+            route = args.residual_route if prec == rlqr.RLQR_MIXED else rlqr.RES_ROUTE_WARP
+            rlqr.rlqr_tune_batched_set(db, o_t, route)
+            tms = None
+        else:
+            route, tms = rlqr.rlqr_autotune_batched(db, o_t, ws_t, st_t)
         tune[name] = {"residual_route": {rlqr.RES_ROUTE_WARP: "warp",
                                          rlqr.RES_ROUTE_GRID: "grid",
                                          rlqr.RES_ROUTE_FUSED: "fused into the first pass",
                                          rlqr.RES_ROUTE_WARP_DUO: "warp, two-warp refinement",
                                          rlqr.RES_ROUTE_FUSED_DUO:
                                              "fused into the first pass, two-warp refinement"}[route],
-                      "ms": round(tms, 4)}
+                      "ms": None if tms is None else round(tms, 4)}
         del ws_t
     with ClockSampler(local) as clk:
         ms_mixed, report, chk_mixed = timed(rlqr.RLQR_MIXED, args.steps, args.warmup, True)
@@ -1312,6 +1319,9 @@ def main():
                          "Gauss-Newton)")
     ap.add_argument("--ipm-max-iter", type=int, default=0,
                     help="with --ipm: iteration limit (default 300; smaller for profiling)")
+    ap.add_argument("--residual-route", type=int, default=0,
+                    help="fix the batched residual route of the headline batch instead of "
+                         "autotuning it (1 = warp residual; for profiler runs)")
     ap.add_argument("--latency", action="store_true",
                     help="latency of one factor + solve of the small single instance")
     ap.add_argument("--ragged", type=int, default=0,
