@@ -282,19 +282,42 @@ __global__ void k_plan(int count, const int32_t *dN, const int32_t *dn, const in
     s += (int64_t)ws_layout(dN[b], dn[b], dm[b], tsize).total;
     s2 += (int64_t)dN[b] + 1;
   }
-  part[t] = s;
-  part2[t] = s2;
-  __syncthreads();
-  if (t == 0) {
-    int64_t acc = (int64_t)batch_header_bytes(count), acc2 = 0;
-    for (int i = 0; i < T; ++i) {
-      const int64_t v = part[i], v2 = part2[i];
-      part[i] = acc;
-      part2[i] = acc2;
-      acc += v;
-      acc2 += v2;
+  // exclusive prefix sums of the per-thread partials over the block: an
+  // inclusive shuffle scan in each warp, then one over the warp totals
+  // (blockDim.x a multiple of 32, at most 1024)
+  __shared__ int64_t wsum[32], wsum2[32];
+  const int lane = t & 31, wid = t >> 5, nw = T >> 5;
+  int64_t in = s, in2 = s2;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t u = __shfl_up_sync(0xffffffffu, in, o), u2 = __shfl_up_sync(0xffffffffu, in2, o);
+    if (lane >= o) {
+      in += u;
+      in2 += u2;
     }
   }
+  if (lane == 31) {
+    wsum[wid] = in;
+    wsum2[wid] = in2;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    int64_t w = lane < nw ? wsum[lane] : 0, w2 = lane < nw ? wsum2[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t u = __shfl_up_sync(0xffffffffu, w, o), u2 = __shfl_up_sync(0xffffffffu, w2, o);
+      if (lane >= o) {
+        w += u;
+        w2 += u2;
+      }
+    }
+    wsum[lane] = w;  // inclusive over warps 0..lane
+    wsum2[lane] = w2;
+  }
+  __syncthreads();
+  const int64_t before = wid > 0 ? wsum[wid - 1] : 0, before2 = wid > 0 ? wsum2[wid - 1] : 0;
+  part[t] = (int64_t)batch_header_bytes(count) + before + in - s;
+  part2[t] = before2 + in2 - s2;
   __syncthreads();
   int64_t *spre = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(ows) +
                                               align_up((size_t)count * sizeof(int64_t)) +
