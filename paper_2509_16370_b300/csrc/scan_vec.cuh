@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(32) k_scan_pvec(BatchArgs a, ScanLayout SL, si
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM &s = *reinterpret_cast<SM *>(smem_raw);
   const int lane = threadIdx.x, c = blockIdx.x;
+  const int lm = lane < m ? lane : 0;  // row of the m-row rounds (0 past m)
   const Inst I = get_inst(a, 0);
   if (FROM_RES && (I.st->converged || I.st->pivot_status == RLQR_ERR_SINGULAR)) return;
   const int N = I.N, s0 = c * SL.L, e0 = min(s0 + SL.L, N);
@@ -174,8 +175,11 @@ __global__ void __launch_bounds__(32) k_scan_pvec(BatchArgs a, ScanLayout SL, si
     // g = p + W (c' - delta p)
     if (lane < n) s.g[lane] = s.p[lane] + scan::dotc<T, NX>(s.W + lane * n, s.v);
     __syncwarp();
-    // h = r' + B^T g
-    if (lane < m) s.h[lane] = cr + scan::dots<T, NX>(s.B + lane, m, s.g);
+    // h = r' + B^T g (every lane on a clamped column; lanes < m store)
+    {
+      const T hv = cr + scan::dots<T, NX>(s.B + lm, m, s.g);
+      if (lane < m) s.h[lane] = hv;
+    }
     __syncwarp();
     // p_i = q' + A^T g + K^T h;  k_i = -G^{-1} h
     T pnew = 0;
@@ -183,7 +187,10 @@ __global__ void __launch_bounds__(32) k_scan_pvec(BatchArgs a, ScanLayout SL, si
       pnew = cq + scan::dots<T, NX>(s.A + lane, n, s.g) + scan::dots<T, NU>(s.K + lane, n, s.h);
       if (MODE == 1) gpv[(size_t)i * n + lane] = pnew;
     }
-    if (MODE == 1 && lane < m) gkv[(size_t)i * m + lane] = -scan::dotc<T, NU>(s.G + lane * m, s.h);
+    if (MODE == 1) {
+      const T kv = -scan::dotc<T, NU>(s.G + lm * m, s.h);
+      if (lane < m) gkv[(size_t)i * m + lane] = kv;
+    }
     __syncwarp();
     if (lane < n) s.p[lane] = pnew;
   }
@@ -299,6 +306,7 @@ __global__ void __launch_bounds__(32) k_scan_xvec(BatchArgs a, ScanLayout SL, si
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SM &s = *reinterpret_cast<SM *>(smem_raw);
   const int lane = threadIdx.x, c = blockIdx.x;
+  const int lm = lane < m ? lane : 0;  // row of the m-row rounds (0 past m)
   const Inst I = get_inst(a, 0);
   if (FROM_RES && (I.st->converged || I.st->pivot_status == RLQR_ERR_SINGULAR)) return;
   const int N = I.N, s0 = c * SL.L, e0 = min(s0 + SL.L, N);
@@ -379,8 +387,11 @@ __global__ void __launch_bounds__(32) k_scan_xvec(BatchArgs a, ScanLayout SL, si
     if (lane < n) s.pn[lane] = cvp;
     if (i + 1 < e0) prefetch(i + 1);
     __syncwarp();
-    // u_i = K x_i + k_i
-    if (lane < m) s.u[lane] = cvk + scan::dotc<T, NX>(s.K + lane * n, s.x);
+    // u_i = K x_i + k_i (every lane on a clamped row; lanes < m store)
+    {
+      const T uv = cvk + scan::dotc<T, NX>(s.K + lm * n, s.x);
+      if (lane < m) s.u[lane] = uv;
+    }
     __syncwarp();
     // v = A x + B u + c'_{i+1} - delta p_{i+1}
     if (lane < n)
