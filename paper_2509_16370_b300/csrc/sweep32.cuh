@@ -70,6 +70,11 @@ struct Sw32 {
   alignas(16) float x[N4];
   alignas(16) float u[M4];
   double S64[NX * NX];            // FP64 LDL^T of I + delta P (certificate fallback)
+  // sizes of chunk16_size: the forward rollout's ring of kFwdSlots stages,
+  // each A_k, W_{k+1}, B_k, K_k, c_{k+1}, p_{k+1}, k_k back to back
+  static constexpr int kFwdSlot = 2 * NX * NX + 2 * NX * NU + 2 * NX + NU;
+  static constexpr int kFwdSlots = 4;
+  alignas(16) float fring[chunk16_size(NX, NU) ? kFwdSlots * kFwdSlot : 4];
 };
 
 // r[q] = (p[2q], p[2q+1]); 16-byte vector loads when L % 4 == 0 (rows are
@@ -637,10 +642,10 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
   const int fx = lane < n ? lane : 0, fu = lane < m ? lane : 0;  // rows of the rounds
   // one forward stage from the set holding its data; the set is refilled
   // with stage k + 2 once committed
-  auto fstage = [&](FwdSet &f, int k) {
-    fcommit(f);
-    if (k + 2 < N) fprefetch(f, k + 2);
-    __syncwarp();
+  // one forward stage from its operands in shared memory (row strides ldn
+  // for n-wide rows, ldm for m-wide rows)
+  auto frounds = [&](const float *sA, const float *sW, const float *sB, const float *sK,
+                     const float *sc, const float *sp, const float *skk, int ldn, int ldm, int k) {
     // (every lane runs each round, lanes past its rows on row 0; only the
     // stores depend on the lane)
     // u_k = K_k x_k + k_k
@@ -648,8 +653,8 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
     lds_row2<n>(s.x, xr);
     {
       float2 kr[H2];
-      lds_row2<n>(s.K + fu * N4, kr);
-      const float t = dot2<n>(kr, xr) + s.kk[fu];
+      lds_row2<n>(sK + fu * ldn, kr);
+      const float t = dot2<n>(kr, xr) + skk[fu];
       if (lane < m) {
         s.u[lane] = t;
         I.u[(size_t)k * m + lane] = widen(t);
@@ -659,25 +664,25 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
     // v = A x + B u + c_{k+1} - delta p_{k+1}
     {
       float2 ar[H2], br[M2], ur[M2];
-      lds_row2<n>(s.A + fx * N4, ar);
-      lds_row2<m>(s.B + fx * M4, br);
+      lds_row2<n>(sA + fx * ldn, ar);
+      lds_row2<m>(sB + fx * ldm, br);
       lds_row2<m>(s.u, ur);
       float2 acc = mul2(ar[0], xr[0]);
 #pragma unroll
       for (int q = 1; q < H2; ++q) acc = fma2(ar[q], xr[q], acc);
 #pragma unroll
       for (int q = 0; q < M2; ++q) acc = fma2(br[q], ur[q], acc);
-      const float vv = acc.x + acc.y + fmaf(-delta, s.p[fx], s.c[fx]);
+      const float vv = acc.x + acc.y + fmaf(-delta, sp[fx], sc[fx]);
       if (lane < n) s.v[lane] = vv;
     }
     __syncwarp();
     // x_{k+1} = v - delta W v, y_{k+1} = W v + p_{k+1}
     {
       float2 wr[H2], vr[H2];
-      lds_row2<n>(s.W + fx * N4, wr);
+      lds_row2<n>(sW + fx * ldn, wr);
       lds_row2<n>(s.v, vr);
       const float t = dot2<n>(wr, vr);
-      const float xv = fmaf(-delta, t, s.v[fx]), yv = t + s.p[fx];
+      const float xv = fmaf(-delta, t, s.v[fx]), yv = t + sp[fx];
       if (lane < n) {
         s.x[lane] = xv;
         I.x[(size_t)(k + 1) * n + lane] = widen(xv);
@@ -687,12 +692,53 @@ __device__ __forceinline__ void sweep32_body(const BatchArgs &a, int b, unsigned
     __syncwarp();
   };
   __syncwarp();
-  FwdSet f0, f1;
-  fprefetch(f0, 0);
-  if (N > 1) fprefetch(f1, 1);
-  for (int k = 0; k < N; k += 2) {
-    fstage(f0, k);
-    if (k + 1 < N) fstage(f1, k + 1);
+  if constexpr (chunk16_size(NX, NU)) {
+    // rows of a multiple of 16 bytes: every operand block of a stage is
+    // contiguous in global memory, so a ring of kFwdSlots stages is filled
+    // by 16-byte cp.async chunks, the lanes taking them in turn (the factor
+    // and copies were written by this warp; the warp syncs above order those
+    // stores before the copies, which read through L2)
+    constexpr int SL = SM::kFwdSlot, D = SM::kFwdSlots;
+    constexpr int oW = nn, oB = 2 * nn, oK = 2 * nn + nm, oc = 2 * nn + 2 * nm, op = oc + n,
+                  ok = op + n;
+    static_assert(SL % 4 == 0 && nn % 4 == 0 && nm % 4 == 0 && n % 4 == 0 && m % 4 == 0,
+                  "16-byte blocks");
+    auto cp = [](const float *p) { return reinterpret_cast<const char *>(p); };
+    const Blk16 fb[7] = {{cp(gAf), nn * 4, 0, nn / 4},           {cp(gW + nn), nn * 4, oW * 4, nn / 4},
+                         {cp(gBf), nm * 4, oB * 4, nm / 4},     {cp(gK), nm * 4, oK * 4, nm / 4},
+                         {cp(gcf + n), n * 4, oc * 4, n / 4},    {cp(gpv + n), n * 4, op * 4, n / 4},
+                         {cp(gkv), m * 4, ok * 4, m / 4}};
+    ChunkPlan<7, (SL / 4 + 31) / 32> plan;
+    plan.init(fb, lane);
+    auto fissue = [&](int k) {
+      if (k < N) plan.issue(reinterpret_cast<unsigned char *>(s.fring + (k % D) * SL), k);
+      cp_async_commit();
+    };
+#pragma unroll 1
+    for (int j = 0; j < D - 1; ++j) fissue(j);
+#pragma unroll 1
+    for (int k = 0; k < N; ++k) {
+      fissue(k + D - 1);
+      cp_async_wait<D - 1>();
+      __syncwarp();
+      const float *sl = s.fring + (k % D) * SL;
+      frounds(sl, sl + oW, sl + oB, sl + oK, sl + oc, sl + op, sl + ok, n, m, k);
+    }
+    cp_async_wait<0>();
+  } else {
+    FwdSet f0, f1;
+    fprefetch(f0, 0);
+    if (N > 1) fprefetch(f1, 1);
+    auto fstage = [&](FwdSet &f, int k) {
+      fcommit(f);
+      if (k + 2 < N) fprefetch(f, k + 2);
+      __syncwarp();
+      frounds(s.A, s.W, s.B, s.K, s.c, s.p, s.kk, N4, M4, k);
+    };
+    for (int k = 0; k < N; k += 2) {
+      fstage(f0, k);
+      if (k + 1 < N) fstage(f1, k + 1);
+    }
   }
 }
 
