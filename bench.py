@@ -139,12 +139,12 @@ class ClockSampler:
 # capture each (the sweep and the residual at 296 instances of this workload,
 # the refinement pass at all 1024; the kernels as they are in this source;
 # see profiles/), scaled by the stages a launch processes.
-TRAFFIC_PER_STAGE = {"k_seq_fp32_solve": 7479.0, "k_residual_ff": 3920.0,
+TRAFFIC_PER_STAGE = {"k_seq_fp32_solve": 7481.0, "k_residual_ff": 3920.0,
                      "k_solve_refine": 4995.0}
 # Warp instructions per instance-stage of the FP32 warp sweep (backward +
 # forward) from the same capture: the length of one instance's instruction
 # stream, which one warp must issue in order.
-SWEEP_INSTR_PER_STAGE = {"k_seq_fp32_solve": 1467.0}
+SWEEP_INSTR_PER_STAGE = {"k_seq_fp32_solve": 1484.0}
 SM_COUNT, SMSP_PER_SM = 148, 4
 
 
