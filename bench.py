@@ -1249,8 +1249,14 @@ def run_ours(args):
                      "escalated_instances": chk_mixed["escalated"]},
         "fp64_plain": {"value": fp64_value, "ms_per_step": ms_fp64,
                        "max_rel_resid": chk_fp64["max_rel"], "all_le_tol": chk_fp64["ok"],
-                       "roofline": fp64_sweep_roofline(report64, n, m, stages, pipes)},
+                       "roofline": fp64_sweep_roofline(report64, n, m, stages, pipes),
+                       # the plain recursion's own floor: its flops at the
+                       # measured FP64 FMA rate (factor alone, no residual)
+                       "fp64_pipe_floor_ms_per_step":
+                           seq_flops_per_stage(n, m) * stages / (pipes["fp64_tflops"] * 1e12) * 1e3},
         "speedup_vs_fp64_plain": value / fp64_value,
+        "speedup_vs_fp64_pipe_floor":
+            seq_flops_per_stage(n, m) * stages / (pipes["fp64_tflops"] * 1e12) * 1e3 / ms_mixed,
         "e2e": {"value": job_rate(stages, world, ms_e2e), "unit": "stage-solves/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
                 "batches_in_flight": 2, "all_le_tol": e2e_ok},
