@@ -140,7 +140,7 @@ class ClockSampler:
 # the refinement pass at all 1024; the kernels as they are in this source;
 # see profiles/), scaled by the stages a launch processes.
 TRAFFIC_PER_STAGE = {"k_seq_fp32_solve": 7481.0, "k_residual_ff": 3920.0,
-                     "k_solve_refine": 4995.0}
+                     "k_solve_refine": 5000.0}
 # Warp instructions per instance-stage of the FP32 warp sweep (backward +
 # forward) from the same capture: the length of one instance's instruction
 # stream, which one warp must issue in order.
