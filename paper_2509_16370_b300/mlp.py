@@ -104,6 +104,30 @@ class WarmStartNet:
                                        _stream(None)), "rlqr_mlp_train_step")
 
 
+def save_checkpoint(net: WarmStartNet, path: str) -> None:
+    """Training state of `net` to an .npz file: the FP32 parameters, the Adam
+    moments, the step counter (the bias correction's t) and the dimensions.
+    The BF16 copy is not stored: it is the rounding of the parameters and is
+    rebuilt on load."""
+    d = net.d
+    np.savez(path, p=net.p.cpu().numpy(), m=net.m.cpu().numpy(), v=net.v.cpu().numpy(),
+             step=np.int64(net.step),
+             dims=np.array([d.n_in, d.width, d.n_out, d.max_rows], np.int64))
+
+
+def load_checkpoint(path: str, device="cuda") -> WarmStartNet:
+    """A network restored from save_checkpoint: training continues from it as
+    from the saved network (same parameters, moments and step counter, so the
+    next Adam steps are bit-identical)."""
+    z = np.load(path)
+    n_in, width, n_out, max_rows = (int(v) for v in z["dims"])
+    net = WarmStartNet(make_dims(n_in, width, n_out, max_rows), z["p"], device=device)
+    net.m.copy_(torch.from_numpy(z["m"]).to(device))
+    net.v.copy_(torch.from_numpy(z["v"]).to(device))
+    net.step = int(z["step"])
+    return net
+
+
 def init_params(d: rlqr_mlp_dims, seed: int) -> np.ndarray:
     """He-uniform weights, zero biases, zero padding (host, seeded)."""
     rng = np.random.default_rng(seed)

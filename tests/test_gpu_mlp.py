@@ -175,6 +175,29 @@ def test_graph_replayed_training_equals_eager_training():
     assert a.step == b.step == 320
 
 
+def test_checkpoint_resume_is_bit_exact(tmp_path):
+    """Training that stops, saves its state (mlp.save_checkpoint), and goes
+    on in a network restored from the file (mlp.load_checkpoint) ends with
+    the parameters, Adam moments, BF16 copy and step counter bit-identical to
+    the same training without the interruption."""
+    n_in, width, n_out = 7, 64, 40
+    d, p, a = _net(n_in, width, n_out, 64, 43)
+    rng = np.random.default_rng(44)
+    X = torch.from_numpy(rng.uniform(-1, 1, size=(700, n_in)).astype(np.float32)).cuda()
+    T = torch.from_numpy(rng.normal(size=(700, n_out)).astype(np.float32)).cuda()
+    mlp.train(a, X, T, steps=150, batch=64, lr=2e-3, seed=6)
+    path = str(tmp_path / "net.npz")
+    mlp.save_checkpoint(a, path)
+    b = mlp.load_checkpoint(path)
+    la = mlp.train(a, X, T, steps=120, batch=64, lr=1e-3, seed=7)
+    lb = mlp.train(b, X, T, steps=120, batch=64, lr=1e-3, seed=7)
+    torch.cuda.synchronize()
+    assert la == lb
+    for k in ("p", "q", "m", "v"):
+        assert torch.equal(getattr(a, k), getattr(b, k)), k
+    assert a.step == b.step == 270
+
+
 def test_learned_warm_start_beats_the_cold_start():
     """The network trained (by these kernels) on the converged cold-start
     solutions of 32768 instances, against the plain cold start on 4096

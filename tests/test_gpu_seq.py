@@ -202,6 +202,29 @@ def test_workload2_small_batch(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_batched_solve_is_bitwise_deterministic(prec):
+    """Two solves of the same batch (fresh workspaces, the outputs cleared in
+    between): x, u, y, the pivot flags, the backward errors, statuses and
+    refinement counts are bit-identical -- no reduction order or race
+    depends on scheduling."""
+    bh = inputs.workload2(count=148, N=64)
+    db = rlqr.DeviceBatch.from_uniform(bh)
+    runs = []
+    for _ in range(2):
+        for t in (db.x, db.u, db.y):
+            t.fill_(float("nan"))
+        db.pivot_pd.fill_(0xAB)
+        out = solve_batch(db, prec)
+        runs.append(dict(x=db.x.clone(), u=db.u.clone(), y=db.y.clone(),
+                         f=db.pivot_pd.clone(), rel=out["rel"], st=out["status"], it=out["iters"]))
+    a, b = runs
+    for k in ("x", "u", "y", "f"):
+        assert torch.equal(a[k].view(torch.uint8), b[k].view(torch.uint8)), k
+    for k in ("rel", "st", "it"):
+        assert np.array_equal(a[k].view(np.uint8), b[k].view(np.uint8)), k
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_workload2_full_batch(prec):
     """The full 1024-instance workload (n=12, m=4, N=256), every instance
     checked: flags byte-identical, oracle rel-resid <= 1e-9."""
