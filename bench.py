@@ -10,10 +10,15 @@ sweep with the FP64 pivot certificate, FP64 KKT residual, FP32 corrections with
 FP64 accumulation until every instance reaches rel-resid <= 1e-9 (device-side
 early exit), i.e. every row of the hot path.  Inputs (0.9 GB) exceed L2, so no
 flush is needed between steps.  The plain FP64 GPU recursion on the same batch
-is timed beside it, and the FP64 CPU oracle is the CPU baseline.
+is timed beside it, and the FP64 CPU oracle is the CPU baseline.  With N = 1
+the line also carries the other configurations under "configs" (the small
+single instance, the long horizon, the first 512 ragged instances and the
+IPM on 8192 cart-double-pendulum trajectories), each with its own timing and
+CPU baseline; --no-extras leaves them out.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
     python bench.py --profile-instances K   # profiling case, no bench line
+    python bench.py --residual-route 1      # fixed residual route (profiler runs)
     python bench.py --long-horizon          # the single long-horizon instance
     python bench.py --latency               # latency of the small single instance
     python bench.py --cross P               # cross-stage variables, p = P
